@@ -1,0 +1,208 @@
+"""QML estimator and pixel likelihood by their definitions (oracle).
+
+Every function states the passage it follows.  Harmonic form: with the
+transfer function folded into Y (see oracle.harmonic), S = Y Lambda Y^T and
+the derivative of S with respect to one spectrum entry a = (XY, l) is
+P_a = Y E_a Y^T (Sect. 2.3.3), where E_a is the 0/1 selector
+
+    E_a = sum_{m-modes i of l} sum_{(u,v) in pairs(a)} e_{u,i} e_{v,i}^T,
+    pairs(XX) = {(X,X)},  pairs(XY) = {(X,Y), (Y,X)} for X != Y
+
+(the symmetric placement of a cross-spectrum entry in the 3x3 blocks of
+Eq. Lambda_TEB).  With W = Y^T C^-1 Y and w = Y^T C^-1 d the trace identities
+used below are the cyclic rewrites of Eqs. fisher, q_ell, noise_bias:
+
+  F_ab = 1/2 tr[C^-1 P_a C^-1 P_b] = 1/2 sum W[v i, u' j] W[v' j, u i]  (Eq. sparse_trace)
+  y_a  = 1/2 d^T C^-1 P_a C^-1 d  = 1/2 sum w[u i] w[v i]               (Eq. q_harmonic)
+  b_a  = 1/2 tr[C^-1 P_a C^-1 N]  = 1/2 sum (Z^T N Z)[v i, u i], Z = C^-1 Y
+
+The noise bias is evaluated with the explicit product Z^T N Z, not through any
+identity the CUDA path may use.  Everything is float64 numpy/scipy.
+
+Fisher index order: spectrum-major over the requested spectra, then l.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+SPEC_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))  # TT EE BB TE TB EB
+
+
+def pairs(spec: int):
+    x, y = SPEC_PAIRS[spec]
+    return [(x, x)] if x == y else [(x, y), (y, x)]
+
+
+def lambda_blocks(cl: np.ndarray, comps, lmin: int, lmax: int) -> np.ndarray:
+    """Lambda_l restricted to the fields present: shape (nl, nc, nc) (Eq. Lambda_TEB)."""
+    nc = len(comps)
+    lam = np.zeros((lmax - lmin + 1, nc, nc))
+    for s, (x, y) in enumerate(SPEC_PAIRS):
+        if x in comps and y in comps:
+            i, j = comps.index(x), comps.index(y)
+            lam[:, i, j] = cl[s, lmin:lmax + 1]
+            lam[:, j, i] = cl[s, lmin:lmax + 1]
+    return lam
+
+
+def _l_of_mode(lmin: int, lmax: int) -> np.ndarray:
+    return np.concatenate([np.full(2 * l + 1, l) for l in range(lmin, lmax + 1)])
+
+
+def apply_lambda(Y: np.ndarray, cl, comps, lmin: int, lmax: int) -> np.ndarray:
+    """Y Lambda (columns mixed within each (l, m) by the 3x3 spectrum block)."""
+    k0 = (lmax + 1) ** 2 - lmin ** 2
+    lam = lambda_blocks(cl, comps, lmin, lmax)
+    lm = _l_of_mode(lmin, lmax) - lmin
+    nc = len(comps)
+    out = np.zeros_like(Y)
+    for b in range(nc):
+        for a in range(nc):
+            out[:, b * k0:(b + 1) * k0] += Y[:, a * k0:(a + 1) * k0] * lam[lm, a, b][None, :]
+    return out
+
+
+def signal_cov(Y, cl, comps, lmin, lmax) -> np.ndarray:
+    """S = Y Lambda Y^T (Eq. S_factored)."""
+    return apply_lambda(Y, cl, comps, lmin, lmax) @ Y.T
+
+
+def total_cov(Y, cl, comps, lmin, lmax, N) -> np.ndarray:
+    """C = S + N (Eq. total_cov)."""
+    return signal_cov(Y, cl, comps, lmin, lmax) + N
+
+
+def _blocksum(H: np.ndarray, lmin: int, lmax: int) -> np.ndarray:
+    """Sum an (k0 x k0) array over (l, l') blocks of modes -> (nl x nl)."""
+    starts = np.array([l * l - lmin * lmin for l in range(lmin, lmax + 1)])
+    return np.add.reduceat(np.add.reduceat(H, starts, axis=0), starts, axis=1)
+
+
+def fisher_from_W(W: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarray:
+    """F_ab = 1/2 tr[W E_a W E_b] (Eqs. fisher_harmonic, sparse_trace)."""
+    k0 = (lmax + 1) ** 2 - lmin ** 2
+    nc = len(comps)
+    nl = lmax - lmin + 1
+    W4 = W.reshape(nc, k0, nc, k0)
+    ci = {c: comps.index(c) for c in comps}
+    ns = len(spec)
+    F = np.zeros((ns * nl, ns * nl))
+    cache = {}
+    for A, sa in enumerate(spec):
+        for B, sb in enumerate(spec):
+            acc = np.zeros((nl, nl))
+            for (u, v) in pairs(sa):
+                for (up, vp) in pairs(sb):
+                    key = (v, up, vp, u)
+                    if key not in cache:
+                        # H[i, j] = W[v i, u' j] * W[v' j, u i]
+                        H = W4[ci[v], :, ci[up], :] * W4[ci[vp], :, ci[u], :].T
+                        cache[key] = _blocksum(H, lmin, lmax)
+                    acc += cache[key]
+            F[A * nl:(A + 1) * nl, B * nl:(B + 1) * nl] = 0.5 * acc
+    return F
+
+
+def trace_selector(M: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarray:
+    """t_a = sum_{(u,v) in pairs(a)} sum_{i in l} M[v i, u i]  (= tr[E_a M])."""
+    k0 = (lmax + 1) ** 2 - lmin ** 2
+    nl = lmax - lmin + 1
+    starts = np.array([l * l - lmin * lmin for l in range(lmin, lmax + 1)])
+    out = np.zeros(len(spec) * nl)
+    for A, sa in enumerate(spec):
+        acc = np.zeros(nl)
+        for (u, v) in pairs(sa):
+            iu, iv = comps.index(u), comps.index(v)
+            d = np.einsum("ii->i", M[iv * k0:(iv + 1) * k0, iu * k0:(iu + 1) * k0])
+            acc += np.add.reduceat(d, starts)
+        out[A * nl:(A + 1) * nl] = acc
+    return out
+
+
+def quad_selector(w: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarray:
+    """y_a = 1/2 w^T E_a w for each column of w (Eq. q_harmonic); shape (na, nsims)."""
+    w = np.atleast_2d(w.T).T if w.ndim == 1 else w
+    k0 = (lmax + 1) ** 2 - lmin ** 2
+    nl = lmax - lmin + 1
+    starts = np.array([l * l - lmin * lmin for l in range(lmin, lmax + 1)])
+    out = np.zeros((len(spec) * nl, w.shape[1]))
+    for A, sa in enumerate(spec):
+        acc = np.zeros((nl, w.shape[1]))
+        for (u, v) in pairs(sa):
+            iu, iv = comps.index(u), comps.index(v)
+            prod = w[iu * k0:(iu + 1) * k0] * w[iv * k0:(iv + 1) * k0]
+            acc += np.add.reduceat(prod, starts, axis=0)
+        out[A * nl:(A + 1) * nl] = 0.5 * acc
+    return out
+
+
+def normalisations(F: np.ndarray, q: np.ndarray, cut: float = 1e-12):
+    """The three output modes of Sect. 2.5.
+
+    deconvolved  C = F^-1 q                          (Eq. deconvolved)
+    decorrelated C = F^-1/2 q, F^-1/2 = U Xi^-1/2 U^T with eigenvalues below
+                 cut * max set to zero               (Eq. decorrelated)
+    convolved    q itself, window matrix F           (Eq. convolved)
+    """
+    cf = sla.cho_factor(F, lower=True)
+    deconv = sla.cho_solve(cf, q)
+    xi, U = np.linalg.eigh(F)
+    keep = xi >= cut * xi.max()
+    inv_sqrt = np.zeros_like(xi)
+    inv_sqrt[keep] = 1.0 / np.sqrt(xi[keep])
+    Fm12 = (U * inv_sqrt) @ U.T
+    decorr = Fm12 @ q
+    return deconv, decorr, q.copy(), Fm12
+
+
+def loglike(C: np.ndarray, d: np.ndarray):
+    """lnL = -1/2 [d^T C^-1 d + ln|C|] with const = 0 (Eq. pixel_likelihood).
+
+    Returns (lnL, chi2, logdet); d may hold several maps as columns.
+    """
+    L = np.linalg.cholesky(C)
+    logdet = 2.0 * np.sum(np.log(np.diag(L)))
+    x = sla.solve_triangular(L, d, lower=True)
+    chi2 = np.sum(x * x, axis=0)
+    return -0.5 * (chi2 + logdet), chi2, logdet
+
+
+def qml(Y, cl_fid, comps, lmin, lmax, N, spec, maps=None, want_bias=True):
+    """Fisher matrix, noise bias, quadratic estimates and Cl in three modes.
+
+    Follows Sect. 2.2 (Eqs. fisher, q_ell, noise_bias, qml_estimate) in the
+    harmonic factorisation of Sect. 2.3.3.  Returns a dict.
+    """
+    C = total_cov(Y, cl_fid, comps, lmin, lmax, N)
+    cf = sla.cho_factor(C, lower=True)
+    Z = sla.cho_solve(cf, Y)          # C^-1 Y
+    W = Y.T @ Z                       # Y^T C^-1 Y   (Eq. projected_inv)
+    W = 0.5 * (W + W.T)
+    F = fisher_from_W(W, spec, comps, lmin, lmax)
+    out = {"F": F, "W": W, "C": C}
+    if want_bias:
+        ZNZ = Z.T @ (N @ Z)
+        out["b"] = 0.5 * trace_selector(ZNZ, spec, comps, lmin, lmax)
+    if maps is not None:
+        maps = maps.reshape(maps.shape[0], -1)
+        w = Y.T @ sla.cho_solve(cf, maps)   # Y^T C^-1 d  (Eq. weighted_data)
+        y = quad_selector(w, spec, comps, lmin, lmax)
+        out["w"] = w
+        out["y"] = y
+        if want_bias:
+            q = y - out["b"][:, None]
+            out["q"] = q
+            dec, decor, conv, Fm12 = normalisations(F, q)
+            out.update(cl_deconv=dec, cl_decorr=decor, q_conv=conv, F_inv_sqrt=Fm12)
+    return out
+
+
+def qml_for(wl, Y, maps=None, want_bias=True):
+    """qml() for a synthetic workload description."""
+    return qml(Y, wl.cl_fid, wl.comps, wl.lmin, wl.lmax, wl.N(), wl.spec, maps, want_bias)
+
+
+def simulate(Y: np.ndarray, alm: np.ndarray, noise: np.ndarray) -> np.ndarray:
+    """d = Y a + n (Eq. data_model with s = Y a)."""
+    return Y @ alm + noise

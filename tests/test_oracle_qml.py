@@ -1,0 +1,184 @@
+"""Pins for the oracle's Fisher matrix, noise bias, estimates and likelihood.
+
+P1 brute force, P2 exact closed form on a quadrature grid, P6 symmetry and
+positive definiteness, P7 the expectation identity <q> = F C, P8 Monte Carlo
+unbiasedness, P9 decorrelation.  Mutation tests plant a mistake in the oracle
+(on the CPU) and check that a pin catches it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import brute, harmonic, qml
+from paper_2605_21149_gb300 import synth
+
+
+def _tiny(has_T=True, has_P=True, nside=2, lmax=5, b0=20.0, cross=True, seed=1):
+    th, ph, z = synth.healpix_ring_centres(nside)
+    keep = synth.galactic_cut(z, b0)
+    th, ph = th[keep], ph[keep]
+    tl = synth.transfer(lmax, nside)
+    cl = synth.spectra(lmax)
+    if cross:
+        cl[4, 2:] = 0.02
+        cl[5, 2:] = 0.003
+    comps = ((0,) if has_T else ()) + ((1, 2) if has_P else ())
+    spec = tuple(s for s, (x, y) in enumerate(qml.SPEC_PAIRS) if x in comps and y in comps)
+    Y = harmonic.build_Y(2, lmax, th, ph, th, ph, tl, tl, has_T, has_P)
+    n = Y.shape[0]
+    g = np.random.default_rng(seed)
+    G = g.normal(size=(n, 5)) * 0.3
+    N = G @ G.T + np.eye(n)
+    d = g.normal(size=(n, 3))
+    return dict(th=th, ph=ph, tl=tl, cl=cl, comps=comps, spec=spec, Y=Y, N=N, d=d,
+                lmax=lmax, has_T=has_T, has_P=has_P)
+
+
+@pytest.mark.parametrize("has_T,has_P", [(True, False), (False, True), (True, True)])
+def test_P1_harmonic_vs_brute(has_T, has_P):
+    t = _tiny(has_T, has_P)
+    r = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"])
+    Ps = brute.pixel_derivatives(t["th"], t["ph"], t["th"], t["ph"], t["tl"], t["tl"],
+                                 has_T, has_P, 2, t["lmax"], t["spec"])
+    rb = brute.qml_dense(Ps, r["C"], t["N"], maps=t["d"])
+    for key in ("F", "b", "y"):
+        assert np.abs(r[key] - rb[key]).max() <= 1e-12 * np.abs(rb[key]).max(), key
+    lnl, chi2, logdet = qml.loglike(r["C"], t["d"])
+    assert np.allclose(lnl, rb["lnL"], rtol=1e-12, atol=0)
+    assert np.allclose(chi2, rb["chi2"], rtol=1e-12, atol=0)
+
+
+def _closed_form(cl, tl, sigma2, spec, comps, lmin, lmax):
+    """Per-l 3x3 closed forms on an exact quadrature grid (P2)."""
+    nl = lmax - lmin + 1
+    na = len(spec) * nl
+    F = np.zeros((na, na))
+    b = np.zeros(na)
+    logdet_sig = 0.0
+    for il, l in enumerate(range(lmin, lmax + 1)):
+        lam = qml.lambda_blocks(cl, comps, lmin, lmax)[il]
+        D = np.diag([tl[l]] * len(comps))
+        Cl = D @ lam @ D + sigma2 * np.eye(len(comps))
+        Ci = np.linalg.inv(Cl)
+        dC = []
+        for s in spec:
+            x, y = qml.SPEC_PAIRS[s]
+            E = np.zeros((len(comps), len(comps)))
+            E[comps.index(x), comps.index(y)] = 1
+            E[comps.index(y), comps.index(x)] = 1
+            dC.append(D @ E @ D)
+        for A in range(len(spec)):
+            for B in range(len(spec)):
+                F[A * nl + il, B * nl + il] = 0.5 * (2 * l + 1) * np.trace(Ci @ dC[A] @ Ci @ dC[B])
+            b[A * nl + il] = 0.5 * (2 * l + 1) * sigma2 * np.trace(Ci @ Ci @ dC[A])
+        logdet_sig += (2 * l + 1) * np.linalg.slogdet(np.eye(len(comps)) + D @ lam @ D / sigma2)[1]
+    return F, b, logdet_sig
+
+
+@pytest.mark.parametrize("has_T,has_P", [(True, False), (False, True), (True, True)])
+def test_P2_quadrature_closed_form(has_T, has_P):
+    """On a full-sky Gauss-Legendre grid with N = diag(sigma^2 / w_p) the harmonic
+    Gram matrix is exactly I/sigma^2, so F, b and ln|C| take per-l closed forms:
+      F^l_ab = (2l+1)/2 tr[Cl^-1 dCl_a Cl^-1 dCl_b],  b^l_a = (2l+1)/2 sigma^2 tr[Cl^-2 dCl_a],
+      ln|C| = sum_p ln(sigma^2/w_p) + sum_l (2l+1) ln|I + T Cl T / sigma^2|,
+    with Cl = T Chat_l T + sigma^2 I (3x3 over the fields present)."""
+    lmin, lmax = 2, 7
+    th, ph, w = synth.gauss_legendre_grid(lmax)
+    tl = synth.gaussian_beam(lmax, 0.25)
+    cl = synth.spectra(lmax)
+    cl[4, 2:] = 0.03
+    cl[5, 2:] = 0.002
+    comps = ((0,) if has_T else ()) + ((1, 2) if has_P else ())
+    spec = tuple(s for s, (x, y) in enumerate(qml.SPEC_PAIRS) if x in comps and y in comps)
+    Y = harmonic.build_Y(lmin, lmax, th, ph, th, ph, tl, tl, has_T, has_P)
+    sigma2 = 0.7
+    wt = np.concatenate([w] * len(comps)) if has_T else np.concatenate([w, w])
+    if has_T and has_P:
+        wt = np.concatenate([w, w, w])
+    N = np.diag(sigma2 / wt)
+    r = qml.qml(Y, cl, comps, lmin, lmax, N, spec)
+    Fc, bc, lds = _closed_form(cl, tl, sigma2, spec, comps, lmin, lmax)
+    assert np.abs(r["F"] - Fc).max() <= 1e-12 * np.abs(Fc).max()
+    assert np.abs(r["b"] - bc).max() <= 1e-12 * np.abs(bc).max()
+    d = np.random.default_rng(3).normal(size=(Y.shape[0], 2))
+    lnl, chi2, logdet = qml.loglike(r["C"], d)
+    ref = np.sum(np.log(sigma2 / wt)) + lds
+    assert abs(logdet - ref) <= 1e-12 * abs(ref)
+
+
+def test_P6_P7_P9_invariants():
+    """F symmetric positive definite (P6); 1/2 tr[C^-1 P_a] = (F C_fid)_a + b_a
+    (P7, exact because C = sum_b C_b P_b + N); F^-1/2 F F^-1/2 = I (P9)."""
+    t = _tiny(True, True, nside=4, lmax=9, cross=False)
+    r = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"])
+    F = r["F"]
+    assert np.abs(F - F.T).max() <= 1e-14 * np.abs(F).max()
+    assert np.linalg.eigvalsh(F).min() > 0
+    nl = t["lmax"] - 1
+    cfid = np.concatenate([t["cl"][s, 2:t["lmax"] + 1] for s in t["spec"]])
+    lhs = 0.5 * qml.trace_selector(r["W"], t["spec"], t["comps"], 2, t["lmax"])
+    rhs = F @ cfid + r["b"]
+    assert np.abs(lhs - rhs).max() <= 1e-10 * np.abs(lhs).max()
+    M = r["F_inv_sqrt"] @ F @ r["F_inv_sqrt"]
+    assert np.abs(M - np.eye(len(F))).max() < 1e-10
+
+
+@pytest.mark.slow
+def test_P8_unbiased_monte_carlo():
+    """Mean of deconvolved Cl over 1000 seeded sims is within 4 sigma/sqrt(N)
+    of the fiducial for every (spectrum, l); the scatter matches F^-1 (P8)."""
+    wl = synth.workload(0)
+    Y = harmonic.build_Y_for(wl)
+    nsims = 1000
+    g = synth.rng(0, synth.P_SIMS)
+    alm = synth.draw_alm(wl.cl_fid, wl.lmin, wl.lmax, wl.comps, nsims, g)
+    noise = synth.noise_draws(wl.G, nsims, g)
+    d = qml.simulate(Y, alm, noise)
+    r = qml.qml_for(wl, Y, maps=d)
+    chat = r["cl_deconv"]
+    Finv = np.linalg.inv(r["F"])
+    sig = np.sqrt(np.diag(Finv))
+    cfid = np.concatenate([wl.cl_fid[s, wl.lmin:wl.lmax + 1] for s in wl.spec])
+    z = (chat.mean(axis=1) - cfid) / (sig / math.sqrt(nsims))
+    assert np.all(np.abs(z) < 4.0)
+    ratio = chat.std(axis=1) / sig
+    assert np.all((ratio > 0.85) & (ratio < 1.15))
+
+
+# ---------------------------------------------------------------------------
+# mutation tests: plant a mistake in the oracle and check a pin fails
+# ---------------------------------------------------------------------------
+def test_mutation_eb_sign_is_caught(monkeypatch):
+    """Flipping the sign of the E combination (Eq. EB_from_spin) in the real
+    basis flips TE/TB: the brute-force pin P1 must notice."""
+    t = _tiny(True, True)
+    orig = harmonic.theta_functions
+
+    def flipped(l, theta):
+        lam, F1, F2 = orig(l, theta)
+        return lam, -F1, -F2
+
+    monkeypatch.setattr(harmonic, "theta_functions", flipped)
+    Y = harmonic.build_Y(2, t["lmax"], t["th"], t["ph"], t["th"], t["ph"], t["tl"], t["tl"], True, True)
+    S = qml.signal_cov(Y, t["cl"], t["comps"], 2, t["lmax"])
+    Ps = brute.pixel_derivatives(t["th"], t["ph"], t["th"], t["ph"], t["tl"], t["tl"],
+                                 True, True, 2, t["lmax"], t["spec"])
+    Sb = brute.signal_from_derivatives(Ps, t["cl"], t["spec"], 2, t["lmax"])
+    assert np.abs(S - Sb).max() > 1e-3 * np.abs(S).max()
+
+
+def test_mutation_dropped_cross_pair_is_caught(monkeypatch):
+    """Dropping the (Y,X) half of a cross-spectrum selector breaks P2."""
+    monkeypatch.setattr(qml, "pairs", lambda s: [qml.SPEC_PAIRS[s]])
+    lmin, lmax = 2, 5
+    th, ph, w = synth.gauss_legendre_grid(lmax)
+    tl = np.ones(lmax + 1)
+    cl = synth.spectra(lmax)
+    comps = (0, 1, 2)
+    spec = tuple(range(6))
+    Y = harmonic.build_Y(lmin, lmax, th, ph, th, ph, tl, tl, True, True)
+    N = np.diag(0.5 / np.concatenate([w, w, w]))
+    r = qml.qml(Y, cl, comps, lmin, lmax, N, spec)
+    Fc, _, _ = _closed_form(cl, tl, 0.5, spec, comps, lmin, lmax)
+    assert np.abs(r["F"] - Fc).max() > 1e-3 * np.abs(Fc).max()
