@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the QML hot path on one or more GB300s (one process per GPU).
+
+Workload: TQU, HEALPix Nside 16 with the |b| < 20 deg cut (n = 5952 rows),
+l = 2..47 (k = 6900 modes), six spectra, dense rank-200 noise, 100 simulated
+maps.  One step = qml_fisher (Y build, C = Y Lambda Y^T + N, Cholesky,
+X = L^-1 Y, W = X^T X, Fisher block sums, noise bias, eigendecomposition of F)
++ qml_estimate on the 100 maps (y, deconvolved / decorrelated / convolved Cl)
++ pix_loglike of one map at the fiducial spectra.  Metric: Fisher + Cl solves
+per second over all ranks (weak scaling: every rank solves its own replica).
+
+--impl reference times the CPU oracle (float64 numpy/scipy on the host
+cores) on the same workload, one solve per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Fisher+Cl solves/s (TQU Nside16 l2-47, 100 sims)"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--nsims", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload_config(nsims):
+    from paper_2605_21149_gb300 import synth
+    wl = synth.workload(1)
+    return wl, {"workload": f"{wl.name}: TQU HEALPix Nside 16, |b|<20 deg cut, n={wl.n} rows, "
+                            f"l=2..47 (k={wl.k}), 6 spectra, dense rank-200 N, {nsims} sims",
+                "n": wl.n, "k": wl.k, "nsims": nsims,
+                "l2": "inputs larger than L2 (N 283 MB, Y 329 MB, W 381 MB per step)"}
+
+
+# ------------------------------------------------------------- oracle ----
+def oracle_solve(wl, Y, maps):
+    from oracle import qml
+    return qml.qml_for(wl, Y, maps=maps)
+
+
+def oracle_inputs(wl, nsims):
+    from oracle import harmonic, qml
+    from paper_2605_21149_gb300 import synth
+    g = synth.rng(1, synth.P_SIMS)
+    alm = synth.draw_alm(wl.cl_fid, wl.lmin, wl.lmax, wl.comps, nsims, g)
+    noise = synth.noise_draws(wl.G, nsims, g)
+    Y = harmonic.build_Y_for(wl)
+    return Y, qml.simulate(Y, alm, noise)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl, cfg = workload_config(args.nsims)
+    Y, maps = oracle_inputs(wl, args.nsims)
+    for _ in range(args.warmup):
+        oracle_solve(wl, Y, maps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_solve(wl, Y, maps)
+    t = time.perf_counter() - t0
+    v = args.steps / t
+    cores = cpu_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one full Fisher + Cl solve per step (oracle, numpy/scipy "
+                                       "float64 on the host cores)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- ours ----
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def measure_fp64_peak(torch, n=8192, reps=4):
+    """cuBLAS DGEMM (torch.matmul float64) throughput: the float64 denominator."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    del a, b
+    torch.cuda.empty_cache()
+    return best
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2605_21149_gb300 import _native, api, build, synth
+    build.build()
+    lib = _native.load()
+
+    wl, cfg = workload_config(args.nsims)
+    cfg["parallelism"] = f"replicas x{world} (no data-path collective)"
+
+    # ---- CPU baseline (rank 0, N = 1 only): the oracle as it stands
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Y, omaps = oracle_inputs(wl, args.nsims)
+        t0 = time.perf_counter()
+        oracle_solve(wl, Y, omaps)
+        tc = time.perf_counter() - t0
+        cpu = {"value": 1.0 / tc, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": "one full Fisher + Cl (100 sims) solve of this workload, "
+                         f"{tc:.1f} s (numpy/scipy float64)"}
+        del Y, omaps
+
+    # ---- device inputs
+    prob = api.Problem.from_workload(wl, device=True)
+    g = synth.rng(1, synth.P_SIMS)
+    alm = synth.draw_alm(wl.cl_fid, wl.lmin, wl.lmax, wl.comps, args.nsims, g)
+    noise = synth.noise_draws(wl.G, args.nsims, g)
+    td = lambda x: torch.as_tensor(x, device="cuda").t().contiguous().t()
+    maps = api.synthesize(prob, td(alm), td(noise))
+    cl_dev = torch.as_tensor(wl.cl_fid.reshape(-1), device="cuda")
+    map1 = maps[:, :1]
+
+    def step():
+        F, plan = api.fisher(prob)
+        plan.estimate(maps)
+        api.loglike(prob, cl_dev, map1)
+        plan.free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    dev_uuid = str(getattr(torch.cuda.get_device_properties(local), "uuid", local))
+    if dev_uuid and not dev_uuid.startswith("GPU-") and len(dev_uuid) > 8:
+        dev_uuid = "GPU-" + dev_uuid
+    sampler = ClockSampler(dev_uuid)
+    sampler.start()
+    time.sleep(0.3)
+    c0 = lib.qml_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    c1 = lib.qml_launch_count()
+    clocks = sampler.stop()
+    t = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        t = float(tt.item())
+    value = world * args.steps / t
+
+    # ---- lnL evals/s (single map, fiducial spectra) and the dominant kernel
+    lnl_rate = None
+    roof = None
+    if rank == 0:
+        reps = max(2, args.steps)
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record()
+        for _ in range(reps):
+            api.loglike(prob, cl_dev, map1)
+        e3.record()
+        e3.synchronize()
+        lnl_rate = reps / (e2.elapsed_time(e3) * 1e-3)
+        # dominant kernel: float64 tiled GEMM; timed on its largest launch of the
+        # step (W = X^T X, lower triangle: k x k x n) with CUDA events on the
+        # stream it runs on
+        X = torch.randn(wl.k, wl.n, dtype=torch.float64, device="cuda").t()
+        W = torch.empty(wl.k, wl.k, dtype=torch.float64, device="cuda").t()
+        api.gemm(X, X, W, transA=True, lower=True)
+        reps_g = 3
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record()
+        for _ in range(reps_g):
+            api.gemm(X, X, W, transA=True, lower=True)
+        e5.record()
+        e5.synchronize()
+        dur = e4.elapsed_time(e5) * 1e-3 / reps_g
+        flops = float(wl.k) * wl.k * wl.n  # k(k+1)/2 outputs x 2n flops
+        achieved = flops / dur / 1e12
+        del X, W
+        torch.cuda.empty_cache()
+        fp64_peak = measure_fp64_peak(torch)
+        roof = {"kernel": "dgemm_kernel<T,N> (W = X^T X lower, k=6900, n=5952)",
+                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "peak_source": "cuBLAS DGEMM (torch.matmul float64 8192^3, best of 4) "
+                               "measured in this run; MEASURED_PEAKS.json has no float64 entry",
+                "traffic": None, "flops_per_launch": flops, "ms_per_launch": dur * 1e3}
+
+    # ---- end to end through the same entry points with pinned host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        def pinned(a):
+            t_ = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+            t_.numpy()[...] = a
+            return t_.numpy()
+        hp = api.Problem(wl.lmin, wl.lmax, theta_T=pinned(wl.theta_T), phi_T=pinned(wl.phi_T),
+                         theta_P=pinned(wl.theta_P), phi_P=pinned(wl.phi_P),
+                         transfer_T=pinned(wl.transfer_T), transfer_P=pinned(wl.transfer_P),
+                         spec=wl.spec, cl_fid=pinned(wl.cl_fid.reshape(-1)), N=pinned(wl.N()))
+        hmaps = np.asfortranarray(maps.cpu().numpy())
+        hm = torch.empty((args.nsims, wl.n), dtype=torch.float64, pin_memory=True).numpy().T
+        hm[...] = hmaps
+        h1 = np.asfortranarray(hm[:, :1])
+        hcl = pinned(wl.cl_fid.reshape(-1))
+
+        def hstep():
+            F, plan = api.fisher(hp)
+            est = plan.estimate(hm)
+            api.loglike(hp, hcl, h1)
+            plan.free()
+            return est
+        hstep()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        te = time.perf_counter() - t0
+        nb = 8
+        geo = (2 * wl.npix_T + 2 * wl.npix_P + 2 * (wl.lmax + 1) + 6 * (wl.lmax + 1)) * nb
+        h2d = 2 * (geo + wl.n * wl.n * nb) + wl.n * args.nsims * nb + wl.n * nb + 6 * (wl.lmax + 1) * nb
+        na = len(wl.spec) * wl.nl
+        d2h = na * na * nb + (4 * na * args.nsims + na) * nb + 3 * nb
+        e2e = {"value": args.steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "note": "same C-ABI calls with pinned host buffers; copies inside the timed region"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": cfg,
+                "lnl_evals_per_s": lnl_rate, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": int(c1 - c0), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

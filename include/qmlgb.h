@@ -1,0 +1,173 @@
+/*
+ * qmlgb.h -- C ABI of the GB300 (sm_103a) QML / pixel-likelihood library.
+ *
+ * The method (Sect. 2 of the paper): data d = s + n with total covariance
+ * C = S + N (Eqs. data_model, total_cov), N a general dense SPD matrix;
+ * S = Y Lambda Y^T through the real harmonic matrix Y (Eqs. addition_theorem,
+ * S_factored, real_ylm; App. A for spin 2, Eqs. V_spin2 .. Lambda_TEB).
+ * Outputs: the Fisher matrix F (Eq. fisher, evaluated as Eq. sparse_trace on
+ * W = Y^T C^-1 Y, Eq. projected_inv), quadratic estimates y and the noise bias
+ * b (Eqs. q_ell, noise_bias, q_harmonic), Cl in the deconvolved, decorrelated
+ * and convolved normalisations (Eqs. deconvolved, decorrelated, convolved),
+ * and the Gaussian pixel log-likelihood (Eq. pixel_likelihood).
+ *
+ * ---------------------------------------------------------------- layout --
+ * All matrices are column-major float64 with the leading dimension equal to
+ * the row count unless an argument says otherwise.
+ *   pixels (rows of Y, rows/cols of N and C):  T pixels, then Q pixels, then
+ *       U pixels of the kept (unmasked) set, n = npix_T + 2 npix_P.
+ *   modes (columns of Y):  component-major over the fields present (T, then
+ *       E, then B), then l = lmin..lmax, then inside l: index 0 for m = 0,
+ *       2m-1 for cos(m phi), 2m for sin(m phi).  k0 = (lmax+1)^2 - lmin^2 per
+ *       component, k = ncomp * k0.  The transfer function T_l = B_l p_l of
+ *       each field is folded into its columns, so Lambda holds plain Cl.
+ *   spectra: index 0..5 = TT, EE, BB, TE, TB, EB.  cl arrays are [6][lmax+1].
+ *   Fisher / estimate index a = (spectrum position in spec[]) * nl + (l - lmin),
+ *       nl = lmax - lmin + 1, na = nspec * nl.
+ *   several maps / simulations are columns: maps is n x nsims, outputs are
+ *       na x nsims.
+ *
+ * ------------------------------------------------------ pointers, memory --
+ * Every array argument may point to device memory or to host memory (pinned
+ * or pageable); the library tells them apart with cudaPointerGetAttributes.
+ * Host inputs are copied to device workspace on `stream`, host outputs are
+ * copied back before the call returns.  Inputs are read-only and never kept;
+ * the caller owns every buffer it passes.  The library allocates its
+ * workspace with cudaMallocAsync on `stream` and frees it before returning,
+ * except what a qml_plan keeps until qml_plan_free.
+ * `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ * stream.  Every call synchronises `stream` before it returns, so the status
+ * covers device-side failures (not SPD, wait timeouts).
+ *
+ * --------------------------------------------------------------- errors --
+ * Calls return a qml_status; on anything but QML_OK the outputs are
+ * undefined and qml_last_error() (thread-local) holds a message.
+ * No call aborts the process.
+ */
+#ifndef QMLGB_H
+#define QMLGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QML_OK = 0,
+  QML_EINVAL = 1,     /* bad argument (sizes, pointers, spectra, lmin) */
+  QML_ENOTSPD = 2,    /* a Cholesky pivot was <= 0: matrix not positive definite */
+  QML_ENOMEM = 3,     /* device workspace allocation failed */
+  QML_ECUDA = 4,      /* a CUDA runtime call failed */
+  QML_ETIMEOUT = 5    /* a device-side wait exceeded its iteration budget */
+} qml_status;
+
+typedef enum {
+  QML_FP64 = 0,        /* every contraction in native float64 */
+  QML_SPLIT_BF16 = 1   /* large contractions as exact bf16-slice products on
+                          tcgen05 tensor cores (Ozaki-style splitting),
+                          recombined in float64; panels, logdets stay float64 */
+} qml_precision;
+
+/* Description of one analysis (Sect. 2.1; App. A.1.3 for several fields).
+ * theta_*, phi_*: colatitude / longitude (radians) of the kept pixel centres
+ * of the T field and of the Q/U field (any geometry).  transfer_*: T_l for
+ * l = 0..lmax.  cl_fid: fiducial spectra [6][lmax+1] defining C = S + N.
+ * N: n x n SPD noise covariance (only its lower triangle is read). */
+typedef struct {
+  int32_t has_T, has_P;
+  int32_t npix_T, npix_P;
+  const double *theta_T, *phi_T;
+  const double *theta_P, *phi_P;
+  int32_t lmin, lmax;            /* signal band = estimation window, lmin >= 2 */
+  const double *transfer_T, *transfer_P;
+  int32_t nspec;                 /* number of estimated spectra, 1..6 */
+  int32_t spec[6];               /* their indices (TT=0 .. EB=5), no repeats */
+  const double *cl_fid;
+  const double *N;
+  int32_t precision;             /* qml_precision */
+  int32_t nslices;               /* bf16 slices per operand for QML_SPLIT_BF16
+                                    (0 = library default) */
+} qml_problem;
+
+typedef struct qml_plan qml_plan;   /* opaque; owned by the library */
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t qml_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all devices); lets a caller count the launches of a region. */
+int64_t qml_launch_count(void);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *qml_last_error(void);
+
+/* Y (n x k, leading dimension ldy >= n): the real spin-0 / spin-2 harmonic
+ * matrix at the pixel centres with the transfer folded into its columns
+ * (Eqs. real_ylm, spin_y_def, EB_from_spin; Wigner d^l_{m,s} by the
+ * three-term recurrence in l of App. A.3 started from the half-angle closed
+ * form at l = max(|m|,|s|)). */
+qml_status qml_ybuild(const qml_problem *prob, double *Y, int64_t ldy, void *stream);
+
+/* Synthetic maps d = Y a + noise (Eq. data_model with s = Y a): alm is
+ * k x nsims real harmonic coefficients (same mode layout), noise is n x nsims.
+ * Output maps n x nsims.  Used to draw simulations from seeded inputs. */
+qml_status qml_synthesize(const qml_problem *prob, const double *alm, const double *noise,
+                          int32_t nsims, double *maps, void *stream);
+
+/* Fisher matrix F (na x na) of the spectra in prob->spec (Eq. fisher via
+ * Eqs. projected_inv, fisher_harmonic, sparse_trace) on the pixel basis:
+ * C = Y Lambda_fid Y^T + N, C = L L^T, X = L^-1 Y, W = X^T X, block sums.
+ * If plan is not NULL, *plan receives a plan holding L, X, F, the noise bias
+ * and the normalisation matrices for qml_estimate (the analogue of handing a
+ * Fisher object to the spectra stage).  Errors: QML_ENOTSPD if C is not
+ * positive definite. */
+qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan, void *stream);
+
+/* Quadratic estimates for nsims maps (n x nsims) against a plan from
+ * qml_fisher: y (na x nsims, Eq. q_harmonic without the bias), b (na, noise
+ * bias, Eq. noise_bias), cl_deconv = F^-1 (y - b) (Eq. deconvolved),
+ * cl_decorr = F^-1/2 (y - b) with eigenvalues below 1e-12 x max dropped
+ * (Eq. decorrelated), q_conv = y - b whose window matrix is F itself
+ * (Eq. convolved).  Any output pointer may be NULL to skip it. */
+qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims,
+                        double *y, double *b, double *cl_deconv, double *cl_decorr,
+                        double *q_conv, void *stream);
+
+/* Release a plan (NULL is accepted). */
+void qml_plan_free(qml_plan *plan);
+
+/* Gaussian pixel log-likelihood of nmaps maps (n x nmaps) at spectra cl_theta
+ * ([6][lmax+1]): lnL = -1/2 (d^T C^-1 d + ln|C|), constant dropped
+ * (Eq. pixel_likelihood), C = Y Lambda(theta) Y^T + N factored by Cholesky,
+ * ln|C| = 2 sum ln L_ii.  Outputs lnL, chi2 (length nmaps) and logdet (1);
+ * any may be NULL.  prob->cl_fid and prob->spec are ignored. */
+qml_status pix_loglike(const qml_problem *prob, const double *cl_theta, const double *maps,
+                       int32_t nmaps, double *lnL, double *chi2, double *logdet, void *stream);
+
+/* ---- dense building blocks (exposed for testing the kernels one by one) -- */
+
+/* In-place lower Cholesky A = L L^T of an n x n SPD matrix (lower triangle
+ * read and overwritten; the strict upper triangle is left untouched).
+ * *logdet (host or device, may be NULL) receives ln|A| = 2 sum ln L_ii.
+ * Errors: QML_ENOTSPD with the failing column in the message. */
+qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t precision,
+                     void *stream);
+
+/* B <- L^-1 B for lower-triangular L (n x n, from qml_potrf) and B n x nrhs. */
+qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, double *B,
+                    int64_t ldb, int32_t precision, void *stream);
+
+/* C <- alpha op(A) op(B) + beta C, op(X) = X or X^T (trans flags 0/1),
+ * op(A) m x kk, op(B) kk x nn, C m x nn.  lower != 0 writes only the lower
+ * triangle (i >= j) of a square C. */
+qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64_t kk,
+                    double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMLGB_H */

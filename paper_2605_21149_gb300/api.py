@@ -1,0 +1,270 @@
+"""Python binding of libqmlgb: argument marshalling only.
+
+Every numeric step runs in the library's CUDA kernels; this module turns
+torch tensors (device memory, current stream) or numpy arrays (host memory,
+staged by the library) into the pointers and sizes of the C ABI.
+
+Layout (see include/qmlgb.h): matrices are column-major.  A torch matrix of
+shape (rows, cols) is used as-is when its strides are (1, rows) (e.g. the
+transpose of a contiguous (cols, rows) tensor); otherwise a column-major copy
+is made first.  Returned matrices are column-major views of that kind.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as nat
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the supported setup
+    torch = None
+
+
+class QMLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{nat.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _lib():
+    return nat.load()
+
+
+def _check(status: int):
+    if status != nat.QML_OK:
+        raise QMLError(status, _lib().qml_last_error().decode(errors="replace"))
+
+
+def _is_torch(x):
+    return torch is not None and isinstance(x, torch.Tensor)
+
+
+def _stream(device_mode: bool):
+    if device_mode and torch is not None and torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _vec(x, keep):
+    """float64 contiguous vector -> pointer (kept alive in `keep`)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        t = x.to(torch.float64).contiguous()
+        keep.append(t)
+        return t.data_ptr()
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _mat(x, rows, cols, keep):
+    """float64 column-major (rows x cols) -> pointer."""
+    if _is_torch(x):
+        t = x.to(torch.float64)
+        if t.dim() == 1:
+            t = t.reshape(rows, cols) if cols == 1 else t.reshape(cols, rows).t()
+        if not (t.shape == (rows, cols) and (t.stride() == (1, rows) or cols == 1 and t.is_contiguous())):
+            t = t.reshape(rows, cols).t().contiguous().t()
+        keep.append(t)
+        return t.data_ptr()
+    a = np.asarray(x, dtype=np.float64)
+    a = np.asfortranarray(a.reshape(rows, cols) if a.ndim == 1 else a)
+    assert a.shape == (rows, cols), (a.shape, rows, cols)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _empty(rows, cols, like_device):
+    """Column-major (rows x cols) output: torch on the device or numpy on the host."""
+    if like_device:
+        return torch.empty((cols, rows), dtype=torch.float64, device="cuda").t()
+    return np.empty((rows, cols), dtype=np.float64, order="F")
+
+
+def _ptr(x):
+    return x.data_ptr() if _is_torch(x) else x.ctypes.data
+
+
+SPEC_INDEX = {"TT": 0, "EE": 1, "BB": 2, "TE": 3, "TB": 4, "EB": 5}
+
+
+class Problem:
+    """One analysis: geometry, band, transfer, spectra, noise (qml_problem).
+
+    Arrays may be torch tensors (device mode: everything must be on the GPU)
+    or numpy arrays (host mode: the library copies them in and results out).
+    """
+
+    def __init__(self, lmin, lmax, *, theta_T=None, phi_T=None, theta_P=None, phi_P=None,
+                 transfer_T=None, transfer_P=None, spec=("TT",), cl_fid=None, N=None,
+                 precision=nat.QML_FP64, nslices=0):
+        self._keep = []
+        has_T = theta_T is not None
+        has_P = theta_P is not None
+        probe = next(a for a in (theta_T, theta_P) if a is not None)
+        self.device = _is_torch(probe)
+        self.lmin, self.lmax = int(lmin), int(lmax)
+        self.npix_T = len(theta_T) if has_T else 0
+        self.npix_P = len(theta_P) if has_P else 0
+        self.n = self.npix_T + 2 * self.npix_P
+        self.comps = ((0,) if has_T else ()) + ((1, 2) if has_P else ())
+        self.k0 = (self.lmax + 1) ** 2 - self.lmin ** 2
+        self.k = len(self.comps) * self.k0
+        self.nl = self.lmax - self.lmin + 1
+        self.spec = tuple(SPEC_INDEX[s] if isinstance(s, str) else int(s) for s in spec)
+        self.na = len(self.spec) * self.nl
+        p = nat.QmlProblem()
+        p.has_T, p.has_P = int(has_T), int(has_P)
+        p.npix_T, p.npix_P = self.npix_T, self.npix_P
+        p.theta_T, p.phi_T = _vec(theta_T, self._keep), _vec(phi_T, self._keep)
+        p.theta_P, p.phi_P = _vec(theta_P, self._keep), _vec(phi_P, self._keep)
+        p.lmin, p.lmax = self.lmin, self.lmax
+        p.transfer_T = _vec(transfer_T, self._keep)
+        p.transfer_P = _vec(transfer_P, self._keep)
+        p.nspec = len(self.spec)
+        for i, s in enumerate(self.spec):
+            p.spec[i] = s
+        p.cl_fid = _vec(cl_fid, self._keep) if cl_fid is not None else None
+        p.N = _mat(N, self.n, self.n, self._keep) if N is not None else None
+        p.precision = int(precision)
+        p.nslices = int(nslices)
+        self._p = p
+
+    @classmethod
+    def from_workload(cls, wl, device=True, precision=nat.QML_FP64, nslices=0):
+        """Problem from a synth.Workload; device=True puts every array on cuda:0."""
+        def conv(a):
+            if a is None or len(a) == 0:
+                return None
+            if device:
+                return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+            return np.ascontiguousarray(a, dtype=np.float64)
+        N = wl.N()
+        return cls(wl.lmin, wl.lmax,
+                   theta_T=conv(wl.theta_T) if wl.has_T else None,
+                   phi_T=conv(wl.phi_T) if wl.has_T else None,
+                   theta_P=conv(wl.theta_P) if wl.has_P else None,
+                   phi_P=conv(wl.phi_P) if wl.has_P else None,
+                   transfer_T=conv(wl.transfer_T) if wl.has_T else None,
+                   transfer_P=conv(wl.transfer_P) if wl.has_P else None,
+                   spec=wl.spec, cl_fid=conv(wl.cl_fid.reshape(-1)),
+                   N=(torch.as_tensor(N, device="cuda") if device else N),
+                   precision=precision, nslices=nslices)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._p)
+
+
+def ybuild(prob: Problem):
+    """Y (n x k, column-major), transfer folded in (qml_ybuild)."""
+    Y = _empty(prob.n, prob.k, prob.device)
+    _check(_lib().qml_ybuild(prob.ref, _ptr(Y), prob.n, _stream(prob.device)))
+    return Y
+
+
+def synthesize(prob: Problem, alm, noise):
+    """maps = Y alm + noise (qml_synthesize); alm k x nsims, noise n x nsims."""
+    keep = []
+    nsims = alm.shape[1] if alm.ndim == 2 else 1
+    a = _mat(alm, prob.k, nsims, keep)
+    nz = _mat(noise, prob.n, nsims, keep)
+    out = _empty(prob.n, nsims, prob.device)
+    _check(_lib().qml_synthesize(prob.ref, a, nz, nsims, _ptr(out), _stream(prob.device)))
+    return out
+
+
+class Plan:
+    """Fisher-stage state reused by the estimates (qml_plan)."""
+
+    def __init__(self, handle, prob: Problem):
+        self._h = handle
+        self.prob = prob
+
+    def estimate(self, maps):
+        """dict y, b, cl_deconv, cl_decorr, q_conv for the columns of maps (n x nsims)."""
+        keep = []
+        pr = self.prob
+        nsims = maps.shape[1] if maps.ndim == 2 else 1
+        d = _mat(maps, pr.n, nsims, keep)
+        dev = pr.device
+        out = {k: _empty(pr.na, nsims, dev) for k in ("y", "cl_deconv", "cl_decorr", "q_conv")}
+        out["b"] = _empty(pr.na, 1, dev)
+        _check(_lib().qml_estimate(self._h, d, nsims, _ptr(out["y"]), _ptr(out["b"]),
+                                   _ptr(out["cl_deconv"]), _ptr(out["cl_decorr"]),
+                                   _ptr(out["q_conv"]), _stream(dev)))
+        out["b"] = out["b"][:, 0]
+        return out
+
+    def free(self):
+        if self._h:
+            _lib().qml_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def fisher(prob: Problem, keep_plan: bool = True):
+    """(F, plan) from qml_fisher; F is na x na, spectrum-major."""
+    F = _empty(prob.na, prob.na, prob.device)
+    h = ctypes.c_void_p(0)
+    _check(_lib().qml_fisher(prob.ref, _ptr(F), ctypes.byref(h) if keep_plan else None,
+                             _stream(prob.device)))
+    return F, (Plan(h, prob) if keep_plan else None)
+
+
+def loglike(prob: Problem, cl_theta, maps):
+    """(lnL, chi2, logdet) of the columns of maps at spectra cl_theta (pix_loglike)."""
+    keep = []
+    nmaps = maps.shape[1] if maps.ndim == 2 else 1
+    cl = _vec(cl_theta.reshape(-1) if hasattr(cl_theta, "reshape") else cl_theta, keep)
+    d = _mat(maps, prob.n, nmaps, keep)
+    dev = prob.device
+    lnl, chi2, ld = _empty(nmaps, 1, dev), _empty(nmaps, 1, dev), _empty(1, 1, dev)
+    _check(_lib().pix_loglike(prob.ref, cl, d, nmaps, _ptr(lnl), _ptr(chi2), _ptr(ld),
+                              _stream(dev)))
+    return lnl[:, 0], chi2[:, 0], ld[0, 0]
+
+
+def potrf(A, precision=nat.QML_FP64):
+    """In-place lower Cholesky of a square column-major matrix; returns ln|A|."""
+    n = A.shape[0]
+    dev = _is_torch(A)
+    ld = _empty(1, 1, dev)
+    _check(_lib().qml_potrf(n, _ptr(A), n, _ptr(ld), precision, _stream(dev)))
+    return ld[0, 0]
+
+
+def trsm(L, B, precision=nat.QML_FP64):
+    """In-place B <- L^-1 B (both column-major)."""
+    n, nrhs = B.shape
+    dev = _is_torch(B)
+    _check(_lib().qml_trsm(n, nrhs, _ptr(L), n, _ptr(B), n, precision, _stream(dev)))
+    return B
+
+
+def gemm(A, B, C=None, transA=False, transB=False, alpha=1.0, beta=0.0, lower=False,
+         precision=nat.QML_FP64):
+    """C <- alpha op(A) op(B) + beta C (column-major operands)."""
+    m = A.shape[1] if transA else A.shape[0]
+    kk = A.shape[0] if transA else A.shape[1]
+    nn = B.shape[0] if transB else B.shape[1]
+    dev = _is_torch(A)
+    if C is None:
+        C = _empty(m, nn, dev)
+        if dev:
+            C.zero_()
+        else:
+            C[:] = 0.0
+    _check(_lib().qml_gemm(int(transA), int(transB), m, nn, kk, alpha, _ptr(A), A.shape[0],
+                           _ptr(B), B.shape[0], beta, _ptr(C), C.shape[0], int(lower),
+                           precision, _stream(dev)))
+    return C

@@ -1,0 +1,582 @@
+// extern "C" entry points of libqmlgb (declared in include/qmlgb.h): argument
+// validation, host/device pointer staging, workspace, and the enqueue order
+// of the kernels for each call.  Everything numeric happens in the kernels of
+// ybuild.cu, dense.cu, fisher.cu and eig.cu.
+#include "qmlgb.h"
+#include "internal.cuh"
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace qmlgb;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void qmlgb::count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_err;
+
+qml_status fail(qml_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+void set_pool_threshold() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done = true;
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// One ABI call: stream, workspace, staging of host buffers, device status.
+struct Call {
+  cudaStream_t st;
+  std::vector<void *> bufs;
+  struct Back {
+    void *host;
+    const void *dev;
+    size_t bytes;
+  };
+  std::vector<Back> backs;
+  DevStatus *status = nullptr;
+  qml_status err = QML_OK;
+
+  explicit Call(void *s) : st((cudaStream_t)s) { set_pool_threshold(); }
+  ~Call() {
+    for (void *p : bufs) cudaFreeAsync(p, st);
+  }
+
+  bool cuda_ok(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    if (err == QML_OK) {
+      err = (e == cudaErrorMemoryAllocation) ? QML_ENOMEM : QML_ECUDA;
+      g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return false;
+  }
+
+  template <class T>
+  T *alloc(size_t count, const char *what = "workspace") {
+    if (err != QML_OK) return nullptr;
+    if (count == 0) count = 1;
+    void *p = nullptr;
+    if (!cuda_ok(cudaMallocAsync(&p, count * sizeof(T), st), what)) return nullptr;
+    bufs.push_back(p);
+    return (T *)p;
+  }
+
+  // device view of an input array (copied in when it lives on the host)
+  template <class T>
+  const T *in(const T *p, size_t count, const char *what) {
+    if (err != QML_OK || !p) return p;
+    if (is_device_ptr(p)) return p;
+    T *d = alloc<T>(count, what);
+    if (!d) return nullptr;
+    cuda_ok(cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, st), what);
+    return d;
+  }
+
+  // device view of an output array (copied back at finish when on the host)
+  template <class T>
+  T *out(T *p, size_t count, const char *what) {
+    if (err != QML_OK || !p) return p;
+    if (is_device_ptr(p)) return p;
+    T *d = alloc<T>(count, what);
+    if (!d) return nullptr;
+    backs.push_back({(void *)p, d, count * sizeof(T)});
+    return d;
+  }
+
+  bool make_status() {
+    status = alloc<DevStatus>(1, "status");
+    if (!status) return false;
+    return cuda_ok(cudaMemsetAsync(status, 0, sizeof(DevStatus), st), "status");
+  }
+
+  // copy host outputs back, wait, and translate the device status
+  qml_status finish() {
+    if (err != QML_OK) {
+      cudaStreamSynchronize(st);
+      return err;
+    }
+    cuda_ok(cudaGetLastError(), "kernel launch");
+    for (auto &b : backs)
+      cuda_ok(cudaMemcpyAsync(b.host, b.dev, b.bytes, cudaMemcpyDeviceToHost, st), "copy out");
+    DevStatus hs{};
+    if (status) cuda_ok(cudaMemcpyAsync(&hs, status, sizeof(hs), cudaMemcpyDeviceToHost, st), "status");
+    cuda_ok(cudaStreamSynchronize(st), "synchronize");
+    if (err != QML_OK) return err;
+    if (hs.code == QML_ENOTSPD) {
+      char buf[160];
+      if (hs.info > 0)
+        snprintf(buf, sizeof buf, "matrix not positive definite (Cholesky pivot at column %d)",
+                 hs.info - 1);
+      else
+        snprintf(buf, sizeof buf, "Fisher matrix not positive definite");
+      return fail(QML_ENOTSPD, buf);
+    }
+    if (hs.code == QML_ETIMEOUT) return fail(QML_ETIMEOUT, "device wait exceeded its budget");
+    if (hs.code != 0) return fail(QML_ECUDA, "device status " + std::to_string(hs.code));
+    return QML_OK;
+  }
+};
+
+// ------------------------------------------------------------- problems --
+const int kSpecX[6] = {0, 1, 2, 0, 0, 1};
+const int kSpecY[6] = {0, 1, 2, 1, 2, 2};
+
+struct Dims {
+  int nT = 0, nP = 0, n = 0;
+  int nc = 0, comps[3] = {0, 0, 0}, pos[3] = {-1, -1, -1};
+  int lmin = 0, lmax = 0, nl = 0, k0 = 0, k = 0;
+  int nspec_full = 0, full_ids[6];
+};
+
+qml_status check_problem(const qml_problem *p, Dims &d, bool need_spec, bool need_N) {
+  if (!p) return fail(QML_EINVAL, "problem is NULL");
+  if (!p->has_T && !p->has_P) return fail(QML_EINVAL, "no field (has_T and has_P both 0)");
+  if (p->lmin < 2) return fail(QML_EINVAL, "lmin must be >= 2");
+  if (p->lmax < p->lmin || p->lmax > 2048) return fail(QML_EINVAL, "need lmin <= lmax <= 2048");
+  if (p->has_T && (p->npix_T <= 0 || !p->theta_T || !p->phi_T || !p->transfer_T))
+    return fail(QML_EINVAL, "T field needs npix_T > 0, theta_T, phi_T, transfer_T");
+  if (p->has_P && (p->npix_P <= 0 || !p->theta_P || !p->phi_P || !p->transfer_P))
+    return fail(QML_EINVAL, "P field needs npix_P > 0, theta_P, phi_P, transfer_P");
+  if (p->precision != QML_FP64)
+    return fail(QML_EINVAL, "precision: only QML_FP64 is available in this build");
+  d.nT = p->has_T ? p->npix_T : 0;
+  d.nP = p->has_P ? p->npix_P : 0;
+  d.n = d.nT + 2 * d.nP;
+  d.nc = 0;
+  if (p->has_T) { d.pos[0] = d.nc; d.comps[d.nc++] = 0; }
+  if (p->has_P) {
+    d.pos[1] = d.nc; d.comps[d.nc++] = 1;
+    d.pos[2] = d.nc; d.comps[d.nc++] = 2;
+  }
+  d.lmin = p->lmin;
+  d.lmax = p->lmax;
+  d.nl = d.lmax - d.lmin + 1;
+  d.k0 = (d.lmax + 1) * (d.lmax + 1) - d.lmin * d.lmin;
+  d.k = d.nc * d.k0;
+  d.nspec_full = 0;
+  for (int s = 0; s < 6; ++s)
+    if (d.pos[kSpecX[s]] >= 0 && d.pos[kSpecY[s]] >= 0) d.full_ids[d.nspec_full++] = s;
+  if (need_spec) {
+    if (p->nspec < 1 || p->nspec > 6) return fail(QML_EINVAL, "nspec must be 1..6");
+    bool seen[6] = {false, false, false, false, false, false};
+    for (int i = 0; i < p->nspec; ++i) {
+      int s = p->spec[i];
+      if (s < 0 || s > 5) return fail(QML_EINVAL, "spectrum index outside 0..5");
+      if (seen[s]) return fail(QML_EINVAL, "spectrum listed twice");
+      seen[s] = true;
+      if (d.pos[kSpecX[s]] < 0 || d.pos[kSpecY[s]] < 0)
+        return fail(QML_EINVAL, "spectrum needs a field that is absent");
+    }
+    if (!p->cl_fid) return fail(QML_EINVAL, "cl_fid is NULL");
+  }
+  if (need_N && !p->N) return fail(QML_EINVAL, "N is NULL");
+  return QML_OK;
+}
+
+void spec_uv(const Dims &d, int s, int *uv) {
+  int x = d.pos[kSpecX[s]], y = d.pos[kSpecY[s]];
+  uv[0] = x;
+  uv[1] = y;
+  if (x == y) {
+    uv[2] = -1;
+    uv[3] = -1;
+  } else {
+    uv[2] = y;
+    uv[3] = x;
+  }
+}
+
+struct Staged {
+  YArgs y;
+  const double *cl = nullptr, *N = nullptr;
+};
+
+bool stage_problem(Call &c, const qml_problem *p, const Dims &d, Staged &s, const double *cl,
+                   bool need_N) {
+  const size_t L = (size_t)d.lmax + 1;
+  s.y.has_T = p->has_T;
+  s.y.has_P = p->has_P;
+  s.y.npix_T = d.nT;
+  s.y.npix_P = d.nP;
+  s.y.lmin = d.lmin;
+  s.y.lmax = d.lmax;
+  s.y.theta_T = p->has_T ? c.in(p->theta_T, d.nT, "theta_T") : nullptr;
+  s.y.phi_T = p->has_T ? c.in(p->phi_T, d.nT, "phi_T") : nullptr;
+  s.y.transfer_T = p->has_T ? c.in(p->transfer_T, L, "transfer_T") : nullptr;
+  s.y.theta_P = p->has_P ? c.in(p->theta_P, d.nP, "theta_P") : nullptr;
+  s.y.phi_P = p->has_P ? c.in(p->phi_P, d.nP, "phi_P") : nullptr;
+  s.y.transfer_P = p->has_P ? c.in(p->transfer_P, L, "transfer_P") : nullptr;
+  if (cl) s.cl = c.in(cl, 6 * L, "cl");
+  if (need_N) s.N = c.in(p->N, (size_t)d.n * d.n, "N");
+  return c.err == QML_OK;
+}
+
+template <class T>
+T *upload(Call &c, const T *host, size_t count, const char *what) {
+  T *d = c.alloc<T>(count, what);
+  if (d) c.cuda_ok(cudaMemcpyAsync(d, host, count * sizeof(T), cudaMemcpyHostToDevice, c.st), what);
+  return d;
+}
+
+// ------------------------------------------------------ blocked drivers --
+// Right-looking blocked Cholesky (block kNB): factor + invert the diagonal
+// block, panel A21 <- A21 L11^-T as a product with the inverse, trailing
+// A22 <- A22 - A21 A21^T on the lower triangle.
+void potrf_blocked(Call &c, double *A, int64_t n, int64_t lda, double *Linv, double *ldparts,
+                   double *logdet) {
+  for (int64_t j = 0; j < n; j += kNB) {
+    const int64_t jb = (n - j) < kNB ? (n - j) : kNB;
+    double *Lb = Linv + (j / kNB) * kNB * kNB;
+    launch_potrf_diag(A + j + j * lda, lda, n, j, Lb, ldparts + j / kNB, c.status, c.st);
+    if (j + jb < n) {
+      const int64_t m2 = n - j - jb;
+      double *A21 = A + (j + jb) + j * lda;
+      double *A22 = A + (j + jb) + (j + jb) * lda;
+      launch_dgemm(0, 1, m2, jb, jb, 1.0, A21, lda, Lb, kNB, 0.0, A21, lda, 0, c.status, c.st);
+      launch_dgemm(0, 1, m2, m2, jb, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1, c.status, c.st);
+    }
+  }
+  if (logdet) launch_sum_logdet(ldparts, (int)((n + kNB - 1) / kNB), logdet, c.st);
+}
+
+// Blocked forward substitution B <- L^-1 B using the diagonal-block inverses.
+void trsm_blocked(Call &c, const double *L, int64_t n, int64_t lda, const double *Linv,
+                  double *B, int64_t nrhs, int64_t ldb) {
+  for (int64_t j = 0; j < n; j += kNB) {
+    const int64_t jb = (n - j) < kNB ? (n - j) : kNB;
+    const double *Lb = Linv + (j / kNB) * kNB * kNB;
+    launch_dgemm(0, 0, jb, nrhs, jb, 1.0, Lb, kNB, B + j, ldb, 0.0, B + j, ldb, 0, c.status, c.st);
+    if (j + jb < n)
+      launch_dgemm(0, 0, n - j - jb, nrhs, jb, -1.0, L + (j + jb) + j * lda, lda, B + j, ldb, 1.0,
+                   B + j + jb, ldb, 0, c.status, c.st);
+  }
+}
+
+// C = Y Lambda(cl) Y^T + N (lower triangle) from a scratch Y buffer (n x k),
+// which is left holding G = Y L_Lambda.
+void build_C(Call &c, const Staged &s, const Dims &d, double *Y, double *C) {
+  double *lamL = c.alloc<double>((size_t)d.nl * d.nc * d.nc, "lambda factors");
+  if (!lamL) return;
+  launch_ybuild(s.y, Y, d.n, c.st);
+  launch_lambda_factor(s.cl, d.lmin, d.lmax, d.nc, d.comps, lamL, c.st);
+  launch_mix_lambda(Y, d.n, d.n, d.nc, d.k0, d.lmin, d.lmax, lamL, c.st);
+  launch_copy_lower(s.N, d.n, C, d.n, d.n, c.st);
+  launch_dgemm(0, 1, d.n, d.n, d.k, 1.0, Y, d.n, Y, d.n, 1.0, C, d.n, 1, c.status, c.st);
+}
+
+}  // namespace
+
+// ======================================================================
+struct qml_plan {
+  Dims d;
+  int nspec = 0;
+  int spec[6];
+  int na = 0;
+  cudaStream_t st = nullptr;
+  std::vector<void *> mem;
+  double *L = nullptr, *Linv = nullptr, *X = nullptr;
+  double *F = nullptr, *b = nullptr, *Finv = nullptr, *Fm12 = nullptr;
+  int *uv = nullptr;
+};
+
+extern "C" {
+
+int32_t qml_version(void) { return 100; }
+
+int64_t qml_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *qml_last_error(void) { return g_err.c_str(); }
+
+qml_status qml_ybuild(const qml_problem *prob, double *Y, int64_t ldy, void *stream) {
+  Dims d;
+  qml_status s = check_problem(prob, d, false, false);
+  if (s != QML_OK) return s;
+  if (!Y || ldy < d.n) return fail(QML_EINVAL, "Y is NULL or ldy < n");
+  Call c(stream);
+  Staged sp;
+  if (!stage_problem(c, prob, d, sp, nullptr, false)) return c.finish();
+  double *Yd = c.out(Y, (size_t)ldy * d.k, "Y");
+  if (!Yd) return c.finish();
+  launch_ybuild(sp.y, Yd, ldy, c.st);
+  return c.finish();
+}
+
+qml_status qml_synthesize(const qml_problem *prob, const double *alm, const double *noise,
+                          int32_t nsims, double *maps, void *stream) {
+  Dims d;
+  qml_status s = check_problem(prob, d, false, false);
+  if (s != QML_OK) return s;
+  if (nsims < 0 || !alm || !noise || !maps) return fail(QML_EINVAL, "bad synthesize arguments");
+  if (nsims == 0) return QML_OK;
+  Call c(stream);
+  Staged sp;
+  if (!stage_problem(c, prob, d, sp, nullptr, false)) return c.finish();
+  const double *a = c.in(alm, (size_t)d.k * nsims, "alm");
+  const double *nz = c.in(noise, (size_t)d.n * nsims, "noise");
+  double *out = c.out(maps, (size_t)d.n * nsims, "maps");
+  double *Y = c.alloc<double>((size_t)d.n * d.k, "Y");
+  if (!c.make_status() || !Y || !out) return c.finish();
+  launch_ybuild(sp.y, Y, d.n, c.st);
+  launch_copy_matrix(nz, d.n, out, d.n, d.n, nsims, c.st);
+  launch_dgemm(0, 0, d.n, nsims, d.k, 1.0, Y, d.n, a, d.k, 1.0, out, d.n, 0, c.status, c.st);
+  return c.finish();
+}
+
+void qml_plan_free(qml_plan *plan) {
+  if (!plan) return;
+  for (void *p : plan->mem) cudaFreeAsync(p, plan->st);
+  cudaStreamSynchronize(plan->st);
+  delete plan;
+}
+
+qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, void *stream) {
+  Dims d;
+  qml_status s = check_problem(prob, d, true, true);
+  if (s != QML_OK) return s;
+  if (!F) return fail(QML_EINVAL, "F is NULL");
+  if (plan_out) *plan_out = nullptr;
+  const int na = prob->nspec * d.nl;
+  const int naf = d.nspec_full * d.nl;
+  Call c(stream);
+  Staged sp;
+  if (!stage_problem(c, prob, d, sp, prob->cl_fid, true)) return c.finish();
+  double *Fout = c.out(F, (size_t)na * na, "F");
+  if (!c.make_status()) return c.finish();
+
+  // plan-owned buffers are allocated outside the per-call list
+  qml_plan *plan = new qml_plan();
+  plan->d = d;
+  plan->nspec = prob->nspec;
+  for (int i = 0; i < 6; ++i) plan->spec[i] = prob->spec[i];
+  plan->na = na;
+  plan->st = c.st;
+  auto palloc = [&](size_t count) -> double * {
+    void *p = nullptr;
+    if (c.err != QML_OK) return nullptr;
+    if (!c.cuda_ok(cudaMallocAsync(&p, count * sizeof(double), c.st), "plan buffers")) return nullptr;
+    plan->mem.push_back(p);
+    return (double *)p;
+  };
+  const int64_t nblocks = (d.n + kNB - 1) / kNB;
+  plan->L = palloc((size_t)d.n * d.n);
+  plan->Linv = palloc((size_t)nblocks * kNB * kNB);
+  plan->X = palloc((size_t)d.n * d.k);
+  plan->F = palloc((size_t)na * na);
+  plan->b = palloc(na);
+  plan->Finv = palloc((size_t)na * na);
+  plan->Fm12 = palloc((size_t)na * na);
+  {
+    void *p = nullptr;
+    if (c.err == QML_OK && c.cuda_ok(cudaMallocAsync(&p, 4 * 6 * sizeof(int), c.st), "plan"))
+      plan->mem.push_back(p);
+    plan->uv = (int *)p;
+  }
+  double *ldparts = c.alloc<double>(nblocks);
+  double *W = c.alloc<double>((size_t)d.k * d.k, "W");
+  const int NP = d.nc * d.nc, NU = NP * (NP + 1) / 2;
+  const int nblk = d.nl * (d.nl + 1) / 2;
+  double *parts = c.alloc<double>((size_t)nblk * NU);
+  double *diag = c.alloc<double>((size_t)d.nl * NP);
+  double *Ffull = c.alloc<double>((size_t)naf * naf);
+  double *tfull = c.alloc<double>(naf);
+  double *eigw = c.alloc<double>(fisher_eig_work_doubles(na));
+  double *minmax = c.alloc<double>(2);
+  int h_uv_full[24], h_uv[24], h_sel[6];
+  for (int i = 0; i < d.nspec_full; ++i) spec_uv(d, d.full_ids[i], h_uv_full + 4 * i);
+  for (int i = 0; i < prob->nspec; ++i) {
+    spec_uv(d, prob->spec[i], h_uv + 4 * i);
+    for (int j = 0; j < d.nspec_full; ++j)
+      if (d.full_ids[j] == prob->spec[i]) h_sel[i] = j;
+  }
+  int *uv_full = upload(c, h_uv_full, 4 * d.nspec_full, "spectra");
+  int *ids_full = upload(c, d.full_ids, d.nspec_full, "spectra");
+  int *sel = upload(c, h_sel, prob->nspec, "spectra");
+  if (c.err == QML_OK)
+    c.cuda_ok(cudaMemcpyAsync(plan->uv, h_uv, 4 * prob->nspec * sizeof(int),
+                              cudaMemcpyHostToDevice, c.st), "spectra");
+  if (c.err != QML_OK) {
+    qml_status e = c.finish();
+    qml_plan_free(plan);
+    return e;
+  }
+
+  // C = Y Lambda Y^T + N ; L L^T = C
+  build_C(c, sp, d, plan->X, plan->L);
+  potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
+  // X = L^-1 Y ; W = X^T X
+  launch_ybuild(sp.y, plan->X, d.n, c.st);
+  trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
+  launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1, c.status, c.st);
+  launch_symmetrize_lower(W, d.k, d.k, c.st);
+  // block sums -> F, noise bias
+  launch_fisher_blocksum(W, d.k, d.nc, d.k0, d.lmin, d.lmax, parts, diag, c.st);
+  launch_fisher_assemble(parts, diag, d.nc, d.nl, d.nspec_full, uv_full, Ffull, tfull, c.st);
+  launch_fisher_select(Ffull, tfull, sp.cl, d.lmin, d.lmax, d.nspec_full, ids_full, prob->nspec,
+                       sel, plan->F, plan->b, c.st);
+  c.cuda_ok(run_fisher_eig(plan->F, na, eigw, plan->Finv, plan->Fm12, minmax, c.status, c.st),
+            "eigendecomposition");
+  launch_copy_matrix(plan->F, na, Fout, na, na, na, c.st);
+  qml_status e = c.finish();
+  if (e != QML_OK || !plan_out) {
+    qml_plan_free(plan);
+    return e;
+  }
+  *plan_out = plan;
+  return QML_OK;
+}
+
+qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims, double *y, double *b,
+                        double *cl_deconv, double *cl_decorr, double *q_conv, void *stream) {
+  if (!plan) return fail(QML_EINVAL, "plan is NULL");
+  if (!maps || nsims <= 0) return fail(QML_EINVAL, "need maps and nsims > 0");
+  const Dims &d = plan->d;
+  const int na = plan->na;
+  Call c(stream);
+  const double *D = c.in(maps, (size_t)d.n * nsims, "maps");
+  double *U = c.alloc<double>((size_t)d.n * nsims, "U");
+  double *w = c.alloc<double>((size_t)d.k * nsims, "w");
+  double *yd = c.out(y, (size_t)na * nsims, "y");
+  if (!yd) yd = c.alloc<double>((size_t)na * nsims, "y");
+  double *q = c.out(q_conv, (size_t)na * nsims, "q");
+  if (!q) q = c.alloc<double>((size_t)na * nsims, "q");
+  double *bd = c.out(b, na, "b");
+  double *dec = c.out(cl_deconv, (size_t)na * nsims, "cl_deconv");
+  double *dcr = c.out(cl_decorr, (size_t)na * nsims, "cl_decorr");
+  if (!c.make_status()) return c.finish();
+  launch_copy_matrix(D, d.n, U, d.n, d.n, nsims, c.st);
+  trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, U, nsims, d.n);
+  // w = Y^T C^-1 d = X^T (L^-1 d)
+  launch_dgemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, w, d.k, 0, c.status, c.st);
+  launch_quad_y(w, d.k, nsims, d.nc, d.k0, d.lmin, d.lmax, plan->nspec, plan->uv, yd, c.st);
+  launch_sub_bias(yd, plan->b, na, nsims, q, c.st);
+  if (bd) launch_copy_matrix(plan->b, na, bd, na, na, 1, c.st);
+  if (dec) launch_dgemm(0, 0, na, nsims, na, 1.0, plan->Finv, na, q, na, 0.0, dec, na, 0, c.status, c.st);
+  if (dcr) launch_dgemm(0, 0, na, nsims, na, 1.0, plan->Fm12, na, q, na, 0.0, dcr, na, 0, c.status, c.st);
+  return c.finish();
+}
+
+qml_status pix_loglike(const qml_problem *prob, const double *cl_theta, const double *maps,
+                       int32_t nmaps, double *lnL, double *chi2, double *logdet, void *stream) {
+  Dims d;
+  qml_status s = check_problem(prob, d, false, true);
+  if (s != QML_OK) return s;
+  if (!cl_theta || !maps || nmaps <= 0) return fail(QML_EINVAL, "need cl_theta, maps, nmaps > 0");
+  Call c(stream);
+  Staged sp;
+  if (!stage_problem(c, prob, d, sp, cl_theta, true)) return c.finish();
+  const double *D = c.in(maps, (size_t)d.n * nmaps, "maps");
+  double *o_lnl = c.out(lnL, nmaps, "lnL");
+  double *o_chi = c.out(chi2, nmaps, "chi2");
+  double *o_ld = c.out(logdet, 1, "logdet");
+  if (!o_chi) o_chi = c.alloc<double>(nmaps);
+  if (!o_ld) o_ld = c.alloc<double>(1);
+  const int64_t nblocks = (d.n + kNB - 1) / kNB;
+  double *Y = c.alloc<double>((size_t)d.n * d.k, "Y");
+  double *C = c.alloc<double>((size_t)d.n * d.n, "C");
+  double *Linv = c.alloc<double>((size_t)nblocks * kNB * kNB);
+  double *ldparts = c.alloc<double>(nblocks);
+  double *U = c.alloc<double>((size_t)d.n * nmaps, "U");
+  if (!c.make_status()) return c.finish();
+  build_C(c, sp, d, Y, C);
+  potrf_blocked(c, C, d.n, d.n, Linv, ldparts, o_ld);
+  launch_copy_matrix(D, d.n, U, d.n, d.n, nmaps, c.st);
+  trsm_blocked(c, C, d.n, d.n, Linv, U, nmaps, d.n);
+  launch_colnorm2(U, d.n, d.n, nmaps, o_chi, c.st);
+  if (o_lnl) launch_loglike_finish(o_chi, o_ld, nmaps, o_lnl, c.st);
+  return c.finish();
+}
+
+qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t precision,
+                     void *stream) {
+  if (n <= 0 || !A || lda < n) return fail(QML_EINVAL, "bad potrf arguments");
+  if (precision != QML_FP64) return fail(QML_EINVAL, "precision: only QML_FP64 in this build");
+  Call c(stream);
+  double *Ad = c.out(A, (size_t)lda * n, "A");
+  if (Ad != A && Ad) {
+    c.cuda_ok(cudaMemcpyAsync(Ad, A, (size_t)lda * n * sizeof(double), cudaMemcpyHostToDevice, c.st),
+              "A");
+  }
+  double *ld = c.out(logdet, 1, "logdet");
+  const int64_t nblocks = (n + kNB - 1) / kNB;
+  double *Linv = c.alloc<double>((size_t)nblocks * kNB * kNB);
+  double *ldparts = c.alloc<double>(nblocks);
+  if (!c.make_status()) return c.finish();
+  potrf_blocked(c, Ad, n, lda, Linv, ldparts, ld);
+  return c.finish();
+}
+
+qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, double *B, int64_t ldb,
+                    int32_t precision, void *stream) {
+  if (n <= 0 || nrhs < 0 || !L || !B || lda < n || ldb < n)
+    return fail(QML_EINVAL, "bad trsm arguments");
+  if (precision != QML_FP64) return fail(QML_EINVAL, "precision: only QML_FP64 in this build");
+  if (nrhs == 0) return QML_OK;
+  Call c(stream);
+  const double *Ld = c.in(L, (size_t)lda * n, "L");
+  double *Bd = c.out(B, (size_t)ldb * nrhs, "B");
+  if (Bd != B && Bd)
+    c.cuda_ok(cudaMemcpyAsync(Bd, B, (size_t)ldb * nrhs * sizeof(double), cudaMemcpyHostToDevice,
+                              c.st), "B");
+  const int64_t nblocks = (n + kNB - 1) / kNB;
+  double *Linv = c.alloc<double>((size_t)nblocks * kNB * kNB);
+  if (!c.make_status()) return c.finish();
+  launch_trtri_blocks(Ld, lda, n, Linv, c.status, c.st);
+  trsm_blocked(c, Ld, n, lda, Linv, Bd, nrhs, ldb);
+  return c.finish();
+}
+
+qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64_t kk,
+                    double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,
+                    void *stream) {
+  if (m < 0 || nn < 0 || kk < 0 || !A || !B || !C) return fail(QML_EINVAL, "bad gemm arguments");
+  if (precision != QML_FP64) return fail(QML_EINVAL, "precision: only QML_FP64 in this build");
+  const int64_t ar = transA ? kk : m, ac = transA ? m : kk;
+  const int64_t br = transB ? nn : kk, bc = transB ? kk : nn;
+  if (lda < (ar > 0 ? ar : 1) || ldb < (br > 0 ? br : 1) || ldc < (m > 0 ? m : 1))
+    return fail(QML_EINVAL, "leading dimension too small");
+  if (lower && m != nn) return fail(QML_EINVAL, "lower needs a square C");
+  if (m == 0 || nn == 0) return QML_OK;
+  Call c(stream);
+  const double *Ad = c.in(A, (size_t)lda * ac, "A");
+  const double *Bd = c.in(B, (size_t)ldb * bc, "B");
+  double *Cd = c.out(C, (size_t)ldc * nn, "C");
+  if (Cd != C && Cd && beta != 0.0)
+    c.cuda_ok(cudaMemcpyAsync(Cd, C, (size_t)ldc * nn * sizeof(double), cudaMemcpyHostToDevice, c.st),
+              "C");
+  if (!c.make_status()) return c.finish();
+  launch_dgemm(transA, transB, m, nn, kk, alpha, Ad, lda, Bd, ldb, beta, Cd, ldc, lower, c.status,
+               c.st);
+  return c.finish();
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations shared by the kernel translation units of libqmlgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qmlgb {
+
+// Device status word written by kernels (first int: qml_status code,
+// second: detail such as the failing Cholesky column + 1).
+struct DevStatus {
+  int code;
+  int info;
+  unsigned bar_count;   // grid barrier arrival counter
+  unsigned bar_gen;     // grid barrier generation
+};
+
+// Count of kernel launches made by this library (reported by qml_launch_count).
+void count_launch(int n = 1);
+
+// Iteration budget of every device-side spin wait (~1 s with 64 ns sleeps).
+constexpr long long kSpinLimit = 1LL << 24;
+
+// ---------------------------------------------------------------- ybuild --
+struct YArgs {
+  int has_T, has_P;
+  int npix_T, npix_P;
+  const double *theta_T, *phi_T, *theta_P, *phi_P;
+  int lmin, lmax;
+  const double *transfer_T, *transfer_P;
+};
+void launch_ybuild(const YArgs &a, double *Y, int64_t ldy, cudaStream_t st);
+
+// Mix the columns of Y inside every (l, m) by the lower Cholesky factor of the
+// 3x3 spectrum block: G = Y L_Lambda, so that G G^T = Y Lambda Y^T.
+// lamL holds per l the nc x nc lower factor (row-major, nc*nc doubles).
+void launch_lambda_factor(const double *cl, int lmin, int lmax, int nc, const int *comps,
+                          double *lamL, cudaStream_t st);
+void launch_mix_lambda(double *Y, int64_t ldy, int n, int nc, int k0, int lmin, int lmax,
+                       const double *lamL, cudaStream_t st);
+
+// ----------------------------------------------------------------- dense --
+// C <- alpha op(A) op(B) + beta C (float64 CUDA-core tiles); see qml_gemm.
+void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                  const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                  double *C, int64_t ldc, int lower, const DevStatus *status, cudaStream_t st);
+
+constexpr int kNB = 64;  // Cholesky / TRSM block size
+
+// Factor the diagonal block of the n x n matrix A (lda) that starts at row and
+// column j0 (size min(kNB, n - j0); A points at the matrix origin plus
+// j0 + j0 lda), lower in place; write its inverse into Linv (ld kNB) and
+// 2 sum ln L_ii into *logdet_part.
+void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,
+                       double *logdet_part, DevStatus *status, cudaStream_t st);
+// Inverses of every kNB diagonal block of an existing lower factor L
+// (block b at Linv + b kNB^2, ld kNB), one CTA per block.
+void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,
+                         DevStatus *status, cudaStream_t st);
+void launch_sum_logdet(const double *parts, int nparts, double *out, cudaStream_t st);
+void launch_copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t n,
+                       cudaStream_t st);
+void launch_symmetrize_lower(double *A, int64_t lda, int64_t n, cudaStream_t st);
+void launch_copy_matrix(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t rows,
+                        int64_t cols, cudaStream_t st);
+void launch_add_matrix(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t rows,
+                       int64_t cols, cudaStream_t st);
+void launch_colnorm2(const double *X, int64_t ldx, int64_t rows, int64_t cols, double *out,
+                     cudaStream_t st);
+void launch_loglike_finish(const double *chi2, const double *logdet, int nmaps, double *lnL,
+                           cudaStream_t st);
+
+// ---------------------------------------------------------------- fisher --
+// Block sums of W (k x k symmetric, full) over all (l >= l') pairs.
+// parts: per (l,l') pair nc^4 sums of W[v i,u' j] W[u i,v' j]; diag: per l
+// nc^2 sums of W[v i, u i].
+void launch_fisher_blocksum(const double *W, int64_t ldw, int nc, int k0, int lmin, int lmax,
+                            double *parts, double *diag, cudaStream_t st);
+// Assemble F_full (na_full x na_full), t_full (na_full) from the parts.
+// spec_full: canonical spectra for the fields present (component indices).
+void launch_fisher_assemble(const double *parts, const double *diag, int nc, int nl,
+                            int nspec_full, const int *spec_uv /* 4 ints per spectrum */,
+                            double *F_full, double *t_full, cudaStream_t st);
+// b = t/2 - F_full c_fid restricted; F = F_full restricted.
+void launch_fisher_select(const double *F_full, const double *t_full, const double *cl_fid,
+                          int lmin, int lmax, int nspec_full, const int *full_spec_ids,
+                          int nspec, const int *sel /* positions into full */, double *F,
+                          double *b, cudaStream_t st);
+// y_a = 1/2 w^T E_a w for every column of w (k x nsims).
+void launch_quad_y(const double *w, int64_t ldw, int nsims, int nc, int k0, int lmin, int lmax,
+                   int nspec, const int *spec_uv, double *y, cudaStream_t st);
+// q = y - b (columns), nsims columns of na.
+void launch_sub_bias(const double *y, const double *b, int na, int nsims, double *q,
+                     cudaStream_t st);
+
+// ------------------------------------------------------------------- eig --
+// Symmetric eigendecomposition of F (na x na) by parallel cyclic Jacobi
+// (cooperative grid, bounded barriers).  Outputs Finv = F^-1 and
+// Fm12 = F^-1/2 (eigenvalues < cut * max dropped), both na x na, and
+// eig_minmax[2].
+cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, double *Fm12,
+                           double *eig_minmax, DevStatus *status, cudaStream_t st);
+size_t fisher_eig_work_doubles(int na);
+
+}  // namespace qmlgb

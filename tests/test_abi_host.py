@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every
+function include/qmlgb.h declares, and rejects bad arguments before touching
+the GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_21149_gb300 import _native as nat
+from paper_2605_21149_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return nat.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = header_functions()
+    assert {"qml_fisher", "qml_estimate", "pix_loglike", "qml_ybuild"} <= decl
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert decl == set(nat.SIGNATURES), decl ^ set(nat.SIGNATURES)
+
+
+def test_version_and_error_string(lib):
+    assert lib.qml_version() >= 100
+    assert isinstance(lib.qml_last_error(), bytes)
+
+
+def _problem(**kw):
+    p = nat.QmlProblem()
+    p.has_T, p.has_P = 1, 0
+    p.npix_T = 10
+    buf = (ctypes.c_double * 64)()
+    ptr = ctypes.cast(buf, ctypes.c_void_p)
+    p.theta_T = p.phi_T = p.transfer_T = ptr
+    p.lmin, p.lmax = 2, 5
+    p.nspec = 1
+    p.spec[0] = 0
+    p.cl_fid = ptr
+    p.N = ptr
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p, buf
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("lmin", 1, "lmin"),
+    ("lmax", 1, "lmax"),
+    ("nspec", 0, "nspec"),
+    ("has_T", 0, "no field"),
+    ("npix_T", 0, "npix_T"),
+    ("precision", 7, "precision"),
+])
+def test_argument_validation(lib, field, value, needle):
+    p, keep = _problem(**{field: value})
+    F = (ctypes.c_double * 16)()
+    st = lib.qml_fisher(ctypes.byref(p), ctypes.cast(F, ctypes.c_void_p), None, None)
+    assert st == nat.QML_EINVAL
+    assert needle in lib.qml_last_error().decode()
+
+
+def test_spectrum_needs_its_field(lib):
+    p, keep = _problem()
+    p.spec[0] = 1  # EE without a polarisation field
+    F = (ctypes.c_double * 16)()
+    assert lib.qml_fisher(ctypes.byref(p), ctypes.cast(F, ctypes.c_void_p), None, None) == nat.QML_EINVAL
+    assert "absent" in lib.qml_last_error().decode()
+
+
+def test_null_problem(lib):
+    assert lib.qml_ybuild(None, None, 0, None) == nat.QML_EINVAL
+    assert lib.qml_estimate(None, None, 0, None, None, None, None, None, None) == nat.QML_EINVAL
+    assert lib.qml_potrf(0, None, 0, None, 0, None) == nat.QML_EINVAL
