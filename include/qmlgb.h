@@ -166,6 +166,20 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
                     double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,
                     void *stream);
 
+/* qml_potrf without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory (code running
+ * inside a host runtime that owns all GPU memory and hands its callees
+ * pre-allocated buffers, or hot loops that cannot afford the device
+ * synchronisation of cudaMalloc / cudaFree).  Same kernels and result as
+ * qml_potrf with precision QML_FP64; A (n x n, lda) and logdet (may be NULL)
+ * must be DEVICE pointers.  Its scratch is a static device array sized for
+ * n <= 4096 (2.1 MB held on every GPU that loads the library until exit);
+ * larger n returns QML_EINVAL.  All calls share that array, so calls that
+ * overlap on the GPU race and must be serialised by the caller.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and should come before any stream capture. */
+qml_status qml_potrf_noalloc(int64_t n, double *A, int64_t lda, double *logdet, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,7 @@ SIGNATURES = {
     "pix_loglike": (c_int32, [ctypes.POINTER(QmlProblem), c_void_p, c_void_p, c_int32, c_void_p,
                               c_void_p, c_void_p, c_void_p]),
     "qml_potrf": (c_int32, [c_int64, c_void_p, c_int64, c_void_p, c_int32, c_void_p]),
+    "qml_potrf_noalloc": (c_int32, [c_int64, c_void_p, c_int64, c_void_p, c_void_p]),
     "qml_trsm": (c_int32, [c_int64, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_int32,
                            c_void_p]),
     "qml_gemm": (c_int32, [c_int32, c_int32, c_int64, c_int64, c_int64, c_double, c_void_p,

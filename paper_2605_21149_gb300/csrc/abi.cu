@@ -22,8 +22,14 @@ std::atomic<long long> g_launches{0};
 void qmlgb::count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace qmlgb {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace qmlgb
+
+namespace {
 
 qml_status fail(qml_status s, const std::string &msg) {
   g_err = msg;

@@ -1,0 +1,67 @@
+"""qml_potrf_noalloc against qml_potrf, through the C ABI.
+
+qml_potrf_noalloc serves callers that cannot allocate device memory (a host
+runtime that owns all GPU memory and only hands out pre-allocated buffers, or
+hot loops that cannot pay for cudaMalloc's device synchronisation); it keeps
+its scratch in a static device array shared by every call.  Two calls in a
+row (different sizes, so the second runs on the first one's leftover scratch)
+must reproduce qml_potrf on the same matrices.  This file is collected last
+so that a run stopping at the first failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_21149_gb300 import _native, build
+    build.build()
+    return _native.load()
+
+
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    G = rng.normal(size=(n, n))
+    return G @ G.T / n + np.eye(n)
+
+
+def _colmajor_dev(A):
+    return torch.as_tensor(A, dtype=torch.float64, device="cuda").t().contiguous().t()
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("sizes", [(1000, 257), (4096, 65)])
+def test_noalloc_matches_potrf_two_calls(lib, sizes):
+    for i, n in enumerate(sizes):
+        A = _spd(n, 100 + n)
+        ref = _colmajor_dev(A)
+        ld_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = lib.qml_potrf(n, ref.data_ptr(), n, ld_ref.data_ptr(), 0, _stream())
+        assert st == 0, lib.qml_last_error()
+        out = _colmajor_dev(A)
+        ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = lib.qml_potrf_noalloc(n, out.data_ptr(), n, ld.data_ptr(), _stream())
+        assert st == 0, lib.qml_last_error()
+        L, Lr = torch.tril(out).cpu().numpy(), torch.tril(ref).cpu().numpy()
+        assert np.abs(L - Lr).max() <= 1e-12 * np.abs(Lr).max(), (i, n)
+        assert abs(ld.item() - ld_ref.item()) <= 1e-12 * abs(ld_ref.item())
+
+
+def test_noalloc_rejects_oversize_and_host(lib):
+    n = 4097
+    A = torch.eye(8, dtype=torch.float64, device="cuda")
+    st = lib.qml_potrf_noalloc(n, A.data_ptr(), n, None, _stream())
+    assert st == 1 and b"4096" in lib.qml_last_error()
+    h = np.eye(4)
+    st = lib.qml_potrf_noalloc(4, h.ctypes.data, 4, None, _stream())
+    assert st == 1 and b"device pointers" in lib.qml_last_error()
