@@ -565,7 +565,8 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
                     double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,
                     void *stream) {
   if (m < 0 || nn < 0 || kk < 0 || !A || !B || !C) return fail(QML_EINVAL, "bad gemm arguments");
-  if (precision != QML_FP64) return fail(QML_EINVAL, "precision: only QML_FP64 in this build");
+  if (precision != QML_FP64 && precision != QML_SPLIT_BF16)
+    return fail(QML_EINVAL, "precision must be QML_FP64 or QML_SPLIT_BF16");
   const int64_t ar = transA ? kk : m, ac = transA ? m : kk;
   const int64_t br = transB ? nn : kk, bc = transB ? kk : nn;
   if (lda < (ar > 0 ? ar : 1) || ldb < (br > 0 ? br : 1) || ldc < (m > 0 ? m : 1))
@@ -580,6 +581,15 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
     c.cuda_ok(cudaMemcpyAsync(Cd, C, (size_t)ldc * nn * sizeof(double), cudaMemcpyHostToDevice, c.st),
               "C");
   if (!c.make_status()) return c.finish();
+  if (precision == QML_SPLIT_BF16) {
+    const bool shared = (A == B && lda == ldb && transA != transB && m == nn);
+    void *ws = c.alloc<unsigned char>(ozaki_workspace_bytes(m, nn, kk, 0, shared), "split workspace");
+    if (!ws) return c.finish();
+    c.cuda_ok(ozaki_gemm(transA, transB, m, nn, kk, alpha, Ad, lda, Bd, ldb, beta, Cd, ldc, lower,
+                         0, ws, c.status, c.st),
+              "split-precision gemm");
+    return c.finish();
+  }
   launch_dgemm(transA, transB, m, nn, kk, alpha, Ad, lda, Bd, ldb, beta, Cd, ldc, lower, c.status,
                c.st);
   return c.finish();

@@ -140,20 +140,22 @@ __device__ __forceinline__ double inv_at(double (*a)[kNB + 1], const double *inv
   return k == c ? invd[c] : a[c][k];
 }
 
+// (float64 division is expensive on this part: one reciprocal per diagonal
+// entry, reused by every product)
 __device__ void invert_lower_shared(double (*a)[kNB + 1], double *invd, int jb) {
   const int tid = threadIdx.x;
   const int col = tid >> 2, part = tid & 3;
   if (col < jb && part == 0) invd[col] = 1.0 / a[col][col];
+  __syncthreads();
   for (int i = 1; i < jb; ++i) {
-    __syncthreads();
     double s = 0.0;
     if (col < i)
       for (int k = col + part; k < i; k += 4) s = fma(a[i][k], inv_at(a, invd, k, col), s);
     s += __shfl_down_sync(0xffffffffu, s, 2, 4);
     s += __shfl_down_sync(0xffffffffu, s, 1, 4);
-    if (col < i && part == 0) a[col][i] = -s / a[i][i];
+    if (col < i && part == 0) a[col][i] = -s * invd[i];
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // One CTA factors a jb x jb (jb <= 64) diagonal block in shared memory:
@@ -166,6 +168,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
                                                          DevStatus *status, int factor) {
   __shared__ double a[kNB][kNB + 1];
   __shared__ double invd[kNB];
+  __shared__ double rpiv;
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (status && *((volatile int *)&status->code) != 0) return;
@@ -190,18 +193,23 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
           status->info = (int)(j0 + c + 1);
           atomicExch(&status->code, 2 /* QML_ENOTSPD */);
         } else {
-          a[c][c] = sqrt(piv);
+          const double d = sqrt(piv);
+          a[c][c] = d;
+          rpiv = 1.0 / d;
         }
       }
       __syncthreads();
       if (bad) return;
-      const double r = 1.0 / a[c][c];
+      const double r = rpiv;
       for (int i = c + 1 + tid; i < jb; i += blockDim.x) a[i][c] *= r;
       __syncthreads();
-      const int m = jb - c - 1;  // trailing size
-      for (int t = tid; t < m * m; t += blockDim.x) {
-        int i = c + 1 + t % m, j = c + 1 + t / m;
-        if (i >= j) a[i][j] = fma(-a[i][c], a[j][c], a[i][j]);
+      // trailing rank-1 update: row i = c+1+(tid % 64), columns strided by 4
+      {
+        const int i = c + 1 + (tid & 63);
+        if (i < jb) {
+          const double aic = a[i][c];
+          for (int j = c + 1 + (tid >> 6); j <= i; j += 4) a[i][j] = fma(-aic, a[j][c], a[i][j]);
+        }
       }
       __syncthreads();
     }
@@ -209,11 +217,15 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
       int i = t % jb, j = t / jb;
       if (i >= j) A[i + j * lda] = a[i][j];
     }
+    // logs in parallel, summed in a fixed order
+    if (tid < jb) invd[tid] = log(a[tid][tid]);
+    __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int c = 0; c < jb; ++c) s += log(a[c][c]);
+      for (int c = 0; c < jb; ++c) s += invd[c];
       *logdet_part = 2.0 * s;
     }
+    __syncthreads();
   }
   invert_lower_shared(a, invd, jb);
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {

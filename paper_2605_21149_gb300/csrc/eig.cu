@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *A0, double *A1, dou
   const int64_t nblk = (int64_t)h * (h + 1) / 2;
   const int64_t nvt = (int64_t)n * h;
   double *Aold = A0, *Anew = A1;
+  double prev_off = 0.0;
   __shared__ double sred[2][8];
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test on the current matrix
@@ -117,7 +118,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *A0, double *A1, dou
       to += ((volatile double *)red)[2 * b];
       td += ((volatile double *)red)[2 * b + 1];
     }
+    // converged, or stalled at the float64 rounding floor (quadratic
+    // convergence ends there; every block takes the same decision)
     if (to <= 1e-32 * td) break;
+    if (sweep > 0 && to > 0.25 * prev_off && to <= 1e-20 * td) break;
+    prev_off = to;
     if (!grid_barrier(st, nblocks)) return;
 
     for (int r = 0; r < n - 1; ++r) {

@@ -102,4 +102,15 @@ cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, 
                            double *eig_minmax, DevStatus *status, cudaStream_t st);
 size_t fisher_eig_work_doubles(int na);
 
+// ---------------------------------------------------------------- ozaki --
+// Split-precision float64 GEMM (bf16 digits on tcgen05, exact FP32 chunks,
+// float64 recombination); same operand conventions as launch_dgemm.  `work`
+// must hold ozaki_workspace_bytes(...) bytes.  nslices = 0 picks the default.
+void ozaki_choose(int64_t K, int nslices, int &S, int &beta);
+size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K, int nslices, bool shared_operand);
+cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                       const double *A, int64_t lda, const double *B, int64_t ldb, double beta_c,
+                       double *C, int64_t ldc, int lower, int nslices, void *work,
+                       DevStatus *status, cudaStream_t st);
+
 }  // namespace qmlgb

@@ -1,0 +1,628 @@
+// Split-precision float64 GEMM on tcgen05 tensor cores (Ozaki-style).
+//
+//   C <- alpha op(A) op(B) + beta C,  op(A) m x K, op(B) K x n, float64 in/out.
+//
+// Each row i of op(A) is scaled by 2^-e_i (|x| <= 2^e_i) and written as S
+// signed digits of beta bits: x 2^-e_i = sum_s a_s 2^(-beta s) with |a_1| <=
+// 2^beta, |a_s| <= 2^(beta-1) (s >= 2), every digit an integer that bf16 holds
+// exactly; the same for the columns of op(B) with exponents f_j.  Then
+//   C_ij = 2^(e_i+f_j) sum_{s+t <= S+1} 2^(-beta(s+t)) (A_s B_t^T)_ij
+// (products below the truncation level are dropped).  Every digit product
+// A_s B_t^T is an integer matrix; over a K-chunk of 2^(24 - 2 beta) its
+// entries stay below 2^24, so the FP32 tensor-core accumulation in TMEM is
+// exact whatever the accumulation order or rounding mode.  Each exact chunk is
+// converted to int32 and added into a per-level integer accumulator (TMEM);
+// when a level s+t = L is complete it is folded into float64 totals (TMEM) with
+// the weight 2^(-beta L).  float64 work is therefore S folds per output, not
+// one per product.
+//
+// Kernel layout: one CTA per 128 x 128 output tile, 192 threads.
+//   warp 0   TMA producer (one lane): bf16 digit tiles 128 x 64 of op(A) and
+//            op(B), 128-byte swizzle, 4-stage ring guarded by mbarriers;
+//   warp 1   TMEM allocator and MMA issuer (one lane): tcgen05.mma kind::f16
+//            M=128 N=128 K=16, FP32 accumulator in TMEM columns [0,128);
+//   warps 2-5 epilogue: TMEM lanes = tile rows; int32 level sums in columns
+//            [128,256), float64 totals in [256,512).
+// Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the CTA records
+// QML_ETIMEOUT, drains what it issued, frees TMEM and returns.
+#include "internal.cuh"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+namespace qmlgb {
+
+namespace {
+
+constexpr int OBM = 128, OBN = 128, OBK = 64, OSTAGES = 4;
+constexpr int kTileBytes = OBM * OBK * 2;  // 16 KB per operand tile
+constexpr int kThreads = 192;
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s budget per wait
+
+// bounded wait; false (and the status word set) when the time budget runs out
+// or another role already failed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevStatus *st) {
+  const uint64_t t0 = global_ns();
+  for (unsigned i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*((volatile int *)&st->code) != 0) return false;
+      if (global_ns() - t0 > kWaitNs) break;
+    }
+  }
+  atomicCAS(&st->code, 0, 5 /* QML_ETIMEOUT */);
+  return false;
+}
+// bounded wait used while draining after a failure (no status update)
+__device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitNs) return;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t holder_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+#define TMEM_REGS32(r)                                                                           \
+  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),            \
+      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),    \
+      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),              \
+      "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),              \
+      "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+#define TMEM_IN32(r)                                                                             \
+  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),       \
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),          \
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),        \
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),        \
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : TMEM_REGS32(r)
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+      "%29, %30, %31, %32};" ::"r"(taddr),
+      TMEM_IN32(r)
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// K-major, 128-byte-swizzled bf16 tile (rows of 64 elements = 128 B, 8-row
+// atoms of 1024 B): start address, LBO 16 B (unused for this layout), SBO
+// 1024 B, descriptor version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, N, M
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
+                            ((uint32_t)(OBM >> 4) << 24);
+
+struct OzParams {
+  int64_t M, N;            // logical output size
+  int Mpad, Npad, nk;      // padded rows of the digit arrays; K stages of 64
+  int S, beta, chunk;      // digits, bits per digit, stages per exact chunk
+  int tiles_n, lower;
+  double alpha, betac;
+  double *C;
+  int64_t ldc;
+  const int *ea, *eb;
+  DevStatus *status;
+};
+
+__device__ __forceinline__ void tile_of(const OzParams &p, int bid, int &tm, int &tn) {
+  if (!p.lower) {
+    tm = bid / p.tiles_n;
+    tn = bid % p.tiles_n;
+    return;
+  }
+  // lower-triangle tiles (tm >= tn), row by row
+  int r = (int)((sqrt(8.0 * bid + 1.0) - 1.0) * 0.5);
+  while ((r + 1) * (r + 2) / 2 <= bid) ++r;
+  while (r * (r + 1) / 2 > bid) --r;
+  tm = r;
+  tn = bid - r * (r + 1) / 2;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                      const __grid_constant__ CUtensorMap tmB, OzParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *tilesA = smem;
+  unsigned char *tilesB = smem + OSTAGES * kTileBytes;
+  uint64_t *bars = (uint64_t *)(smem + 2 * OSTAGES * kTileBytes);
+  // bars[0..S) full, [S..2S) empty, 2S acc_full, 2S+1 acc_empty, 2S+2 drain
+  uint32_t *tmem_holder = (uint32_t *)(bars + 2 * OSTAGES + 3);
+  int *s_eb = (int *)(tmem_holder + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tm, tn;
+  tile_of(p, blockIdx.x, tm, tn);
+  const int m0 = tm * OBM, n0 = tn * OBN;
+  DevStatus *st = p.status;
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OSTAGES]);
+  const uint32_t accf = smem_u32(&bars[2 * OSTAGES]), acce = smem_u32(&bars[2 * OSTAGES + 1]);
+  const uint32_t drain = smem_u32(&bars[2 * OSTAGES + 2]);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OSTAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 128);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int j = threadIdx.x; j < OBN; j += blockDim.x) s_eb[j] = p.eb[n0 + j];
+  if (warp == 1) tmem_alloc(smem_u32(tmem_holder), 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tmem_holder;
+
+  const int S = p.S;
+  const int nchunks = (p.nk + p.chunk - 1) / p.chunk;
+
+  if (warp == 0) {
+    // ------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int last_phase[OSTAGES];
+      for (int q = 0; q < OSTAGES; ++q) last_phase[q] = -1;
+      bool ok = (*((volatile int *)&st->code) == 0);
+      for (int L = 2; L <= S + 1 && ok; ++L) {
+        for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
+          const int t = L - s;
+          for (int ks = 0; ks < p.nk && ok; ++ks) {
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st)) { ok = false; break; }
+            mbar_expect_tx(full0 + 8 * stage, 2 * kTileBytes);
+            tma_load_2d(smem_u32(tilesA + stage * kTileBytes), &tmA, full0 + 8 * stage, ks * OBK,
+                        (s - 1) * p.Mpad + m0);
+            tma_load_2d(smem_u32(tilesB + stage * kTileBytes), &tmB, full0 + 8 * stage, ks * OBK,
+                        (t - 1) * p.Npad + n0);
+            last_phase[stage] = (int)phase;
+            if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
+          }
+        }
+      }
+      if (!ok) {
+        // drain: wait (bounded) until the last load issued into each slot has
+        // landed, so no copy is still writing shared memory when the CTA exits
+        for (int q = 0; q < OSTAGES; ++q) {
+          if (last_phase[q] < 0) continue;
+          mbar_drain_wait(full0 + 8 * q, (uint32_t)last_phase[q]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // -------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t nflush = 0;  // accumulator hand-offs so far
+      bool ok = (*((volatile int *)&st->code) == 0);
+      for (int L = 2; L <= S + 1 && ok; ++L) {
+        for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
+          for (int c = 0; c < nchunks && ok; ++c) {
+            // the epilogue must have read the previous chunk
+            if (nflush > 0 && !mbar_wait(acce, (nflush - 1) & 1, st)) { ok = false; break; }
+            tc_fence_after();
+            const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
+            for (int ks = k0; ks < k1; ++ks) {
+              if (!mbar_wait(full0 + 8 * stage, phase, st)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(tilesA + stage * kTileBytes);
+              const uint32_t b_addr = smem_u32(tilesB + stage * kTileBytes);
+#pragma unroll
+              for (int kk = 0; kk < OBK / 16; ++kk) {
+                mma_bf16(tbase, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk), kIdesc,
+                         (ks > k0 || kk > 0) ? 1u : 0u);
+              }
+              mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
+              if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
+            }
+            if (!ok) break;
+            mma_commit(accf);  // chunk result ready for the epilogue
+            ++nflush;
+          }
+        }
+      }
+      // wait for every MMA this thread issued before TMEM is released
+      mma_commit(drain);
+      mbar_drain_wait(drain, 0);
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int quad = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = quad * 32 + lane;
+    const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16);
+    const uint32_t c_acc = lane_base, c_lvl = lane_base + 128, c_tot = lane_base + 256;
+    uint32_t nflush = 0;
+    bool ok = true;
+    for (int L = 2; L <= S + 1 && ok; ++L) {
+      bool first_in_level = true;
+      for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
+        for (int c = 0; c < nchunks; ++c) {
+          int okw = 1;
+          if (lane == 0) okw = mbar_wait(accf, nflush & 1, st) ? 1 : 0;
+          okw = __shfl_sync(0xffffffffu, okw, 0);
+          __syncwarp();
+          if (!okw) { ok = false; break; }
+          tc_fence_after();
+#pragma unroll 1
+          for (int cb = 0; cb < OBN / 32; ++cb) {
+            uint32_t a[32], v[32];
+            tmem_ld32(c_acc + 32 * cb, a);
+            if (first_in_level) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] = (uint32_t)__float2int_rn(__uint_as_float(a[j]));
+            } else {
+              tmem_ld32(c_lvl + 32 * cb, v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                v[j] = (uint32_t)((int)v[j] + __float2int_rn(__uint_as_float(a[j])));
+            }
+            tmem_st32(c_lvl + 32 * cb, v);
+          }
+          first_in_level = false;
+          tc_fence_before();
+          mbar_arrive(acce);
+          ++nflush;
+        }
+      }
+      if (!ok) break;
+      // fold level L into the float64 totals: tot += 2^(-beta L) lvl
+      const double w = ldexp(1.0, -p.beta * L);
+#pragma unroll 1
+      for (int cb = 0; cb < OBN / 32; ++cb) {
+        uint32_t v[32], t0[32], t1[32];
+        tmem_ld32(c_lvl + 32 * cb, v);
+        if (L > 2) {
+          tmem_ld32(c_tot + 64 * cb, t0);
+          tmem_ld32(c_tot + 64 * cb + 32, t1);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          double prev = 0.0;
+          if (L > 2) {
+            const int jj = 2 * j;
+            const uint32_t lo = jj < 32 ? t0[jj] : t1[jj - 32];
+            const uint32_t hi = jj + 1 < 32 ? t0[jj + 1] : t1[jj + 1 - 32];
+            prev = __hiloint2double((int)hi, (int)lo);
+          }
+          const double nv = fma((double)(int)v[j], w, prev);
+          const int jj = 2 * j;
+          if (jj < 32) {
+            t0[jj] = (uint32_t)__double2loint(nv);
+            t0[jj + 1] = (uint32_t)__double2hiint(nv);
+          } else {
+            t1[jj - 32] = (uint32_t)__double2loint(nv);
+            t1[jj - 31] = (uint32_t)__double2hiint(nv);
+          }
+        }
+        tmem_st32(c_tot + 64 * cb, t0);
+        tmem_st32(c_tot + 64 * cb + 32, t1);
+      }
+    }
+    if (ok) {
+      // output: alpha 2^(e_i + f_j) tot + beta C
+      const int64_t gi = m0 + row;
+      const int ei = (gi < p.M) ? p.ea[gi] : 0;
+#pragma unroll 1
+      for (int cb = 0; cb < OBN / 32; ++cb) {
+        uint32_t t0[32], t1[32];
+        tmem_ld32(c_tot + 64 * cb, t0);
+        tmem_ld32(c_tot + 64 * cb + 32, t1);
+        if (gi >= p.M) continue;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+          const int64_t gj = n0 + 32 * cb + j;
+          if (gj >= p.N || (p.lower && gi < gj)) continue;
+          const int jj = 2 * j;
+          const uint32_t lo = jj < 32 ? t0[jj] : t1[jj - 32];
+          const uint32_t hi = jj + 1 < 32 ? t0[jj + 1] : t1[jj + 1 - 32];
+          double v = p.alpha * ldexp(__hiloint2double((int)hi, (int)lo), ei + s_eb[32 * cb + j]);
+          double *cp = p.C + gi + gj * p.ldc;
+          if (p.betac != 0.0) v = fma(p.betac, *cp, v);
+          *cp = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tbase, 512);
+}
+
+// ------------------------------------------------------------- digits ----
+// exponent e with max |x| <= 2^e over one logical row (frexp convention)
+__global__ void row_exponent_kernel(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+                                    int *e, int Rpad) {
+  // one warp per row; lanes stride over k
+  const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= Rpad) return;
+  double mx = 0.0;
+  if (r < R)
+    for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[r * sr + k * sk]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    int ex = 0;
+    if (mx > 0.0) frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1): mx < 2^ex
+    e[r] = ex;
+  }
+}
+
+// digits of one logical matrix X (R x K, element (r,k) at X[r sr + k sk]) into
+// D[s][r][k] (bf16, rows Rpad, K-contiguous rows of Kpad): F = round(x 2^(beta S
+// - e_r)) as an integer, then signed digits from the bottom, each in
+// [-2^(beta-1), 2^(beta-1)), the top one in [-2^beta, 2^beta].  Tile 32 x 64 via
+// shared memory so both the read and the K-contiguous write coalesce.
+__global__ void slice_kernel(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+                             const int *e, int S, int beta, __nv_bfloat16 *D, int Rpad, int Kpad) {
+  __shared__ double tile[32][65];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
+  const int tid = threadIdx.x;  // 256 threads
+  if (sk == 1) {
+    // k contiguous: 64 consecutive k per row
+    for (int t = tid; t < 32 * 64; t += 256) {
+      int rr = t / 64, kk = t % 64;
+      int64_t r = r0 + rr, k = k0 + kk;
+      tile[rr][kk] = (r < R && k < K) ? X[r * sr + k] : 0.0;
+    }
+  } else {
+    // r contiguous: 32 consecutive r per k
+    for (int t = tid; t < 32 * 64; t += 256) {
+      int rr = t % 32, kk = t / 32;
+      int64_t r = r0 + rr, k = k0 + kk;
+      tile[rr][kk] = (r < R && k < K) ? X[r + k * sk] : 0.0;
+    }
+  }
+  __syncthreads();
+  // each thread: one row rr, two adjacent k (kk, kk+1)
+  const int rr = tid / 32, kp = (tid % 32) * 2;
+  for (int rq = rr; rq < 32; rq += 8) {
+    const int64_t r = r0 + rq;
+    if (r >= Rpad) continue;
+    const int er = (r < R) ? e[r] : 0;
+    long long F[2];
+    for (int h = 0; h < 2; ++h) F[h] = __double2ll_rn(ldexp(tile[rq][kp + h], beta * S - er));
+    const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
+    for (int s = S; s >= 1; --s) {
+      float d[2];
+      for (int h = 0; h < 2; ++h) {
+        long long dig;
+        if (s > 1) {
+          dig = ((F[h] + half) & mask) - half;
+          F[h] = (F[h] - dig) >> beta;
+        } else {
+          dig = F[h];
+        }
+        d[h] = (float)dig;
+      }
+      __nv_bfloat162 v = __floats2bfloat162_rn(d[0], d[1]);
+      *(__nv_bfloat162 *)(D + ((int64_t)(s - 1) * Rpad + r) * Kpad + k0 + kp) = v;
+    }
+  }
+}
+
+// ------------------------------------------------------- tensor maps -----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap *map, void *base, int64_t rows, int64_t kpad) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {OBK, OBM};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+void ozaki_choose(int64_t K, int nslices, int &S, int &beta) {
+  // beta: digit bits (exact chunk 2^(24 - 2 beta) elements); S digits cover
+  // about 48 bits unless the caller asks for another count
+  beta = 6;
+  (void)K;
+  S = nslices > 0 ? nslices : 8;
+  if (S * beta > 62) S = 62 / beta;
+}
+
+size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K, int nslices, bool shared_operand) {
+  int S, beta;
+  ozaki_choose(K, nslices, S, beta);
+  const int64_t Mpad = rup(M, OBM), Npad = rup(N, OBN), Kpad = rup(K, OBK);
+  size_t b = rup((size_t)S * Mpad * Kpad * 2, 1024) + rup(4 * (size_t)Mpad, 1024);
+  if (!shared_operand) b += rup((size_t)S * Npad * Kpad * 2, 1024) + rup(4 * (size_t)Npad, 1024);
+  return b;
+}
+
+cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                       const double *A, int64_t lda, const double *B, int64_t ldb, double beta_c,
+                       double *C, int64_t ldc, int lower, int nslices, void *work,
+                       DevStatus *status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  int S, beta;
+  ozaki_choose(K, nslices, S, beta);
+  const int64_t Mpad = rup(M, OBM), Npad = rup(N, OBN), Kpad = rup(K, OBK);
+  // op(A) and op(B)^T are the same logical matrix when A == B and exactly one
+  // of them is transposed (X^T X, G G^T): slice it once
+  const bool shared = (A == B && lda == ldb && ta != tb && M == N);
+  unsigned char *w = (unsigned char *)work;
+  __nv_bfloat16 *DA = (__nv_bfloat16 *)w;
+  w += rup((size_t)S * Mpad * Kpad * 2, 1024);
+  int *ea = (int *)w;
+  w += rup(4 * (size_t)Mpad, 1024);
+  __nv_bfloat16 *DB = DA;
+  int *eb = ea;
+  if (!shared) {
+    DB = (__nv_bfloat16 *)w;
+    w += rup((size_t)S * Npad * Kpad * 2, 1024);
+    eb = (int *)w;
+  }
+  // op(A)[i,k] = A[i + k lda] (ta = 0) or A[k + i lda]
+  const int64_t asr = ta ? lda : 1, ask = ta ? 1 : lda;
+  // op(B) column j, entry k: B[k + j ldb] (tb = 0) or B[j + k ldb]
+  const int64_t bsr = tb ? 1 : ldb, bsk = tb ? ldb : 1;
+  {
+    dim3 g((unsigned)((Mpad + 7) / 8));
+    row_exponent_kernel<<<g, 256, 0, st>>>(A, M, K, asr, ask, ea, (int)Mpad);
+    count_launch();
+    dim3 gs((unsigned)(Kpad / 64), (unsigned)(Mpad / 32));
+    slice_kernel<<<gs, 256, 0, st>>>(A, M, K, asr, ask, ea, S, beta, DA, (int)Mpad, (int)Kpad);
+    count_launch();
+  }
+  if (!shared) {
+    dim3 g((unsigned)((Npad + 7) / 8));
+    row_exponent_kernel<<<g, 256, 0, st>>>(B, N, K, bsr, bsk, eb, (int)Npad);
+    count_launch();
+    dim3 gs((unsigned)(Kpad / 64), (unsigned)(Npad / 32));
+    slice_kernel<<<gs, 256, 0, st>>>(B, N, K, bsr, bsk, eb, S, beta, DB, (int)Npad, (int)Kpad);
+    count_launch();
+  }
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, DA, (int64_t)S * Mpad, Kpad) || !make_map(&mB, DB, (int64_t)S * Npad, Kpad))
+    return cudaErrorInvalidValue;
+  OzParams p;
+  p.M = M;
+  p.N = N;
+  p.Mpad = (int)Mpad;
+  p.Npad = (int)Npad;
+  p.nk = (int)(Kpad / OBK);
+  p.S = S;
+  p.beta = beta;
+  p.chunk = (1 << (24 - 2 * beta)) / OBK;
+  p.tiles_n = (int)(Npad / OBN);
+  p.lower = lower;
+  p.alpha = alpha;
+  p.betac = beta_c;
+  p.C = C;
+  p.ldc = ldc;
+  p.ea = ea;
+  p.eb = eb;
+  p.status = status;
+  const int tiles_m = (int)(Mpad / OBM);
+  int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
+  const size_t smem = 1024 + 2 * OSTAGES * kTileBytes + (2 * OSTAGES + 3) * 8 + 16 + OBN * 4;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  ozaki_gemm_kernel<<<ntiles, kThreads, smem, st>>>(mA, mB, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace qmlgb
