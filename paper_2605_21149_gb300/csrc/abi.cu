@@ -172,8 +172,9 @@ qml_status check_problem(const qml_problem *p, Dims &d, bool need_spec, bool nee
     return fail(QML_EINVAL, "T field needs npix_T > 0, theta_T, phi_T, transfer_T");
   if (p->has_P && (p->npix_P <= 0 || !p->theta_P || !p->phi_P || !p->transfer_P))
     return fail(QML_EINVAL, "P field needs npix_P > 0, theta_P, phi_P, transfer_P");
-  if (p->precision != QML_FP64)
-    return fail(QML_EINVAL, "precision: only QML_FP64 is available in this build");
+  if (p->precision != QML_FP64 && p->precision != QML_SPLIT_BF16)
+    return fail(QML_EINVAL, "precision must be QML_FP64 or QML_SPLIT_BF16");
+  if (p->nslices < 0 || p->nslices > 10) return fail(QML_EINVAL, "nslices must be 0..10");
   d.nT = p->has_T ? p->npix_T : 0;
   d.nP = p->has_P ? p->npix_P : 0;
   d.n = d.nT + 2 * d.nP;
@@ -299,6 +300,101 @@ void build_C(Call &c, const Staged &s, const Dims &d, double *Y, double *C) {
   launch_dgemm(0, 1, d.n, d.n, d.k, 1.0, Y, d.n, Y, d.n, 1.0, C, d.n, 1, c.status, c.st);
 }
 
+// ------------------------------------------------ split-precision drivers --
+// Panels of kNBS columns: the diagonal block is factored in float64 (64-wide
+// blocks), its explicit inverse formed by a float64 solve of the identity, and
+// the panel solve and trailing update run as split-precision products with
+// K = kNBS.
+constexpr int64_t kNBS = 512;
+
+struct Split {
+  Call *c;
+  int nslices;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  double *eye = nullptr;  // kNBS x kNBS scratch for block inverses
+  // make sure the digit workspace holds a product of this shape
+  bool reserve(int64_t M, int64_t N, int64_t K, bool shared) {
+    size_t need = ozaki_workspace_bytes(M, N, K, nslices, shared);
+    if (need <= ws_bytes) return true;
+    ws = c->alloc<unsigned char>(need, "split workspace");
+    ws_bytes = ws ? need : 0;
+    return ws != nullptr;
+  }
+  void gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+            int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+            int lower) {
+    if (c->err != QML_OK || M <= 0 || N <= 0) return;
+    const bool shared = (A == B && lda == ldb && ta != tb && M == N);
+    if (!reserve(M, N, K, shared)) return;
+    c->cuda_ok(ozaki_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, nslices,
+                          ws, c->status, c->st),
+               "split-precision gemm");
+  }
+};
+
+// Cholesky A = L L^T (lower, in place).  Linv64: inverses of the 64-blocks
+// (n/64 blocks of 64x64); LinvB: explicit inverses of the kNBS diagonal blocks
+// (ceil(n/kNBS) blocks of kNBS x kNBS, ld kNBS).
+void potrf_split(Call &c, Split &sp, double *A, int64_t n, int64_t lda, double *Linv64,
+                 double *LinvB, double *ldparts, double *logdet) {
+  for (int64_t j = 0; j < n; j += kNBS) {
+    const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
+    double *Ajj = A + j + j * lda;
+    // float64 blocked factorisation of the diagonal block (64-wide)
+    for (int64_t i = 0; i < jb; i += kNB) {
+      const int64_t ib = (jb - i) < kNB ? (jb - i) : kNB;
+      double *Lb = Linv64 + ((j + i) / kNB) * kNB * kNB;
+      launch_potrf_diag(A + (j + i) + (j + i) * lda, lda, j + jb, j + i, Lb,
+                        ldparts + (j + i) / kNB, c.status, c.st);
+      if (i + ib < jb) {
+        const int64_t m2 = jb - i - ib;
+        double *A21 = Ajj + (i + ib) + i * lda;
+        double *A22 = Ajj + (i + ib) + (i + ib) * lda;
+        launch_dgemm(0, 1, m2, ib, ib, 1.0, A21, lda, Lb, kNB, 0.0, A21, lda, 0, c.status, c.st);
+        launch_dgemm(0, 1, m2, m2, ib, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1, c.status, c.st);
+      }
+    }
+    // explicit inverse of the diagonal block: solve L_jj X = I (float64)
+    double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
+    launch_set_identity(Xinv, kNBS, jb, c.st);
+    trsm_blocked(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, jb, kNBS);
+    if (j + jb < n) {
+      const int64_t m2 = n - j - jb;
+      double *A21 = A + (j + jb) + j * lda;
+      double *A22 = A + (j + jb) + (j + jb) * lda;
+      // panel: A21 <- A21 L_jj^-T ; trailing: A22 <- A22 - A21 A21^T (lower)
+      sp.gemm(0, 1, m2, jb, jb, 1.0, A21, lda, Xinv, kNBS, 0.0, A21, lda, 0);
+      sp.gemm(0, 1, m2, m2, jb, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1);
+    }
+  }
+  if (logdet) launch_sum_logdet(ldparts, (int)((n + kNB - 1) / kNB), logdet, c.st);
+}
+
+// B <- L^-1 B with the explicit kNBS block inverses (split products).
+void trsm_split(Call &c, Split &sp, const double *L, int64_t n, int64_t lda, const double *LinvB,
+                double *B, int64_t nrhs, int64_t ldb) {
+  for (int64_t j = 0; j < n; j += kNBS) {
+    const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
+    const double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
+    sp.gemm(0, 0, jb, nrhs, jb, 1.0, Xinv, kNBS, B + j, ldb, 0.0, B + j, ldb, 0);
+    if (j + jb < n)
+      sp.gemm(0, 0, n - j - jb, nrhs, jb, -1.0, L + (j + jb) + j * lda, lda, B + j, ldb, 1.0,
+              B + j + jb, ldb, 0);
+  }
+}
+
+// C = Y Lambda Y^T + N with the split product for G G^T.
+void build_C_split(Call &c, Split &sp, const Staged &s, const Dims &d, double *Y, double *C) {
+  double *lamL = c.alloc<double>((size_t)d.nl * d.nc * d.nc, "lambda factors");
+  if (!lamL) return;
+  launch_ybuild(s.y, Y, d.n, c.st);
+  launch_lambda_factor(s.cl, d.lmin, d.lmax, d.nc, d.comps, lamL, c.st);
+  launch_mix_lambda(Y, d.n, d.n, d.nc, d.k0, d.lmin, d.lmax, lamL, c.st);
+  launch_copy_lower(s.N, d.n, C, d.n, d.n, c.st);
+  sp.gemm(0, 1, d.n, d.n, d.k, 1.0, Y, d.n, Y, d.n, 1.0, C, d.n, 1);
+}
+
 }  // namespace
 
 // ======================================================================
@@ -310,6 +406,9 @@ struct qml_plan {
   cudaStream_t st = nullptr;
   std::vector<void *> mem;
   double *L = nullptr, *Linv = nullptr, *X = nullptr;
+  double *LinvB = nullptr;  // kNBS-block inverses (split precision)
+  bool split = false;
+  int nslices = 0;
   double *F = nullptr, *b = nullptr, *Finv = nullptr, *Fm12 = nullptr;
   int *uv = nullptr;
 };
@@ -393,8 +492,11 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
     return (double *)p;
   };
   const int64_t nblocks = (d.n + kNB - 1) / kNB;
+  plan->split = (prob->precision == QML_SPLIT_BF16);
+  plan->nslices = prob->nslices;
   plan->L = palloc((size_t)d.n * d.n);
   plan->Linv = palloc((size_t)nblocks * kNB * kNB);
+  if (plan->split) plan->LinvB = palloc((size_t)((d.n + kNBS - 1) / kNBS) * kNBS * kNBS);
   plan->X = palloc((size_t)d.n * d.k);
   plan->F = palloc((size_t)na * na);
   plan->b = palloc(na);
@@ -435,13 +537,23 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
     return e;
   }
 
-  // C = Y Lambda Y^T + N ; L L^T = C
-  build_C(c, sp, d, plan->X, plan->L);
-  potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
-  // X = L^-1 Y ; W = X^T X
-  launch_ybuild(sp.y, plan->X, d.n, c.st);
-  trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
-  launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1, c.status, c.st);
+  if (plan->split) {
+    Split spl{&c, prob->nslices};
+    build_C_split(c, spl, sp, d, plan->X, plan->L);
+    potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr);
+    launch_ybuild(sp.y, plan->X, d.n, c.st);
+    trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, plan->X, d.k, d.n);
+    spl.gemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1);
+  } else {
+    // C = Y Lambda Y^T + N ; L L^T = C
+    build_C(c, sp, d, plan->X, plan->L);
+    potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
+    // X = L^-1 Y ; W = X^T X
+    launch_ybuild(sp.y, plan->X, d.n, c.st);
+    trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
+    launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1, c.status,
+                 c.st);
+  }
   launch_symmetrize_lower(W, d.k, d.k, c.st);
   // block sums -> F, noise bias
   launch_fisher_blocksum(W, d.k, d.nc, d.k0, d.lmin, d.lmax, parts, diag, c.st);
@@ -479,9 +591,15 @@ qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims, doubl
   double *dcr = c.out(cl_decorr, (size_t)na * nsims, "cl_decorr");
   if (!c.make_status()) return c.finish();
   launch_copy_matrix(D, d.n, U, d.n, d.n, nsims, c.st);
-  trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, U, nsims, d.n);
   // w = Y^T C^-1 d = X^T (L^-1 d)
-  launch_dgemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, w, d.k, 0, c.status, c.st);
+  if (plan->split) {
+    Split spl{&c, plan->nslices};
+    trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, U, nsims, d.n);
+    spl.gemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, w, d.k, 0);
+  } else {
+    trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, U, nsims, d.n);
+    launch_dgemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, w, d.k, 0, c.status, c.st);
+  }
   launch_quad_y(w, d.k, nsims, d.nc, d.k0, d.lmin, d.lmax, plan->nspec, plan->uv, yd, c.st);
   launch_sub_bias(yd, plan->b, na, nsims, q, c.st);
   if (bd) launch_copy_matrix(plan->b, na, bd, na, na, 1, c.st);
@@ -512,10 +630,20 @@ qml_status pix_loglike(const qml_problem *prob, const double *cl_theta, const do
   double *ldparts = c.alloc<double>(nblocks);
   double *U = c.alloc<double>((size_t)d.n * nmaps, "U");
   if (!c.make_status()) return c.finish();
-  build_C(c, sp, d, Y, C);
-  potrf_blocked(c, C, d.n, d.n, Linv, ldparts, o_ld);
-  launch_copy_matrix(D, d.n, U, d.n, d.n, nmaps, c.st);
-  trsm_blocked(c, C, d.n, d.n, Linv, U, nmaps, d.n);
+  if (prob->precision == QML_SPLIT_BF16) {
+    Split spl{&c, prob->nslices};
+    double *LinvB = c.alloc<double>((size_t)((d.n + kNBS - 1) / kNBS) * kNBS * kNBS);
+    if (!LinvB) return c.finish();
+    build_C_split(c, spl, sp, d, Y, C);
+    potrf_split(c, spl, C, d.n, d.n, Linv, LinvB, ldparts, o_ld);
+    launch_copy_matrix(D, d.n, U, d.n, d.n, nmaps, c.st);
+    trsm_split(c, spl, C, d.n, d.n, LinvB, U, nmaps, d.n);
+  } else {
+    build_C(c, sp, d, Y, C);
+    potrf_blocked(c, C, d.n, d.n, Linv, ldparts, o_ld);
+    launch_copy_matrix(D, d.n, U, d.n, d.n, nmaps, c.st);
+    trsm_blocked(c, C, d.n, d.n, Linv, U, nmaps, d.n);
+  }
   launch_colnorm2(U, d.n, d.n, nmaps, o_chi, c.st);
   if (o_lnl) launch_loglike_finish(o_chi, o_ld, nmaps, o_lnl, c.st);
   return c.finish();

@@ -303,6 +303,14 @@ __global__ void loglike_finish_kernel(const double *chi2, const double *logdet, 
   if (j < nmaps) lnL[j] = -0.5 * (chi2[j] + *logdet);
 }
 
+__global__ void set_identity_kernel(double *X, int64_t ld, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ld * ld;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t % ld, j = t / ld;
+    X[t] = (i == j && i < n) ? 1.0 : 0.0;
+  }
+}
+
 int grid_for(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
@@ -370,6 +378,10 @@ void launch_colnorm2(const double *X, int64_t ldx, int64_t rows, int64_t cols, d
 void launch_loglike_finish(const double *chi2, const double *logdet, int nmaps, double *lnL,
                            cudaStream_t st) {
   { loglike_finish_kernel<<<(nmaps + 127) / 128, 128, 0, st>>>(chi2, logdet, nmaps, lnL); count_launch(); }
+}
+
+void launch_set_identity(double *X, int64_t ld, int64_t n, cudaStream_t st) {
+  { set_identity_kernel<<<grid_for(ld * ld), 256, 0, st>>>(X, ld, n); count_launch(); }
 }
 
 }  // namespace qmlgb

@@ -57,6 +57,8 @@ void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Li
 // (block b at Linv + b kNB^2, ld kNB), one CTA per block.
 void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,
                          DevStatus *status, cudaStream_t st);
+// ld x ld matrix with the n x n identity in its top-left corner, zeros elsewhere
+void launch_set_identity(double *X, int64_t ld, int64_t n, cudaStream_t st);
 void launch_sum_logdet(const double *parts, int nparts, double *out, cudaStream_t st);
 void launch_copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t n,
                        cudaStream_t st);

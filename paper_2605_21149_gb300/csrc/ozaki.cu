@@ -10,19 +10,21 @@
 // (products below the truncation level are dropped).  Every digit product
 // A_s B_t^T is an integer matrix; over a K-chunk of 2^(24 - 2 beta) its
 // entries stay below 2^24, so the FP32 tensor-core accumulation in TMEM is
-// exact whatever the accumulation order or rounding mode.  Each exact chunk is
-// converted to int32 and added into a per-level integer accumulator (TMEM);
-// when a level s+t = L is complete it is folded into float64 totals (TMEM) with
-// the weight 2^(-beta L).  float64 work is therefore S folds per output, not
-// one per product.
+// exact whatever the accumulation order or rounding mode.  Each exact chunk
+// is converted to int32 and added, shifted left by shift_L = shift_top -
+// beta (L - 2) bits (right, rounded, when negative) for its level L = s + t,
+// into one int64 fixed-point accumulator per output held in registers; the
+// top level fills at most 62 bits.  One float64 conversion per output remains.
 //
-// Kernel layout: one CTA per 128 x 128 output tile, 192 threads.
+// Kernel layout: one CTA per 128 x 128 output tile, 320 threads.
 //   warp 0   TMA producer (one lane): bf16 digit tiles 128 x 64 of op(A) and
 //            op(B), 128-byte swizzle, 4-stage ring guarded by mbarriers;
 //   warp 1   TMEM allocator and MMA issuer (one lane): tcgen05.mma kind::f16
-//            M=128 N=128 K=16, FP32 accumulator in TMEM columns [0,128);
-//   warps 2-5 epilogue: TMEM lanes = tile rows; int32 level sums in columns
-//            [128,256), float64 totals in [256,512).
+//            M=128 N=128 K=16 into one of two FP32 accumulators in TMEM
+//            (columns [0,128) and [128,256)), so a flush of one overlaps the
+//            MMAs of the next chunk;
+//   warps 2-9 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows)
+//            and 64 columns (half (w - 2) / 4 of the tile).
 // Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the CTA records
 // QML_ETIMEOUT, drains what it issued, frees TMEM and returns.
 #include "internal.cuh"
@@ -39,7 +41,7 @@ namespace {
 
 constexpr int OBM = 128, OBN = 128, OBK = 64, OSTAGES = 4;
 constexpr int kTileBytes = OBM * OBK * 2;  // 16 KB per operand tile
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
 
 // ------------------------------------------------------------ PTX helpers --
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -130,39 +132,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-#define TMEM_REGS32(r)                                                                           \
-  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),            \
-      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),    \
-      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),              \
-      "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),              \
-      "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-#define TMEM_IN32(r)                                                                             \
-  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),       \
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),          \
-      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),        \
-      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),        \
-      "r"(r[29]), "r"(r[30]), "r"(r[31])
-
-// 32 consecutive 32-bit TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : TMEM_REGS32(r)
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
-      "%29, %30, %31, %32};" ::"r"(taddr),
-      TMEM_IN32(r)
-      : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
 // K-major, 128-byte-swizzled bf16 tile (rows of 64 elements = 128 B, 8-row
 // atoms of 1024 B): start address, LBO 16 B (unused for this layout), SBO
 // 1024 B, descriptor version 1, layout type 2 (128-byte swizzle).
@@ -183,6 +163,7 @@ struct OzParams {
   int64_t M, N;            // logical output size
   int Mpad, Npad, nk;      // padded rows of the digit arrays; K stages of 64
   int S, beta, chunk;      // digits, bits per digit, stages per exact chunk
+  int shift_top;           // left shift of level-2 chunk sums in the int64 accumulator
   int tiles_n, lower;
   double alpha, betac;
   double *C;
@@ -214,8 +195,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char *tilesA = smem;
   unsigned char *tilesB = smem + OSTAGES * kTileBytes;
   uint64_t *bars = (uint64_t *)(smem + 2 * OSTAGES * kTileBytes);
-  // bars[0..S) full, [S..2S) empty, 2S acc_full, 2S+1 acc_empty, 2S+2 drain
-  uint32_t *tmem_holder = (uint32_t *)(bars + 2 * OSTAGES + 3);
+  // bars: [0,ST) full, [ST,2ST) empty, 2ST+b acc_full[b], 2ST+2+b acc_empty[b], 2ST+4 drain
+  uint32_t *tmem_holder = (uint32_t *)(bars + 2 * OSTAGES + 5);
   int *s_eb = (int *)(tmem_holder + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -224,21 +205,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int m0 = tm * OBM, n0 = tn * OBN;
   DevStatus *st = p.status;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OSTAGES]);
-  const uint32_t accf = smem_u32(&bars[2 * OSTAGES]), acce = smem_u32(&bars[2 * OSTAGES + 1]);
-  const uint32_t drain = smem_u32(&bars[2 * OSTAGES + 2]);
+  const uint32_t accf0 = smem_u32(&bars[2 * OSTAGES]), acce0 = smem_u32(&bars[2 * OSTAGES + 2]);
+  const uint32_t drain = smem_u32(&bars[2 * OSTAGES + 4]);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OSTAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accf, 1);
-    mbar_init(acce, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 256);
+    }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int j = threadIdx.x; j < OBN; j += blockDim.x) s_eb[j] = p.eb[n0 + j];
-  if (warp == 1) tmem_alloc(smem_u32(tmem_holder), 512);
+  if (warp == 1) tmem_alloc(smem_u32(tmem_holder), 256);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -284,14 +267,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t nflush = 0;  // accumulator hand-offs so far
+      uint32_t q = 0;  // chunk accumulations so far; buffer q & 1
       bool ok = (*((volatile int *)&st->code) == 0);
       for (int L = 2; L <= S + 1 && ok; ++L) {
         for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
           for (int c = 0; c < nchunks && ok; ++c) {
-            // the epilogue must have read the previous chunk
-            if (nflush > 0 && !mbar_wait(acce, (nflush - 1) & 1, st)) { ok = false; break; }
+            const uint32_t b = q & 1;
+            // the epilogue must have read this buffer's previous chunk
+            if (q >= 2 && !mbar_wait(acce0 + 8 * b, ((q >> 1) - 1) & 1, st)) { ok = false; break; }
             tc_fence_after();
+            const uint32_t dacc = tbase + 128 * b;
             const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
             for (int ks = k0; ks < k1; ++ks) {
               if (!mbar_wait(full0 + 8 * stage, phase, st)) { ok = false; break; }
@@ -300,15 +285,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t b_addr = smem_u32(tilesB + stage * kTileBytes);
 #pragma unroll
               for (int kk = 0; kk < OBK / 16; ++kk) {
-                mma_bf16(tbase, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk), kIdesc,
+                mma_bf16(dacc, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk), kIdesc,
                          (ks > k0 || kk > 0) ? 1u : 0u);
               }
               mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
               if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
             }
             if (!ok) break;
-            mma_commit(accf);  // chunk result ready for the epilogue
-            ++nflush;
+            mma_commit(accf0 + 8 * b);  // chunk result ready for the epilogue
+            ++q;
           }
         }
       }
@@ -318,95 +303,59 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------------------------------------------------- epilogue
-    const int quad = warp & 3;  // TMEM lane quarter this warp may access
+    const int quad = warp & 3;            // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;     // which 64 columns of the tile
     const int row = quad * 32 + lane;
-    const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16);
-    const uint32_t c_acc = lane_base, c_lvl = lane_base + 128, c_tot = lane_base + 256;
-    uint32_t nflush = 0;
+    const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16) + 64 * half;
+    long long acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    uint32_t q = 0;
     bool ok = true;
     for (int L = 2; L <= S + 1 && ok; ++L) {
-      bool first_in_level = true;
+      const int sh = p.shift_top - p.beta * (L - 2);
       for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
         for (int c = 0; c < nchunks; ++c) {
+          const uint32_t b = q & 1;
           int okw = 1;
-          if (lane == 0) okw = mbar_wait(accf, nflush & 1, st) ? 1 : 0;
+          if (lane == 0) okw = mbar_wait(accf0 + 8 * b, (q >> 1) & 1, st) ? 1 : 0;
           okw = __shfl_sync(0xffffffffu, okw, 0);
           __syncwarp();
           if (!okw) { ok = false; break; }
           tc_fence_after();
-#pragma unroll 1
-          for (int cb = 0; cb < OBN / 32; ++cb) {
-            uint32_t a[32], v[32];
-            tmem_ld32(c_acc + 32 * cb, a);
-            if (first_in_level) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) v[j] = (uint32_t)__float2int_rn(__uint_as_float(a[j]));
+          for (int cb = 0; cb < 4; ++cb) {
+            uint32_t a[16];
+            tmem_ld16(lane_base + 128 * b + 16 * cb, a);
+            if (sh >= 0) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                acc[16 * cb + j] += (long long)__float2int_rn(__uint_as_float(a[j])) << sh;
             } else {
-              tmem_ld32(c_lvl + 32 * cb, v);
+              const int r = -sh;
+              const long long rnd = 1LL << (r - 1);
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                v[j] = (uint32_t)((int)v[j] + __float2int_rn(__uint_as_float(a[j])));
+              for (int j = 0; j < 16; ++j)
+                acc[16 * cb + j] += ((long long)__float2int_rn(__uint_as_float(a[j])) + rnd) >> r;
             }
-            tmem_st32(c_lvl + 32 * cb, v);
           }
-          first_in_level = false;
           tc_fence_before();
-          mbar_arrive(acce);
-          ++nflush;
+          mbar_arrive(acce0 + 8 * b);
+          ++q;
         }
-      }
-      if (!ok) break;
-      // fold level L into the float64 totals: tot += 2^(-beta L) lvl
-      const double w = ldexp(1.0, -p.beta * L);
-#pragma unroll 1
-      for (int cb = 0; cb < OBN / 32; ++cb) {
-        uint32_t v[32], t0[32], t1[32];
-        tmem_ld32(c_lvl + 32 * cb, v);
-        if (L > 2) {
-          tmem_ld32(c_tot + 64 * cb, t0);
-          tmem_ld32(c_tot + 64 * cb + 32, t1);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          double prev = 0.0;
-          if (L > 2) {
-            const int jj = 2 * j;
-            const uint32_t lo = jj < 32 ? t0[jj] : t1[jj - 32];
-            const uint32_t hi = jj + 1 < 32 ? t0[jj + 1] : t1[jj + 1 - 32];
-            prev = __hiloint2double((int)hi, (int)lo);
-          }
-          const double nv = fma((double)(int)v[j], w, prev);
-          const int jj = 2 * j;
-          if (jj < 32) {
-            t0[jj] = (uint32_t)__double2loint(nv);
-            t0[jj + 1] = (uint32_t)__double2hiint(nv);
-          } else {
-            t1[jj - 32] = (uint32_t)__double2loint(nv);
-            t1[jj - 31] = (uint32_t)__double2hiint(nv);
-          }
-        }
-        tmem_st32(c_tot + 64 * cb, t0);
-        tmem_st32(c_tot + 64 * cb + 32, t1);
       }
     }
     if (ok) {
-      // output: alpha 2^(e_i + f_j) tot + beta C
+      // output: alpha 2^(e_i + f_j - 2 beta - shift_top) acc + beta C
       const int64_t gi = m0 + row;
-      const int ei = (gi < p.M) ? p.ea[gi] : 0;
-#pragma unroll 1
-      for (int cb = 0; cb < OBN / 32; ++cb) {
-        uint32_t t0[32], t1[32];
-        tmem_ld32(c_tot + 64 * cb, t0);
-        tmem_ld32(c_tot + 64 * cb + 32, t1);
-        if (gi >= p.M) continue;
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-          const int64_t gj = n0 + 32 * cb + j;
+      if (gi < p.M) {
+        const int ebase = p.ea[gi] - 2 * p.beta - p.shift_top;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int jl = 64 * half + j;
+          const int64_t gj = n0 + jl;
           if (gj >= p.N || (p.lower && gi < gj)) continue;
-          const int jj = 2 * j;
-          const uint32_t lo = jj < 32 ? t0[jj] : t1[jj - 32];
-          const uint32_t hi = jj + 1 < 32 ? t0[jj + 1] : t1[jj + 1 - 32];
-          double v = p.alpha * ldexp(__hiloint2double((int)hi, (int)lo), ei + s_eb[32 * cb + j]);
+          double v = p.alpha * ldexp((double)acc[j], ebase + s_eb[jl]);
           double *cp = p.C + gi + gj * p.ldc;
           if (p.betac != 0.0) v = fma(p.betac, *cp, v);
           *cp = v;
@@ -417,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tbase, 512);
+  if (warp == 1) tmem_dealloc(tbase, 256);
 }
 
 // ------------------------------------------------------------- digits ----
@@ -601,6 +550,14 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.S = S;
   p.beta = beta;
   p.chunk = (1 << (24 - 2 * beta)) / OBK;
+  {
+    // level-2 chunk sums are < 2^24 each; nchunks of them (plus the smaller
+    // lower levels, < 6 % extra) must fit in 62 bits after the shift
+    const int nchunks = (p.nk + p.chunk - 1) / p.chunk;
+    int lg = 0;
+    while ((1 << lg) < nchunks) ++lg;
+    p.shift_top = 37 - lg;
+  }
   p.tiles_n = (int)(Npad / OBN);
   p.lower = lower;
   p.alpha = alpha;
@@ -612,7 +569,7 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.status = status;
   const int tiles_m = (int)(Mpad / OBM);
   int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
-  const size_t smem = 1024 + 2 * OSTAGES * kTileBytes + (2 * OSTAGES + 3) * 8 + 16 + OBN * 4;
+  const size_t smem = 1024 + 2 * OSTAGES * kTileBytes + (2 * OSTAGES + 5) * 8 + 16 + OBN * 4;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel,

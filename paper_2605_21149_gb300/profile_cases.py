@@ -1,6 +1,7 @@
 """Single-call cases for profiler captures (ncu), on the TQU Nside 16 workload.
 
     python -m paper_2605_21149_gb300.profile_cases syrk     # W = X^T X, k=6900, n=5952
+    python -m paper_2605_21149_gb300.profile_cases syrk_split  # the same, split precision
     python -m paper_2605_21149_gb300.profile_cases ybuild   # Y, 5952 x 6900
     python -m paper_2605_21149_gb300.profile_cases fisher   # one full qml_fisher
 
@@ -18,16 +19,17 @@ def main():
     from . import api, build, synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=("syrk", "ybuild", "fisher"))
+    ap.add_argument("case", choices=("syrk", "syrk_split", "ybuild", "fisher"))
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
     build.build()
     wl = synth.workload(1)
     prob = api.Problem.from_workload(wl)
-    if args.case == "syrk":
+    if args.case in ("syrk", "syrk_split"):
         X = torch.randn(wl.k, wl.n, dtype=torch.float64, device="cuda").t()
         W = torch.empty(wl.k, wl.k, dtype=torch.float64, device="cuda").t()
-        fn = lambda: api.gemm(X, X, W, transA=True, lower=True)
+        prec = 1 if args.case == "syrk_split" else 0
+        fn = lambda: api.gemm(X, X, W, transA=True, lower=True, precision=prec)
     elif args.case == "ybuild":
         fn = lambda: api.ybuild(prob)
     else:
