@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--nsims", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the split-precision forms")
+    ap.add_argument("--no-fp64-qu32", action="store_true",
+                    help="skip the single float64 solve of the QU Nside 32 workload")
     return ap.parse_args()
 
 
@@ -289,6 +292,97 @@ def run_ours(args):
                                "measured in this run; MEASURED_PEAKS.json has no float64 entry",
                 "traffic": None, "flops_per_launch": flops, "ms_per_launch": dur * 1e3}
 
+    # ---- split-precision form (bf16 digits on tcgen05, float64 recombination;
+    # 1e-8 against the float64 oracle in tests/test_gpu_split_pipeline.py)
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {}
+        prob_s = api.Problem.from_workload(wl, device=True, precision=1)
+
+        def step_s():
+            F, plan = api.fisher(prob_s)
+            plan.estimate(maps)
+            api.loglike(prob_s, cl_dev, map1)
+            plan.free()
+        for _ in range(max(2, args.warmup)):
+            step_s()
+        torch.cuda.synchronize()
+        e6, e7 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e6.record()
+        for _ in range(args.steps):
+            step_s()
+        e7.record()
+        e7.synchronize()
+        ts = e6.elapsed_time(e7) * 1e-3
+        forms["split_bf16"] = {"workload": cfg["workload"], "value": args.steps / ts, "unit": UNIT,
+                               "ms_per_step": 1e3 * ts / args.steps,
+                               "speedup_vs_fp64": (args.steps / ts) / (args.steps / (t / world)),
+                               "tolerance": "1e-8 vs float64 oracle"}
+        # the QU Nside 32 split-precision workload (n = 17152, k = 18424)
+        wl3 = synth.workload(2)
+        p3s = api.Problem.from_workload(wl3, device=True, precision=1)
+        g3 = synth.rng(2, synth.P_SIMS)
+        alm3 = synth.draw_alm(wl3.cl_fid, wl3.lmin, wl3.lmax, wl3.comps, 2, g3)
+        noise3 = synth.noise_draws(wl3.G, 2, g3)
+        maps3 = api.synthesize(p3s, td(alm3), td(noise3))
+        cl3 = torch.as_tensor(wl3.cl_fid.reshape(-1), device="cuda")
+
+        def step3(pr):
+            F, plan = api.fisher(pr)
+            plan.estimate(maps3)
+            api.loglike(pr, cl3, maps3[:, :1])
+            plan.free()
+        step3(p3s)
+        torch.cuda.synchronize()
+        e8, e9 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e8.record()
+        for _ in range(2):
+            step3(p3s)
+        e9.record()
+        e9.synchronize()
+        t3s = e8.elapsed_time(e9) * 1e-3 / 2
+        f3 = {"workload": f"{wl3.name}: QU HEALPix Nside 32, f_sky 0.7 cut, n={wl3.n}, "
+                          f"l=2..95 (k={wl3.k}), 3 spectra, rank-200 N, 2 maps",
+              "split_bf16": {"value": 1.0 / t3s, "unit": UNIT, "ms_per_step": 1e3 * t3s}}
+        if not args.no_fp64_qu32:
+            p3d = api.Problem.from_workload(wl3, device=True, precision=0)
+            e10, e11 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e10.record()
+            step3(p3d)
+            e11.record()
+            e11.synchronize()
+            t3d = e10.elapsed_time(e11) * 1e-3
+            f3["fp64"] = {"value": 1.0 / t3d, "unit": UNIT, "ms_per_step": 1e3 * t3d, "steps": 1}
+            f3["split_speedup_vs_fp64"] = t3d / t3s
+            del p3d
+        forms["qu_nside32"] = f3
+        del p3s, maps3
+        torch.cuda.empty_cache()
+        # the split kernel against the measured bf16 tensor peak: W = X^T X
+        # (k=6900, n=5952), 36 digit products of 2 k(k+1)/2 n flops each
+        X = torch.randn(wl.k, wl.n, dtype=torch.float64, device="cuda").t()
+        W = torch.empty(wl.k, wl.k, dtype=torch.float64, device="cuda").t()
+        api.gemm(X, X, W, transA=True, lower=True, precision=1)
+        e12, e13 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e12.record()
+        for _ in range(3):
+            api.gemm(X, X, W, transA=True, lower=True, precision=1)
+        e13.record()
+        e13.synchronize()
+        dur_s = e12.elapsed_time(e13) * 1e-3 / 3
+        pk = peaks()
+        bf16_peak = pk.get("bf16_tflops", 1900.0)
+        tensor_flops = 36 * float(wl.k) * wl.k * wl.n
+        forms["roofline_split"] = {
+            "kernel": "split GEMM (slicing + ozaki_gemm_kernel), W = X^T X lower, k=6900, n=5952",
+            "bound": "tensor", "achieved": tensor_flops / dur_s / 1e12, "peak": bf16_peak,
+            "unit": "TFLOP/s", "frac": tensor_flops / dur_s / 1e12 / bf16_peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured",
+            "fp64_equivalent_tflops": float(wl.k) * wl.k * wl.n / dur_s / 1e12,
+            "ms_per_launch": dur_s * 1e3}
+        del X, W
+        torch.cuda.empty_cache()
+
     # ---- end to end through the same entry points with pinned host buffers
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -332,7 +426,7 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "config": cfg,
                 "lnl_evals_per_s": lnl_rate, "roofline": roof, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": int(c1 - c0), "clocks": clocks}
+                "e2e": e2e, "gpu_launches": int(c1 - c0), "clocks": clocks, "forms": forms}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
