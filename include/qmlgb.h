@@ -145,6 +145,31 @@ void qml_plan_free(qml_plan *plan);
 qml_status pix_loglike(const qml_problem *prob, const double *cl_theta, const double *maps,
                        int32_t nmaps, double *lnL, double *chi2, double *logdet, void *stream);
 
+/* One mask of a batched likelihood scan: its problem (geometry, transfer,
+ * noise N, precision; cl_fid and spec are ignored) and the nmaps maps
+ * (n x nmaps) observed through it. */
+typedef struct {
+  qml_problem prob;
+  const double *maps;
+  int32_t nmaps;
+} lnl_mask;
+
+/* Batched pixel log-likelihood over a parameter scan with mixed masks
+ * (Sect. 2.6, Eq. pixel_likelihood, evaluated through the SMW identity and the
+ * determinant lemma, Eqs. smw, logdet and quad_form_smw, in the congruent form
+ * Kt = I + L^T M L with M = Y^T N^-1 Y and Lambda(theta) = L L^T per (l, m),
+ * App. C.3): ln|C| = ln|N| + ln|Kt|, d^T C^-1 d = d^T N^-1 d - |Lk^-1 L^T Y^T
+ * N^-1 d|^2.  masks: HOST array of nmask descriptors (same fields and
+ * multipole band).  Item i uses mask item_mask[i] (host or device, nitems) and
+ * spectra item_cl + i*6*(lmax+1).  Outputs (row-major per item, leading
+ * dimension ld_out >= the largest nmaps): lnL[i*ld_out + j], chi2[...] and
+ * logdet[i]; any may be NULL.  The per-mask part (Cholesky of N, M, Y^T N^-1 d)
+ * runs once; items run on four internal streams.  Errors: QML_EINVAL,
+ * QML_ENOTSPD (N not positive definite), QML_ETIMEOUT. */
+qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitems,
+                             const int32_t *item_mask, const double *item_cl, int32_t ld_out,
+                             double *lnL, double *chi2, double *logdet, void *stream);
+
 /* ---- dense building blocks (exposed for testing the kernels one by one) -- */
 
 /* In-place lower Cholesky A = L L^T of an n x n SPD matrix (lower triangle

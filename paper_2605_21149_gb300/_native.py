@@ -32,6 +32,10 @@ class QmlProblem(ctypes.Structure):
     ]
 
 
+class LnlMask(ctypes.Structure):
+    _fields_ = [("prob", QmlProblem), ("maps", c_void_p), ("nmaps", c_int32)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "qml_version": (c_int32, []),
@@ -47,6 +51,8 @@ SIGNATURES = {
     "qml_plan_free": (None, [c_void_p]),
     "pix_loglike": (c_int32, [ctypes.POINTER(QmlProblem), c_void_p, c_void_p, c_int32, c_void_p,
                               c_void_p, c_void_p, c_void_p]),
+    "pix_loglike_batch": (c_int32, [ctypes.POINTER(LnlMask), c_int32, c_int32, c_void_p, c_void_p,
+                                    c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "qml_potrf": (c_int32, [c_int64, c_void_p, c_int64, c_void_p, c_int32, c_void_p]),
     "qml_potrf_noalloc": (c_int32, [c_int64, c_void_p, c_int64, c_void_p, c_void_p]),
     "qml_trsm": (c_int32, [c_int64, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_int32,

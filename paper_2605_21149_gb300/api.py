@@ -234,6 +234,34 @@ def loglike(prob: Problem, cl_theta, maps):
     return lnl[:, 0], chi2[:, 0], ld[0, 0]
 
 
+def loglike_batch(masks, item_mask, item_cl):
+    """Batched lnL over items with mixed masks (pix_loglike_batch).
+
+    masks: list of (Problem, maps) with maps n x nmaps; item_mask: nitems ints;
+    item_cl: nitems x 6 x (lmax+1) spectra.  Returns (lnL, chi2, logdet) with
+    lnL, chi2 of shape (nitems, max nmaps) and logdet (nitems,).
+    """
+    keep = []
+    arr = (nat.LnlMask * len(masks))()
+    maxmaps = 0
+    for i, (prob, maps) in enumerate(masks):
+        nm = maps.shape[1] if maps.ndim == 2 else 1
+        arr[i].prob = prob._p
+        arr[i].maps = _mat(maps, prob.n, nm, keep)
+        arr[i].nmaps = nm
+        maxmaps = max(maxmaps, nm)
+    dev = masks[0][0].device
+    nitems = len(item_mask)
+    im = np.ascontiguousarray(np.asarray(item_mask), dtype=np.int32)
+    keep.append(im)
+    cl = _vec(item_cl.reshape(-1) if hasattr(item_cl, "reshape") else item_cl, keep)
+    lnl, chi2 = _empty(maxmaps, nitems, dev), _empty(maxmaps, nitems, dev)
+    ld = _empty(nitems, 1, dev)
+    _check(_lib().pix_loglike_batch(arr, len(masks), nitems, im.ctypes.data, cl, maxmaps,
+                                    _ptr(lnl), _ptr(chi2), _ptr(ld), _stream(dev)))
+    return lnl.T, chi2.T, ld[:, 0]
+
+
 def potrf(A, precision=nat.QML_FP64):
     """In-place lower Cholesky of a square column-major matrix; returns ln|A|."""
     n = A.shape[0]

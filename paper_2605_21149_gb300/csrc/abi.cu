@@ -242,6 +242,7 @@ bool stage_problem(Call &c, const qml_problem *p, const Dims &d, Staged &s, cons
   s.y.theta_P = p->has_P ? c.in(p->theta_P, d.nP, "theta_P") : nullptr;
   s.y.phi_P = p->has_P ? c.in(p->phi_P, d.nP, "phi_P") : nullptr;
   s.y.transfer_P = p->has_P ? c.in(p->transfer_P, L, "transfer_P") : nullptr;
+  s.y.coef = c.alloc<unsigned char>(ybuild_coef_bytes(d.lmax), "recurrence coefficients");
   if (cl) s.cl = c.in(cl, 6 * L, "cl");
   if (need_N) s.N = c.in(p->N, (size_t)d.n * d.n, "N");
   return c.err == QML_OK;
@@ -313,6 +314,11 @@ struct Split {
   void *ws = nullptr;
   size_t ws_bytes = 0;
   double *eye = nullptr;  // kNBS x kNBS scratch for block inverses
+  // use a caller-provided workspace (no allocation later)
+  void preset(void *p, size_t bytes) {
+    ws = p;
+    ws_bytes = bytes;
+  }
   // make sure the digit workspace holds a product of this shape
   bool reserve(int64_t M, int64_t N, int64_t K, bool shared) {
     size_t need = ozaki_workspace_bytes(M, N, K, nslices, shared);
@@ -647,6 +653,185 @@ qml_status pix_loglike(const qml_problem *prob, const double *cl_theta, const do
   launch_colnorm2(U, d.n, d.n, nmaps, o_chi, c.st);
   if (o_lnl) launch_loglike_finish(o_chi, o_ld, nmaps, o_lnl, c.st);
   return c.finish();
+}
+
+qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitems,
+                             const int32_t *item_mask, const double *item_cl, int32_t ld_out,
+                             double *lnL, double *chi2, double *logdet, void *stream) {
+  if (!masks || nmask < 1) return fail(QML_EINVAL, "need nmask >= 1 masks");
+  if (nitems < 0 || (nitems > 0 && (!item_mask || !item_cl)))
+    return fail(QML_EINVAL, "need item_mask and item_cl for nitems > 0");
+  std::vector<Dims> dims(nmask);
+  int maxmaps = 0;
+  for (int m = 0; m < nmask; ++m) {
+    qml_status st = check_problem(&masks[m].prob, dims[m], false, true);
+    if (st != QML_OK) return fail(st, "mask " + std::to_string(m) + ": " + g_err);
+    if (!masks[m].maps || masks[m].nmaps < 1)
+      return fail(QML_EINVAL, "mask " + std::to_string(m) + ": need maps and nmaps >= 1");
+    if (dims[m].lmin != dims[0].lmin || dims[m].lmax != dims[0].lmax ||
+        dims[m].nc != dims[0].nc || masks[m].prob.has_T != masks[0].prob.has_T)
+      return fail(QML_EINVAL, "all masks need the same fields and multipole band");
+    maxmaps = masks[m].nmaps > maxmaps ? masks[m].nmaps : maxmaps;
+  }
+  if (ld_out < maxmaps) return fail(QML_EINVAL, "ld_out < largest nmaps");
+  if (nitems == 0) return QML_OK;
+  const Dims &d0 = dims[0];
+  const size_t L = (size_t)d0.lmax + 1;
+  // item -> mask on the host (the schedule is built there)
+  std::vector<int32_t> imask(nitems);
+  if (is_device_ptr(item_mask)) {
+    if (cudaMemcpy(imask.data(), item_mask, nitems * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return fail(QML_ECUDA, "item_mask copy");
+  } else {
+    memcpy(imask.data(), item_mask, nitems * sizeof(int32_t));
+  }
+  for (int i = 0; i < nitems; ++i)
+    if (imask[i] < 0 || imask[i] >= nmask) return fail(QML_EINVAL, "item_mask out of range");
+
+  Call c(stream);
+  const double *cl_d = c.in(item_cl, (size_t)nitems * 6 * L, "item_cl");
+  double *o_lnl = c.out(lnL, (size_t)nitems * ld_out, "lnL");
+  double *o_chi = c.out(chi2, (size_t)nitems * ld_out, "chi2");
+  double *o_ld = c.out(logdet, (size_t)nitems, "logdet");
+  if (!c.make_status()) return c.finish();
+
+  // ---- per-mask setup: L_N, M = Y^T N^-1 Y, v = Y^T N^-1 d, d^T N^-1 d, ln|N|
+  struct MaskState {
+    double *M = nullptr, *v = nullptr, *dnd = nullptr, *lnN = nullptr;
+  };
+  std::vector<MaskState> ms(nmask);
+  const int k = d0.k;
+  for (int m = 0; m < nmask; ++m) {
+    const Dims &d = dims[m];
+    const qml_problem *pr = &masks[m].prob;
+    const int nm = masks[m].nmaps;
+    Staged sp;
+    if (!stage_problem(c, pr, d, sp, nullptr, true)) return c.finish();
+    const double *D = c.in(masks[m].maps, (size_t)d.n * nm, "maps");
+    const int64_t nb = (d.n + kNB - 1) / kNB;
+    double *U = c.alloc<double>((size_t)d.n * k, "Y");
+    double *LN = c.alloc<double>((size_t)d.n * d.n, "L_N");
+    double *Linv = c.alloc<double>((size_t)nb * kNB * kNB);
+    double *ldp = c.alloc<double>(nb);
+    double *u = c.alloc<double>((size_t)d.n * nm);
+    ms[m].M = c.alloc<double>((size_t)k * k, "M");
+    ms[m].v = c.alloc<double>((size_t)k * nm);
+    ms[m].dnd = c.alloc<double>(nm);
+    ms[m].lnN = c.alloc<double>(1);
+    if (c.err != QML_OK) return c.finish();
+    launch_ybuild(sp.y, U, d.n, c.st);
+    launch_copy_lower(sp.N, d.n, LN, d.n, d.n, c.st);
+    launch_copy_matrix(D, d.n, u, d.n, d.n, nm, c.st);
+    if (pr->precision == QML_SPLIT_BF16) {
+      Split spl{&c, pr->nslices};
+      double *LinvB = c.alloc<double>((size_t)((d.n + kNBS - 1) / kNBS) * kNBS * kNBS);
+      if (!LinvB) return c.finish();
+      potrf_split(c, spl, LN, d.n, d.n, Linv, LinvB, ldp, ms[m].lnN);
+      trsm_split(c, spl, LN, d.n, d.n, LinvB, U, k, d.n);
+      trsm_split(c, spl, LN, d.n, d.n, LinvB, u, nm, d.n);
+      spl.gemm(1, 0, k, k, d.n, 1.0, U, d.n, U, d.n, 0.0, ms[m].M, k, 1);
+      spl.gemm(1, 0, k, nm, d.n, 1.0, U, d.n, u, d.n, 0.0, ms[m].v, k, 0);
+    } else {
+      potrf_blocked(c, LN, d.n, d.n, Linv, ldp, ms[m].lnN);
+      trsm_blocked(c, LN, d.n, d.n, Linv, U, k, d.n);
+      trsm_blocked(c, LN, d.n, d.n, Linv, u, nm, d.n);
+      launch_dgemm(1, 0, k, k, d.n, 1.0, U, d.n, U, d.n, 0.0, ms[m].M, k, 1, c.status, c.st);
+      launch_dgemm(1, 0, k, nm, d.n, 1.0, U, d.n, u, d.n, 0.0, ms[m].v, k, 0, c.status, c.st);
+    }
+    launch_symmetrize_lower(ms[m].M, k, k, c.st);
+    launch_colnorm2(u, d.n, d.n, nm, ms[m].dnd, c.st);
+  }
+
+  // ---- per-item work, round-robin over worker streams
+  const int NS = nitems < 4 ? nitems : 4;
+  bool any_split = false;
+  for (int m = 0; m < nmask; ++m) any_split |= (masks[m].prob.precision == QML_SPLIT_BF16);
+  struct Worker {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    double *K, *lamL, *z, *rr, *Linv, *LinvB, *ldp;
+    void *ws;
+    size_t ws_bytes;
+  };
+  std::vector<Worker> wk(NS);
+  const int64_t nbk = (k + kNB - 1) / kNB, nbbk = (k + kNBS - 1) / kNBS;
+  size_t wsb = 0;
+  if (any_split) {
+    wsb = ozaki_workspace_bytes(k, k, kNBS, 0, true);
+    size_t b2 = ozaki_workspace_bytes(k, kNBS, kNBS, 0, false);
+    size_t b3 = ozaki_workspace_bytes(k, maxmaps, kNBS, 0, false);
+    if (b2 > wsb) wsb = b2;
+    if (b3 > wsb) wsb = b3;
+  }
+  double *lnK = c.alloc<double>(nitems);
+  for (int w = 0; w < NS; ++w) {
+    wk[w].K = c.alloc<double>((size_t)k * k, "Kt");
+    wk[w].lamL = c.alloc<double>((size_t)d0.nl * d0.nc * d0.nc);
+    wk[w].z = c.alloc<double>((size_t)k * maxmaps);
+    wk[w].rr = c.alloc<double>(maxmaps);
+    wk[w].Linv = c.alloc<double>((size_t)nbk * kNB * kNB);
+    wk[w].LinvB = any_split ? c.alloc<double>((size_t)nbbk * kNBS * kNBS) : nullptr;
+    wk[w].ldp = c.alloc<double>(nbk);
+    wk[w].ws = any_split ? (void *)c.alloc<unsigned char>(wsb, "split workspace") : nullptr;
+    wk[w].ws_bytes = wsb;
+  }
+  if (c.err != QML_OK) return c.finish();
+  cudaEvent_t setup_done;
+  if (!c.cuda_ok(cudaEventCreateWithFlags(&setup_done, cudaEventDisableTiming), "event"))
+    return c.finish();
+  c.cuda_ok(cudaEventRecord(setup_done, c.st), "event");
+  for (int w = 0; w < NS && c.err == QML_OK; ++w) {
+    c.cuda_ok(cudaStreamCreateWithFlags(&wk[w].st, cudaStreamNonBlocking), "worker stream");
+    c.cuda_ok(cudaEventCreateWithFlags(&wk[w].done, cudaEventDisableTiming), "event");
+    if (wk[w].st) c.cuda_ok(cudaStreamWaitEvent(wk[w].st, setup_done, 0), "event wait");
+  }
+  std::vector<Call *> wc(NS, nullptr);
+  for (int w = 0; w < NS; ++w) {
+    wc[w] = new Call(wk[w].st);
+    wc[w]->status = c.status;
+  }
+  for (int i = 0; i < nitems && c.err == QML_OK; ++i) {
+    const int w = i % NS, m = imask[i];
+    Call &cw = *wc[w];
+    Worker &W = wk[w];
+    const int nm = masks[m].nmaps;
+    const bool split = masks[m].prob.precision == QML_SPLIT_BF16;
+    launch_lambda_factor(cl_d + (size_t)i * 6 * L, d0.lmin, d0.lmax, d0.nc, d0.comps, W.lamL, W.st);
+    launch_form_ktilde(ms[m].M, k, d0.nc, d0.k0, d0.lmin, W.lamL, W.K, k, W.st);
+    launch_lambda_t_apply(ms[m].v, k, d0.nc, d0.k0, d0.lmin, W.lamL, nm, W.z, k, W.st);
+    if (split) {
+      Split spl{&cw, masks[m].prob.nslices};
+      spl.preset(W.ws, W.ws_bytes);
+      potrf_split(cw, spl, W.K, k, k, W.Linv, W.LinvB, W.ldp, lnK + i);
+      trsm_split(cw, spl, W.K, k, k, W.LinvB, W.z, nm, k);
+    } else {
+      potrf_blocked(cw, W.K, k, k, W.Linv, W.ldp, lnK + i);
+      trsm_blocked(cw, W.K, k, k, W.Linv, W.z, nm, k);
+    }
+    launch_colnorm2(W.z, k, k, nm, W.rr, W.st);
+    launch_batch_finish(W.rr, ms[m].dnd, ms[m].lnN, lnK + i, nm,
+                        o_lnl ? o_lnl + (size_t)i * ld_out : nullptr,
+                        o_chi ? o_chi + (size_t)i * ld_out : nullptr, o_ld ? o_ld + i : nullptr,
+                        W.st);
+    if (cw.err != QML_OK && c.err == QML_OK) {
+      c.err = cw.err;
+    }
+  }
+  for (int w = 0; w < NS; ++w) {
+    if (wk[w].st && wk[w].done) {
+      cudaEventRecord(wk[w].done, wk[w].st);
+      cudaStreamWaitEvent(c.st, wk[w].done, 0);
+    }
+  }
+  qml_status res = c.finish();
+  for (int w = 0; w < NS; ++w) {
+    delete wc[w];
+    if (wk[w].done) cudaEventDestroy(wk[w].done);
+    if (wk[w].st) cudaStreamDestroy(wk[w].st);
+  }
+  cudaEventDestroy(setup_done);
+  return res;
 }
 
 qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t precision,

@@ -7,8 +7,9 @@
 // rounds of a sweep the n indices form n/2 disjoint pairs; every pair gets the
 // Jacobi rotation that zeroes its off-diagonal entry, and because the pairs
 // are disjoint the update A <- J^T A J splits into independent 2x2 blocks
-// R_a^T A[pair a, pair b] R_b.  One cooperative kernel runs all rounds; a grid
-// barrier separates them (A is double-buffered).  float64 on CUDA cores is a
+// R_a^T A[pair a, pair b] R_b.  One cooperative kernel runs all rounds: each
+// round computes the n/2 rotations once, then applies them; grid barriers
+// separate the phases (A is double-buffered).  float64 on CUDA cores is a
 // few FMAs per clock per SM on GB300, so the work of a round is spread over
 // every SM rather than one CTA.  Only blocks a <= b are computed and mirrored,
 // which keeps A exactly symmetric.  Barrier waits are bounded: after
@@ -75,7 +76,7 @@ __device__ __forceinline__ void rotation(double app, double aqq, double apq, dou
 }
 
 __global__ void __launch_bounds__(256) jacobi_kernel(double *A0, double *A1, double *V, int n,
-                                                     int max_sweeps, double *red,
+                                                     int max_sweeps, double *red, double *rot,
                                                      DevStatus *st) {
   const unsigned nblocks = gridDim.x;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -126,26 +127,37 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *A0, double *A1, dou
     if (!grid_barrier(st, nblocks)) return;
 
     for (int r = 0; r < n - 1; ++r) {
+      // phase 1: one rotation per pair, computed once (float64 division and
+      // square root are expensive on this part)
+      for (int64_t a = gtid; a < h; a += gsize) {
+        const int pa = player((int)a, r, n), qa = player(n - 1 - (int)a, r, n);
+        double c, sn, t;
+        const double apq = Aold[pa + (int64_t)qa * n];
+        rotation(Aold[pa + (int64_t)pa * n], Aold[qa + (int64_t)qa * n], apq, c, sn, t);
+        rot[4 * a] = c;
+        rot[4 * a + 1] = sn;
+        rot[4 * a + 2] = t * apq;
+      }
+      if (!grid_barrier(st, nblocks)) return;
+      // phase 2: apply every 2x2 block update and the eigenvector rotation
       for (int64_t task = gtid; task < nblk + nvt; task += gsize) {
         if (task < nblk) {
-          // upper-triangular block index (a <= b)
+          // upper-triangular block index (bb <= a)
           int a = (int)((sqrt(8.0 * task + 1.0) - 1.0) * 0.5);
           while ((int64_t)(a + 1) * (a + 2) / 2 <= task) ++a;
           while ((int64_t)a * (a + 1) / 2 > task) --a;
-          const int bb = (int)(task - (int64_t)a * (a + 1) / 2);  // bb <= a
+          const int bb = (int)(task - (int64_t)a * (a + 1) / 2);
           const int pa = player(bb, r, n), qa = player(n - 1 - bb, r, n);
           const int pb = player(a, r, n), qb = player(n - 1 - a, r, n);
-          double ca, sa, ta, cb, sb, tb;
-          const double apq_a = Aold[pa + (int64_t)qa * n];
-          rotation(Aold[pa + (int64_t)pa * n], Aold[qa + (int64_t)qa * n], apq_a, ca, sa, ta);
+          const double ca = rot[4 * bb], sa = rot[4 * bb + 1];
           if (a == bb) {
-            Anew[pa + (int64_t)pa * n] = Aold[pa + (int64_t)pa * n] - ta * apq_a;
-            Anew[qa + (int64_t)qa * n] = Aold[qa + (int64_t)qa * n] + ta * apq_a;
+            const double tapq = rot[4 * bb + 2];
+            Anew[pa + (int64_t)pa * n] = Aold[pa + (int64_t)pa * n] - tapq;
+            Anew[qa + (int64_t)qa * n] = Aold[qa + (int64_t)qa * n] + tapq;
             Anew[pa + (int64_t)qa * n] = 0.0;
             Anew[qa + (int64_t)pa * n] = 0.0;
           } else {
-            const double apq_b = Aold[pb + (int64_t)qb * n];
-            rotation(Aold[pb + (int64_t)pb * n], Aold[qb + (int64_t)qb * n], apq_b, cb, sb, tb);
+            const double cb = rot[4 * a], sb = rot[4 * a + 1];
             const double x00 = Aold[pa + (int64_t)pb * n], x01 = Aold[pa + (int64_t)qb * n];
             const double x10 = Aold[qa + (int64_t)pb * n], x11 = Aold[qa + (int64_t)qb * n];
             // X J_b, J = [[c, s], [-s, c]]
@@ -167,9 +179,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double *A0, double *A1, dou
           const int64_t vt = task - nblk;
           const int row = (int)(vt % n), a = (int)(vt / n);
           const int pa = player(a, r, n), qa = player(n - 1 - a, r, n);
-          double ca, sa, ta;
-          rotation(Aold[pa + (int64_t)pa * n], Aold[qa + (int64_t)qa * n],
-                   Aold[pa + (int64_t)qa * n], ca, sa, ta);
+          const double ca = rot[4 * a], sa = rot[4 * a + 1];
           const double vp = V[row + (int64_t)pa * n], vq = V[row + (int64_t)qa * n];
           V[row + (int64_t)pa * n] = ca * vp - sa * vq;
           V[row + (int64_t)qa * n] = sa * vp + ca * vq;
@@ -233,7 +243,7 @@ __global__ void eig_scale_kernel(const double *A, const double *V, int na, int n
 
 size_t fisher_eig_work_doubles(int na) {
   size_t n = (size_t)(na + (na & 1));
-  return 5 * n * n + 2 * 4096;
+  return 5 * n * n + 2 * 4096 + 4 * n;
 }
 
 cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, double *Fm12,
@@ -241,7 +251,7 @@ cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, 
   const int n = na + (na & 1);
   const size_t nn = (size_t)n * n;
   double *A0 = work, *A1 = work + nn, *V = work + 2 * nn, *S1 = work + 3 * nn,
-         *S2 = work + 4 * nn, *red = work + 5 * nn;
+         *S2 = work + 4 * nn, *red = work + 5 * nn, *rot = red + 2 * 4096;
   eig_setup_kernel<<<64, 256, 0, st>>>(F, na, n, A0, V);
   count_launch();
   int dev = 0;
@@ -258,7 +268,7 @@ cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, 
   int max_sweeps = 30;
   int nn_arg = n;
   void *args[] = {(void *)&A0, (void *)&A1, (void *)&V, (void *)&nn_arg, (void *)&max_sweeps,
-                  (void *)&red, (void *)&status};
+                  (void *)&red, (void *)&rot, (void *)&status};
   cudaError_t e = cudaLaunchCooperativeKernel((const void *)jacobi_kernel, dim3(nblocks),
                                               dim3(256), args, 0, st);
   if (e != cudaSuccess) return e;

@@ -28,7 +28,9 @@ struct YArgs {
   const double *theta_T, *phi_T, *theta_P, *phi_P;
   int lmin, lmax;
   const double *transfer_T, *transfer_P;
+  void *coef;  // workspace of ybuild_coef_bytes(lmax) bytes (recurrence coefficients)
 };
+size_t ybuild_coef_bytes(int lmax);
 void launch_ybuild(const YArgs &a, double *Y, int64_t ldy, cudaStream_t st);
 
 // Mix the columns of Y inside every (l, m) by the lower Cholesky factor of the
@@ -103,6 +105,18 @@ void launch_sub_bias(const double *y, const double *b, int na, int nsims, double
 cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, double *Fm12,
                            double *eig_minmax, DevStatus *status, cudaStream_t st);
 size_t fisher_eig_work_doubles(int na);
+
+// ---------------------------------------------------------------- batch --
+// Kt = I + L_Lambda^T M L_Lambda (lower triangle), z = L_Lambda^T v, and the
+// per-item lnL / chi2 / logdet (batched likelihood scan, harmonic form).
+void launch_form_ktilde(const double *M, int64_t ldm, int nc, int k0, int lmin,
+                        const double *lamL, double *K, int64_t ldk, cudaStream_t st);
+void launch_lambda_t_apply(const double *v, int64_t ldv, int nc, int k0, int lmin,
+                           const double *lamL, int nmaps, double *z, int64_t ldz,
+                           cudaStream_t st);
+void launch_batch_finish(const double *rr, const double *dnd, const double *lnN,
+                         const double *lnK, int nmaps, double *lnL, double *chi2, double *logdet,
+                         cudaStream_t st);
 
 // ---------------------------------------------------------------- ozaki --
 // Split-precision float64 GEMM (bf16 digits on tcgen05, exact FP32 chunks,

@@ -58,55 +58,84 @@ __device__ double wigner_start(int m, int s, double lc, double ls, double c, dou
   return v;
 }
 
-// advance (dm1 = d^{l-1}, d0 = d^l) -> d^{l+1}
-__device__ __forceinline__ double wigner_next(int l, int m, int s, double x, double dm1, double d0) {
-  const double lp = l + 1.0;
-  const double m2 = (double)m * m, s2 = (double)s * s;
-  if (l == 0) return x * d0;  // only m = s = 0: d^1_00 = cos(theta)
-  double a = (2.0 * l + 1.0) * ((double)l * lp * x - (double)m * s);
-  double b = lp * sqrt(((double)l * l - m2) * ((double)l * l - s2));
-  double den = (double)l * sqrt((lp * lp - m2) * (lp * lp - s2));
-  return (a * d0 - b * dm1) / den;
+// Recurrence coefficients, one entry per (m, l) (index m (lmax+1) + l):
+//   d^{l+1} = (alpha x - beta) d^l - gamma d^{l-1}
+//   alpha = (2l+1) l (l+1) / den,  beta = (2l+1) m s / den,
+//   gamma = (l+1) sqrt((l^2-m^2)(l^2-s^2)) / den,
+//   den = l sqrt(((l+1)^2-m^2)((l+1)^2-s^2))
+// Spin 0 (s = 0) uses c0 = (alpha, gamma); spin 2 uses c2 = (alpha, beta(s=2),
+// gamma), and s = -2 flips the sign of beta.  At l = 0 (m = s = 0 only)
+// d^1 = x: alpha = 1, beta = gamma = 0.
+struct RecCoef {
+  double a0, g0, a2, b2, g2;
+};
+
+__global__ void rec_coef_kernel(int lmax, RecCoef *tab) {
+  const int L = lmax + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L * L; t += gridDim.x * blockDim.x) {
+    const int m = t / L, l = t % L;
+    RecCoef c = {0, 0, 0, 0, 0};
+    const double lp = l + 1.0, m2 = (double)m * m;
+    if (l == 0) {
+      c.a0 = 1.0;
+    } else if (l >= m) {
+      double den0 = (double)l * sqrt((lp * lp - m2) * lp * lp);
+      c.a0 = (2.0 * l + 1.0) * (double)l * lp / den0;
+      c.g0 = lp * sqrt(((double)l * l - m2) * (double)l * l) / den0;
+      if (l >= 2) {
+        double den2 = (double)l * sqrt((lp * lp - m2) * (lp * lp - 4.0));
+        c.a2 = (2.0 * l + 1.0) * (double)l * lp / den2;
+        c.b2 = (2.0 * l + 1.0) * 2.0 * m / den2;
+        c.g2 = lp * sqrt(((double)l * l - m2) * ((double)l * l - 4.0)) / den2;
+      }
+    }
+    tab[t] = c;
+  }
 }
 
-__global__ void ybuild_T_kernel(YArgs a, double *Y, int64_t ldy) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.npix_T) return;
+// one thread per (pixel, m): the l recurrence of d^l_{m,0}; writes the m
+// columns of its pixel's row for every l >= max(lmin, m)
+__global__ void ybuild_T_kernel(YArgs a, const RecCoef *tab, double *Y, int64_t ldy) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int L = a.lmax + 1;
+  if (t >= (int64_t)a.npix_T * L) return;
+  const int p = (int)(t % a.npix_T), m = (int)(t / a.npix_T);
   const double th = a.theta_T[p], ph = a.phi_T[p];
   const double x = cos(th);
   const double c = cos(0.5 * th), sn = sin(0.5 * th);
   const double lc = log(c), ls = log(sn);
   const int lmin = a.lmin, lmax = a.lmax;
   double *row = Y + p;
-  for (int m = 0; m <= lmax; ++m) {
-    double sm, cm;
-    sincos((double)m * ph, &sm, &cm);
-    int l0 = m;
-    double dm1 = 0.0, d0 = wigner_start(m, 0, lc, ls, c, sn);
-    for (int l = l0; l <= lmax; ++l) {
-      if (l >= lmin) {
-        const double lam = sqrt((2.0 * l + 1.0) * kInv4Pi) * d0 * a.transfer_T[l];
-        const int64_t col = (int64_t)l * l - (int64_t)lmin * lmin;
-        if (m == 0) {
-          row[col * ldy] = lam;
-        } else {
-          row[(col + 2 * m - 1) * ldy] = kSqrt2 * lam * cm;
-          row[(col + 2 * m) * ldy] = kSqrt2 * lam * sm;
-        }
+  double sm, cm;
+  sincos((double)m * ph, &sm, &cm);
+  const RecCoef *tc = tab + (int64_t)m * L;
+  double dm1 = 0.0, d0 = wigner_start(m, 0, lc, ls, c, sn);
+  for (int l = m; l <= lmax; ++l) {
+    if (l >= lmin) {
+      const double lam = sqrt((2.0 * l + 1.0) * kInv4Pi) * d0 * a.transfer_T[l];
+      const int64_t col = (int64_t)l * l - (int64_t)lmin * lmin;
+      if (m == 0) {
+        row[col * ldy] = lam;
+      } else {
+        row[(col + 2 * m - 1) * ldy] = kSqrt2 * lam * cm;
+        row[(col + 2 * m) * ldy] = kSqrt2 * lam * sm;
       }
-      if (l < lmax) {
-        double dn = wigner_next(l, m, 0, x, dm1, d0);
-        dm1 = d0;
-        d0 = dn;
-      }
+    }
+    if (l < lmax) {
+      const RecCoef cc = tc[l];
+      const double dn = cc.a0 * x * d0 - cc.g0 * dm1;
+      dm1 = d0;
+      d0 = dn;
     }
   }
 }
 
-__global__ void ybuild_P_kernel(YArgs a, double *Y, int64_t ldy, int64_t colE, int64_t colB,
-                                int64_t rowQ, int64_t rowU) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.npix_P) return;
+__global__ void ybuild_P_kernel(YArgs a, const RecCoef *tab, double *Y, int64_t ldy,
+                                int64_t colE, int64_t colB, int64_t rowQ, int64_t rowU) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int L = a.lmax + 1;
+  if (t >= (int64_t)a.npix_P * L) return;
+  const int p = (int)(t % a.npix_P), m = (int)(t / a.npix_P);
   const double th = a.theta_P[p], ph = a.phi_P[p];
   const double x = cos(th);
   const double c = cos(0.5 * th), sn = sin(0.5 * th);
@@ -114,45 +143,46 @@ __global__ void ybuild_P_kernel(YArgs a, double *Y, int64_t ldy, int64_t colE, i
   const int lmin = a.lmin, lmax = a.lmax;
   double *rq = Y + rowQ + p;
   double *ru = Y + rowU + p;
-  for (int m = 0; m <= lmax; ++m) {
-    double sm, cm;
-    sincos((double)m * ph, &sm, &cm);
-    int l0 = m > 2 ? m : 2;
-    double pm1 = 0.0, p0 = wigner_start(m, 2, lc, ls, c, sn);    // d^l_{m,2}
-    double qm1 = 0.0, q0 = wigner_start(m, -2, lc, ls, c, sn);   // d^l_{m,-2}
-    for (int l = l0; l <= lmax; ++l) {
-      if (l >= lmin) {
-        const double nrm = sqrt((2.0 * l + 1.0) * kInv4Pi) * a.transfer_P[l];
-        const double F1 = -0.5 * nrm * (p0 + q0);
-        const double F2 = 0.5 * nrm * (q0 - p0);
-        const int64_t col = (int64_t)l * l - (int64_t)lmin * lmin;
-        if (m == 0) {
-          rq[(colE + col) * ldy] = F1;
-          ru[(colE + col) * ldy] = 0.0;
-          rq[(colB + col) * ldy] = 0.0;
-          ru[(colB + col) * ldy] = F1;
-        } else {
-          const double f1c = kSqrt2 * F1 * cm, f1s = kSqrt2 * F1 * sm;
-          const double f2c = kSqrt2 * F2 * cm, f2s = kSqrt2 * F2 * sm;
-          const int64_t ic = col + 2 * m - 1, is = col + 2 * m;
-          rq[(colE + ic) * ldy] = f1c;
-          ru[(colE + ic) * ldy] = -f2s;
-          rq[(colE + is) * ldy] = f1s;
-          ru[(colE + is) * ldy] = f2c;
-          rq[(colB + ic) * ldy] = f2s;
-          ru[(colB + ic) * ldy] = f1c;
-          rq[(colB + is) * ldy] = -f2c;
-          ru[(colB + is) * ldy] = f1s;
-        }
+  double sm, cm;
+  sincos((double)m * ph, &sm, &cm);
+  const RecCoef *tc = tab + (int64_t)m * L;
+  const int l0 = m > 2 ? m : 2;
+  double pm1 = 0.0, p0 = wigner_start(m, 2, lc, ls, c, sn);    // d^l_{m,2}
+  double qm1 = 0.0, q0 = wigner_start(m, -2, lc, ls, c, sn);   // d^l_{m,-2}
+  for (int l = l0; l <= lmax; ++l) {
+    if (l >= lmin) {
+      const double nrm = sqrt((2.0 * l + 1.0) * kInv4Pi) * a.transfer_P[l];
+      const double F1 = -0.5 * nrm * (p0 + q0);
+      const double F2 = 0.5 * nrm * (q0 - p0);
+      const int64_t col = (int64_t)l * l - (int64_t)lmin * lmin;
+      if (m == 0) {
+        rq[(colE + col) * ldy] = F1;
+        ru[(colE + col) * ldy] = 0.0;
+        rq[(colB + col) * ldy] = 0.0;
+        ru[(colB + col) * ldy] = F1;
+      } else {
+        const double f1c = kSqrt2 * F1 * cm, f1s = kSqrt2 * F1 * sm;
+        const double f2c = kSqrt2 * F2 * cm, f2s = kSqrt2 * F2 * sm;
+        const int64_t ic = col + 2 * m - 1, is = col + 2 * m;
+        rq[(colE + ic) * ldy] = f1c;
+        ru[(colE + ic) * ldy] = -f2s;
+        rq[(colE + is) * ldy] = f1s;
+        ru[(colE + is) * ldy] = f2c;
+        rq[(colB + ic) * ldy] = f2s;
+        ru[(colB + ic) * ldy] = f1c;
+        rq[(colB + is) * ldy] = -f2c;
+        ru[(colB + is) * ldy] = f1s;
       }
-      if (l < lmax) {
-        double pn = wigner_next(l, m, 2, x, pm1, p0);
-        double qn = wigner_next(l, m, -2, x, qm1, q0);
-        pm1 = p0;
-        p0 = pn;
-        qm1 = q0;
-        q0 = qn;
-      }
+    }
+    if (l < lmax) {
+      const RecCoef cc = tc[l];
+      const double ax = cc.a2 * x;
+      const double pn = (ax - cc.b2) * p0 - cc.g2 * pm1;
+      const double qn = (ax + cc.b2) * q0 - cc.g2 * qm1;
+      pm1 = p0;
+      p0 = pn;
+      qm1 = q0;
+      q0 = qn;
     }
   }
 }
@@ -174,12 +204,20 @@ void launch_ybuild(const YArgs &a, double *Y, int64_t ldy, cudaStream_t st) {
   const int k0 = (a.lmax + 1) * (a.lmax + 1) - a.lmin * a.lmin;
   const int nT = a.has_T ? a.npix_T : 0;
   const int nP = a.has_P ? a.npix_P : 0;
+  const int L = a.lmax + 1;
+  // recurrence coefficient table ((lmax+1)^2 entries) in the caller's workspace
+  RecCoef *tab = (RecCoef *)a.coef;
+  { rec_coef_kernel<<<(L * L + 255) / 256, 256, 0, st>>>(a.lmax, tab); count_launch(); }
   const int threads = 128;
-  if (nT > 0) { ybuild_T_kernel<<<(nT + threads - 1) / threads, threads, 0, st>>>(a, Y, ldy); count_launch(); }
+  if (nT > 0) {
+    const int64_t tot = (int64_t)nT * L;
+    { ybuild_T_kernel<<<(unsigned)((tot + threads - 1) / threads), threads, 0, st>>>(a, tab, Y, ldy); count_launch(); }
+  }
   if (nP > 0) {
     int64_t colE = a.has_T ? k0 : 0;
-    { ybuild_P_kernel<<<(nP + threads - 1) / threads, threads, 0, st>>>(
-        a, Y, ldy, colE, colE + k0, nT, (int64_t)nT + nP); count_launch(); }
+    const int64_t tot = (int64_t)nP * L;
+    { ybuild_P_kernel<<<(unsigned)((tot + threads - 1) / threads), threads, 0, st>>>(
+        a, tab, Y, ldy, colE, colE + k0, nT, (int64_t)nT + nP); count_launch(); }
   }
   if (nT > 0 && nP > 0) {
     // T rows x (E, B) columns and (Q, U) rows x T columns are structurally zero
@@ -258,6 +296,8 @@ __global__ void mix_lambda_kernel(double *Y, int64_t ldy, int n, int nc, int k0,
 }
 
 }  // namespace
+
+size_t ybuild_coef_bytes(int lmax) { return (size_t)(lmax + 1) * (lmax + 1) * sizeof(RecCoef); }
 
 void launch_lambda_factor(const double *cl, int lmin, int lmax, int nc, const int *comps,
                           double *lamL, cudaStream_t st) {

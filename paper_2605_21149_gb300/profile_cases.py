@@ -4,6 +4,8 @@
     python -m paper_2605_21149_gb300.profile_cases syrk_split  # the same, split precision
     python -m paper_2605_21149_gb300.profile_cases ybuild   # Y, 5952 x 6900
     python -m paper_2605_21149_gb300.profile_cases fisher   # one full qml_fisher
+    python -m paper_2605_21149_gb300.profile_cases step --precision 1
+        # one bench step: qml_fisher + qml_estimate (100 maps) + pix_loglike
 
 Each case runs its call `--reps` times (default 2) after one untimed call and
 prints the CUDA-event time per call.
@@ -19,12 +21,13 @@ def main():
     from . import api, build, synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=("syrk", "syrk_split", "ybuild", "fisher"))
+    ap.add_argument("case", choices=("syrk", "syrk_split", "ybuild", "fisher", "step"))
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--precision", type=int, default=0)
     args = ap.parse_args()
     build.build()
     wl = synth.workload(1)
-    prob = api.Problem.from_workload(wl)
+    prob = api.Problem.from_workload(wl, precision=args.precision)
     if args.case in ("syrk", "syrk_split"):
         X = torch.randn(wl.k, wl.n, dtype=torch.float64, device="cuda").t()
         W = torch.empty(wl.k, wl.k, dtype=torch.float64, device="cuda").t()
@@ -32,8 +35,21 @@ def main():
         fn = lambda: api.gemm(X, X, W, transA=True, lower=True, precision=prec)
     elif args.case == "ybuild":
         fn = lambda: api.ybuild(prob)
-    else:
+    elif args.case == "fisher":
         fn = lambda: api.fisher(prob, keep_plan=False)
+    else:
+        g = synth.rng(1, synth.P_SIMS)
+        alm = synth.draw_alm(wl.cl_fid, wl.lmin, wl.lmax, wl.comps, 100, g)
+        noise = synth.noise_draws(wl.G, 100, g)
+        td = lambda x: torch.as_tensor(x, device="cuda").t().contiguous().t()
+        maps = api.synthesize(prob, td(alm), td(noise))
+        cl = torch.as_tensor(wl.cl_fid.reshape(-1), device="cuda")
+
+        def fn():
+            F, plan = api.fisher(prob)
+            plan.estimate(maps)
+            api.loglike(prob, cl, maps[:, :1])
+            plan.free()
     fn()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -323,3 +323,26 @@ def gauss_legendre_grid(lmax: int):
     phi = np.tile(ph, lmax + 1)
     w = np.repeat(wx * (2.0 * np.pi / nphi), nphi)
     return theta, phi, w
+
+
+def batch_workload(nside: int = 16, lmax: int = 47, fskies=(0.5, 0.7, 0.9), rank: int = 200,
+                   ngrid: int = 64, config: int = 3):
+    """The parameter-scan workload: TQU masks at the given sky fractions (each
+    its own seeded rank-`rank` noise), and the (tau, r) grid of the scan,
+    tau in [0.03, 0.09] (the EE reionisation bump scales as tau^2), r in
+    [0, 0.1] (BB gains 0.1 r TT).  Item i = (grid point i, mask i mod nmask).
+    Returns (masks, taus, rs)."""
+    masks = []
+    for j, fs in enumerate(fskies):
+        masks.append(make_workload(f"TQU nside{nside} fsky{fs}", nside, lmax, True, True,
+                                   fsky_cut_deg(fs), SPEC_NAMES, rank, 10 * config + j))
+    tau = np.linspace(0.03, 0.09, ngrid)
+    r = np.linspace(0.0, 0.1, ngrid)
+    T, R = np.meshgrid(tau, r, indexing="ij")
+    return masks, T.reshape(-1), R.reshape(-1)
+
+
+def batch_item_spectra(lmax: int, taus, rs) -> np.ndarray:
+    """item_cl array (nitems, 6, lmax+1) for the scan grid."""
+    return np.stack([spectra(lmax, tau=t, r=r) for t, r in zip(taus, rs)])
+
