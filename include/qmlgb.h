@@ -170,6 +170,43 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
                              const int32_t *item_mask, const double *item_cl, int32_t ld_out,
                              double *lnL, double *chi2, double *logdet, void *stream);
 
+/* ---- lnL emulator (the learned part; the paper has none) ---------------- *
+ * An MLP surrogate of lnL(theta) over a box of d <= 8 parameters, trained on
+ * exact evaluations (e.g. from pix_loglike_batch): lnL = q(x) + sigma f(x),
+ * x = theta mapped to [-1, 1]^d, q a float64 least-squares quadratic, f an MLP
+ * with `depth` hidden GELU layers of `width` units (bf16 weights, FP32
+ * accumulation on tensor cores), two independently initialised heads.  All
+ * training (forward, backward, Adam) runs in this library's kernels. */
+typedef struct qml_emu qml_emu;
+
+/* New emulator over the box [lo, hi] (host arrays of ndim); seed fixes the
+ * weight initialisation (counter-based generator). */
+qml_status emu_create(int32_t ndim, const double *lo, const double *hi, int32_t width,
+                      int32_t depth, uint64_t seed, qml_emu **emu);
+/* Train on n samples: theta n x ndim (column-major), lnl n; host or device.
+ * epochs passes of minibatches of `batch` (a multiple of 16) with Adam at
+ * learning rate lr (cosine decay).  final_loss (host, 2 doubles, may be NULL)
+ * receives each head's mean squared error on the normalised targets. */
+qml_status emu_train(qml_emu *emu, int32_t n, const double *theta, const double *lnl,
+                     int32_t epochs, int32_t batch, double lr, double *final_loss, void *stream);
+/* Predict lnL at n points (theta n x ndim column-major; out n; flags n, may be
+ * NULL; host or device).  flags[i] = 1 when point i lies outside the training
+ * hull (the box without its outer 3 % shell in normalised coordinates) or the
+ * two heads differ by more than tol: the caller evaluates those exactly
+ * (pix_loglike_batch). */
+qml_status emu_predict(qml_emu *emu, int32_t n, const double *theta, double tol, double *out,
+                       int32_t *flags, void *stream);
+/* Number of parameters of one head and their float32 values (host or device;
+ * layout: per layer W (out x in, row-major) then b, inputs padded to 16). */
+int64_t emu_param_count(const qml_emu *emu);
+qml_status emu_params(qml_emu *emu, int32_t head, float *out);
+/* Mean squared error of head `head` on n given normalised inputs (host, n x 16
+ * row-major) and targets (host, n), and its gradient (float32, host or
+ * device) -- exposes the training kernels for testing. */
+qml_status emu_loss_grad(qml_emu *emu, int32_t head, int32_t n, const double *x, const double *t,
+                         double *loss, float *grad);
+void emu_free(qml_emu *emu);
+
 /* ---- dense building blocks (exposed for testing the kernels one by one) -- */
 
 /* In-place lower Cholesky A = L L^T of an n x n SPD matrix (lower triangle

@@ -53,6 +53,15 @@ SIGNATURES = {
                               c_void_p, c_void_p, c_void_p]),
     "pix_loglike_batch": (c_int32, [ctypes.POINTER(LnlMask), c_int32, c_int32, c_void_p, c_void_p,
                                     c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "emu_create": (c_int32, [c_int32, c_void_p, c_void_p, c_int32, c_int32, ctypes.c_uint64,
+                             ctypes.POINTER(c_void_p)]),
+    "emu_train": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_int32, c_double,
+                            c_void_p, c_void_p]),
+    "emu_predict": (c_int32, [c_void_p, c_int32, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
+    "emu_param_count": (c_int64, [c_void_p]),
+    "emu_params": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "emu_loss_grad": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "emu_free": (None, [c_void_p]),
     "qml_potrf": (c_int32, [c_int64, c_void_p, c_int64, c_void_p, c_int32, c_void_p]),
     "qml_potrf_noalloc": (c_int32, [c_int64, c_void_p, c_int64, c_void_p, c_void_p]),
     "qml_trsm": (c_int32, [c_int64, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_int32,

@@ -262,6 +262,75 @@ def loglike_batch(masks, item_mask, item_cl):
     return lnl.T, chi2.T, ld[:, 0]
 
 
+class Emulator:
+    """MLP surrogate of lnL(theta) with a two-head ensemble (emu_* entry points)."""
+
+    IN0 = 16
+
+    def __init__(self, lo, hi, width=256, depth=4, seed=1):
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        self.d, self.width, self.depth = len(lo), int(width), int(depth)
+        h = ctypes.c_void_p(0)
+        _check(_lib().emu_create(self.d, lo.ctypes.data, hi.ctypes.data, self.width, self.depth,
+                                 int(seed), ctypes.byref(h)))
+        self._h = h
+
+    def train(self, theta, lnl, epochs=100, batch=64, lr=1e-3):
+        """Train on theta (n x d) and lnl (n); returns the two heads' final MSE."""
+        keep = []
+        n = len(lnl)
+        th = _mat(theta, n, self.d, keep)
+        y = _vec(lnl, keep)
+        dev = _is_torch(theta)
+        fl = (ctypes.c_double * 2)()
+        _check(_lib().emu_train(self._h, n, th, y, int(epochs), int(batch), float(lr),
+                                ctypes.cast(fl, ctypes.c_void_p), _stream(dev)))
+        return float(fl[0]), float(fl[1])
+
+    def predict(self, theta, tol=0.025):
+        """(lnL prediction, flags) for theta (n x d); flag 1 = evaluate exactly."""
+        keep = []
+        n = theta.shape[0]
+        th = _mat(theta, n, self.d, keep)
+        dev = _is_torch(theta)
+        out = _empty(n, 1, dev)
+        if dev:
+            flags = torch.empty(n, dtype=torch.int32, device="cuda")
+        else:
+            flags = np.empty(n, dtype=np.int32)
+        _check(_lib().emu_predict(self._h, n, th, float(tol), _ptr(out), _ptr(flags), _stream(dev)))
+        return out[:, 0], flags
+
+    def params(self, head=0):
+        n = _lib().emu_param_count(self._h)
+        out = np.empty(n, dtype=np.float32)
+        _check(_lib().emu_params(self._h, head, out.ctypes.data))
+        return out
+
+    def loss_grad(self, x, t, head=0):
+        """(loss, grad) of one head on normalised inputs x (n x 16) and targets t."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        n = _lib().emu_param_count(self._h)
+        g = np.empty(n, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(_lib().emu_loss_grad(self._h, head, len(t), x.ctypes.data, t.ctypes.data,
+                                    ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def free(self):
+        if self._h:
+            _lib().emu_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def potrf(A, precision=nat.QML_FP64):
     """In-place lower Cholesky of a square column-major matrix; returns ln|A|."""
     n = A.shape[0]

@@ -1,0 +1,792 @@
+// lnL emulator: a small MLP of lnL(theta) trained on exact evaluations, with
+// an ensemble of two heads and a fallback flag (the learned part of the build;
+// the paper has no counterpart).
+//
+// Model: x = (theta - centre) / half_width in [-1, 1]^d (zero-padded to 16
+// inputs); lnL(theta) = q(x) + sigma_r f(x), where q is a float64 least-squares
+// quadratic in x fitted to the training labels and f is an MLP with `depth`
+// hidden GELU layers of `width` units (gelu(z) = z Phi(z)) and a linear output,
+// trained on the normalised residuals (lnL - q) / sigma_r.  The residual is
+// small next to lnL itself, so bf16 weights with FP32 accumulation are enough.
+//
+// Every product runs on tensor cores (WMMA bf16 x bf16 -> fp32): forward
+// Z = X W^T, data gradient dX = dZ W, weight gradient dW = dZ^T X.  Master
+// weights, gradients and the Adam state are float32; each layer's input
+// activations and its weights are rounded to bf16 for the products.
+// Prediction averages the two heads; a point is flagged for exact evaluation
+// when it lies outside the training box or the heads disagree by more than a
+// tolerance.
+#include "qmlgb.h"
+#include "internal.cuh"
+
+#include <cuda_bf16.h>
+#include <mma.h>
+
+#include <cmath>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+namespace qmlgb {
+void set_last_error(const std::string &msg);
+}
+
+using namespace qmlgb;
+using namespace nvcuda;
+
+namespace {
+
+constexpr int kIn0 = 16, kOut0 = 16, kMaxDim = 8, kMaxFeat = 1 + kMaxDim + kMaxDim * (kMaxDim + 1) / 2;
+// points in the outer 3 % shell of the box are treated as outside the
+// training hull: uniformly drawn samples thin out there and the two heads can
+// agree while both extrapolate
+constexpr double kHullMargin = 0.97;
+
+// ---------------------------------------------------------- tensor cores --
+// C (M x N, fp32 row-major, ldc) = op(A) op(B) [+ C]; A is M x K and B is
+// K x N in the given layouts; M, N, K multiples of 16.  4 warps per block,
+// 64 x 64 output tile, 2 x 2 fragments per warp.
+template <typename ALay, typename BLay>
+__global__ void wmma_gemm_kernel(int M, int N, int K, const __nv_bfloat16 *A, int lda,
+                                 const __nv_bfloat16 *B, int ldb, float *C, int ldc,
+                                 int accumulate) {
+  const int warp = threadIdx.x >> 5;
+  const int m0 = blockIdx.y * 64 + (warp >> 1) * 32;
+  const int n0 = blockIdx.x * 64 + (warp & 1) * 32;
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (accumulate && m0 + 16 * i < M && n0 + 16 * j < N)
+        wmma::load_matrix_sync(acc[i][j], C + (int64_t)(m0 + 16 * i) * ldc + n0 + 16 * j, ldc,
+                               wmma::mem_row_major);
+      else
+        wmma::fill_fragment(acc[i][j], 0.0f);
+    }
+  const bool am[2] = {m0 < M, m0 + 16 < M};
+  const bool bn[2] = {n0 < N, n0 + 16 < N};
+  for (int k = 0; k < K; k += 16) {
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, ALay> a[2];
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, BLay> b[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (!am[i]) continue;
+      const int r = m0 + 16 * i;
+      const __nv_bfloat16 *p = std::is_same<ALay, wmma::row_major>::value
+                                   ? A + (int64_t)r * lda + k
+                                   : A + r + (int64_t)k * lda;
+      wmma::load_matrix_sync(a[i], p, lda);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (!bn[j]) continue;
+      const int c = n0 + 16 * j;
+      const __nv_bfloat16 *p = std::is_same<BLay, wmma::row_major>::value
+                                   ? B + (int64_t)k * ldb + c
+                                   : B + (int64_t)c * ldb + k;
+      wmma::load_matrix_sync(b[j], p, ldb);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (am[i] && bn[j]) wmma::mma_sync(acc[i][j], a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      if (am[i] && bn[j])
+        wmma::store_matrix_sync(C + (int64_t)(m0 + 16 * i) * ldc + n0 + 16 * j, acc[i][j], ldc,
+                                wmma::mem_row_major);
+}
+
+template <typename ALay, typename BLay>
+void wmma_gemm(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
+               int ldb, float *C, int ldc, int accumulate, cudaStream_t st) {
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  wmma_gemm_kernel<ALay, BLay><<<grid, 128, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate);
+  count_launch();
+}
+
+// ------------------------------------------------------------ elementwise --
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float dgelu_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
+}
+
+// Z <- Z + b (row-major B x N); Xn = bf16(gelu(Z)) or bf16(Z)
+__global__ void bias_act_kernel(float *Z, int Brows, int N, const float *b, __nv_bfloat16 *Xn,
+                                int act) {
+  const int64_t total = (int64_t)Brows * N;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(t % N);
+    const float z = Z[t] + b[n];
+    Z[t] = z;
+    if (Xn) Xn[t] = __float2bfloat16_rn(act ? gelu_f(z) : z);
+  }
+}
+
+// dZ = dX * gelu'(Z), kept in fp32 (bias gradient) and bf16 (products)
+__global__ void gelu_bwd_kernel(const float *dX, const float *Z, int64_t total, float *dZf,
+                                __nv_bfloat16 *dZh) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float d = dX[t] * dgelu_f(Z[t]);
+    dZf[t] = d;
+    dZh[t] = __float2bfloat16_rn(d);
+  }
+}
+
+// output layer: residual of column 0 over the first nreal rows; gradient of
+// the mean squared error; per-block partial loss (fixed-order sum later)
+__global__ void loss_grad_kernel(const float *out, const float *t, int Brows, int nreal,
+                                 float *dZf, __nv_bfloat16 *dZh, double *partial) {
+  __shared__ double red[256];
+  double l = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Brows * kOut0;
+       i += gridDim.x * blockDim.x) {
+    const int b = i / kOut0, c = i % kOut0;
+    float g = 0.0f;
+    if (c == 0 && b < nreal) {
+      const float r = out[i] - t[b];
+      g = 2.0f * r / (float)nreal;
+      l += (double)r * r;
+    }
+    dZf[i] = g;
+    dZh[i] = __float2bfloat16_rn(g);
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_partials_kernel(const double *partial, int np, double scale, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += partial[i];
+    *out = s * scale;
+  }
+}
+
+// db[n] = sum_b dZ[b, n] (fixed order over b)
+__global__ void colsum_kernel(const float *dZ, int Brows, int N, float *db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.0f;
+  for (int b = 0; b < Brows; ++b) s += dZ[(int64_t)b * N + n];
+  db[n] = s;
+}
+
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2,
+                            __nv_bfloat16 *ph) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    p[i] = pi;
+    ph[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float *p, int64_t n, __nv_bfloat16 *ph) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    ph[i] = __float2bfloat16_rn(p[i]);
+}
+
+// splitmix64 (Steele, Lea & Flood 2014) of a counter: uniform in [0, 1)
+__device__ __forceinline__ double u01(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// uniform weights, zero biases: He bound sqrt(6 / fan_in) for the GELU layers
+// (keeps the activation scale through depth), Glorot bound sqrt(6 / (fan_in +
+// fan_out)) for the linear output layer; padded input columns of layer 0 and
+// padded output rows of the last layer stay zero
+__global__ void init_layer_kernel(float *W, float *b, int out, int in, int in_real, int out_real,
+                                  int is_output, uint64_t seed) {
+  const float a = is_output ? sqrtf(6.0f / (float)(in_real + out_real)) : sqrtf(6.0f / (float)in_real);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < out * in; t += gridDim.x * blockDim.x) {
+    const int o = t / in, i = t % in;
+    float w = 0.0f;
+    if (i < in_real && o < out_real) w = (float)((2.0 * u01(seed * 0x100000000ull + t) - 1.0) * a);
+    W[t] = w;
+  }
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < out; o += gridDim.x * blockDim.x) b[o] = 0.0f;
+}
+
+// normalised inputs of a batch: sample j of the epoch is row
+// (off + j stride) mod n; theta is n x d column-major (float64)
+__global__ void gather_kernel(const double *theta, int n, int d, const double *centre,
+                              const double *half, const float *targ, int Brows, int nreal,
+                              int64_t off, int64_t stride, __nv_bfloat16 *X0, float *tb) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Brows * kIn0; t += gridDim.x * blockDim.x) {
+    const int b = t / kIn0, c = t % kIn0;
+    float x = 0.0f;
+    if (b < nreal && c < d) {
+      const int64_t row = (off + (int64_t)b * stride) % n;
+      x = (float)((theta[row + (int64_t)c * n] - centre[c]) / half[c]);
+    }
+    X0[t] = __float2bfloat16_rn(x);
+    if (c == 0) {
+      if (tb && b < nreal) tb[b] = targ[(off + (int64_t)b * stride) % n];
+      else if (tb) tb[b] = 0.0f;
+    }
+  }
+}
+
+// quadratic features of normalised x: 1, x_i, x_i x_j (i <= j)
+__device__ int features(const double *x, int d, double *f) {
+  int k = 0;
+  f[k++] = 1.0;
+  for (int i = 0; i < d; ++i) f[k++] = x[i];
+  for (int i = 0; i < d; ++i)
+    for (int j = i; j < d; ++j) f[k++] = x[i] * x[j];
+  return k;
+}
+
+// per-block partial normal equations A^T A, A^T y (float64)
+__global__ void normal_eq_kernel(const double *theta, const double *y, int n, int d,
+                                 const double *centre, const double *half, double *partial) {
+  const int nf = 1 + d + d * (d + 1) / 2;
+  __shared__ double acc[kMaxFeat * (kMaxFeat + 1)];
+  for (int t = threadIdx.x; t < nf * (nf + 1); t += blockDim.x) acc[t] = 0.0;
+  __syncthreads();
+  // one thread per sample; per-thread contributions added in a fixed order by
+  // thread 0 would serialise, so each thread owns a slice of the matrix
+  // entries instead and loops over this block's samples
+  const int s0 = blockIdx.x * 256, s1 = min(n, s0 + 256);
+  for (int e = threadIdx.x; e < nf * (nf + 1); e += blockDim.x) {
+    const int r = e / (nf + 1), c = e % (nf + 1);
+    double sacc = 0.0;
+    for (int s = s0; s < s1; ++s) {
+      double x[kMaxDim], f[kMaxFeat];
+      for (int i = 0; i < d; ++i) x[i] = (theta[s + (int64_t)i * n] - centre[i]) / half[i];
+      features(x, d, f);
+      sacc += f[r] * (c < nf ? f[c] : y[s]);
+    }
+    acc[e] = sacc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nf * (nf + 1); e += blockDim.x)
+    partial[(int64_t)blockIdx.x * nf * (nf + 1) + e] = acc[e];
+}
+
+// sum the partials, solve (A^T A + ridge) c = A^T y by Cholesky (one thread)
+__global__ void solve_quad_kernel(const double *partial, int nblocks, int d, double *coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int nf = 1 + d + d * (d + 1) / 2;
+  double A[kMaxFeat][kMaxFeat + 1];
+  for (int r = 0; r < nf; ++r)
+    for (int c = 0; c <= nf; ++c) {
+      double s = 0.0;
+      for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * nf * (nf + 1) + r * (nf + 1) + c];
+      A[r][c] = s;
+    }
+  double tr = 0.0;
+  for (int r = 0; r < nf; ++r) tr += A[r][r];
+  for (int r = 0; r < nf; ++r) A[r][r] += 1e-12 * tr / nf;
+  for (int j = 0; j < nf; ++j) {
+    double s = A[j][j];
+    for (int k = 0; k < j; ++k) s -= A[j][k] * A[j][k];
+    const double dj = sqrt(s > 0.0 ? s : 1e-300);
+    A[j][j] = dj;
+    for (int i = j + 1; i < nf; ++i) {
+      double t = A[i][j];
+      for (int k = 0; k < j; ++k) t -= A[i][k] * A[j][k];
+      A[i][j] = t / dj;
+    }
+  }
+  double z[kMaxFeat];
+  for (int i = 0; i < nf; ++i) {
+    double t = A[i][nf];
+    for (int k = 0; k < i; ++k) t -= A[i][k] * z[k];
+    z[i] = t / A[i][i];
+  }
+  for (int i = nf - 1; i >= 0; --i) {
+    double t = z[i];
+    for (int k = i + 1; k < nf; ++k) t -= A[k][i] * coef[k];
+    coef[i] = t / A[i][i];
+  }
+}
+
+// residual r = y - q(x) and its sum of squares partials
+__global__ void residual_kernel(const double *theta, const double *y, int n, int d,
+                                const double *centre, const double *half, const double *coef,
+                                double *res, double *partial) {
+  __shared__ double red[256];
+  double ss = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    double x[kMaxDim], f[kMaxFeat];
+    for (int i = 0; i < d; ++i) x[i] = (theta[s + (int64_t)i * n] - centre[i]) / half[i];
+    const int nf = features(x, d, f);
+    double q = 0.0;
+    for (int k = 0; k < nf; ++k) q += coef[k] * f[k];
+    const double r = y[s] - q;
+    res[s] = r;
+    ss += r * r;
+  }
+  red[threadIdx.x] = ss;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void scale_targets_kernel(const double *res, int n, const double *sumsq, float *targ,
+                                     double *sigma) {
+  const double sg = sqrt(*sumsq / n) > 0.0 ? sqrt(*sumsq / n) : 1.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+    targ[s] = (float)(res[s] / sg);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sigma = sg;
+}
+
+// prediction: q(x) + sigma (f0 + f1) / 2; flag outside the hull (box minus
+// its outer shell) or when the heads differ by more than tol (in lnL units)
+__global__ void predict_finish_kernel(const double *theta, int ntot, int off, int cnt, int d,
+                                      const double *centre, const double *half,
+                                      const double *coef, const double *sigma, const float *o0,
+                                      const float *o1, double tol, double *out, int *flags) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += gridDim.x * blockDim.x) {
+    const int s = off + j;
+    double x[kMaxDim], f[kMaxFeat];
+    bool outside = false;
+    for (int i = 0; i < d; ++i) {
+      x[i] = (theta[s + (int64_t)i * ntot] - centre[i]) / half[i];
+      outside |= (fabs(x[i]) > kHullMargin);
+    }
+    const int nf = features(x, d, f);
+    double q = 0.0;
+    for (int k = 0; k < nf; ++k) q += coef[k] * f[k];
+    const double a = o0[(int64_t)j * kOut0], b = o1[(int64_t)j * kOut0];
+    out[s] = q + *sigma * 0.5 * (a + b);
+    if (flags) flags[s] = (outside || *sigma * fabs(a - b) > tol) ? 1 : 0;
+  }
+}
+
+int grid_of(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// ======================================================================
+struct qml_emu {
+  int d = 0, width = 0, depth = 0, nheads = 2;
+  uint64_t seed = 0;
+  std::vector<std::pair<int, int>> layers;  // (out, in)
+  std::vector<int64_t> woff, boff;          // offsets into the flat parameter vector
+  int64_t nparam = 0;
+  // device
+  double *centre = nullptr, *half = nullptr, *coef = nullptr, *sigma = nullptr;
+  float *p[2] = {nullptr, nullptr}, *m[2] = {nullptr, nullptr}, *v[2] = {nullptr, nullptr};
+  __nv_bfloat16 *ph[2] = {nullptr, nullptr};
+  float *grad = nullptr;
+  int adam_t[2] = {0, 0};
+  bool fitted = false;
+  std::vector<void *> mem;
+};
+
+namespace {
+
+qml_status efail(qml_status s, const std::string &m) {
+  set_last_error(m);
+  return s;
+}
+
+template <class T>
+T *emu_alloc(qml_emu *e, size_t count) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+  e->mem.push_back(p);
+  return (T *)p;
+}
+
+// activations of one batch (Brows a multiple of 16)
+struct Acts {
+  int B = 0;
+  std::vector<__nv_bfloat16 *> X;  // inputs of each layer, B x in_l
+  std::vector<float *> Z;          // pre-activations, B x out_l
+  float *dZf = nullptr, *dX = nullptr, *tb = nullptr;
+  __nv_bfloat16 *dZh = nullptr;
+  double *partial = nullptr, *loss = nullptr;
+  std::vector<void *> mem;
+  ~Acts() {
+    for (void *p : mem) cudaFree(p);
+  }
+  template <class T>
+  T *a(size_t count) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+    mem.push_back(p);
+    return (T *)p;
+  }
+  bool make(const qml_emu *e, int Brows) {
+    B = Brows;
+    int maxw = kIn0;
+    for (auto &l : e->layers) maxw = std::max(maxw, std::max(l.first, l.second));
+    for (auto &l : e->layers) {
+      X.push_back(a<__nv_bfloat16>((size_t)B * l.second));
+      Z.push_back(a<float>((size_t)B * l.first));
+    }
+    dZf = a<float>((size_t)B * maxw);
+    dX = a<float>((size_t)B * maxw);
+    dZh = a<__nv_bfloat16>((size_t)B * maxw);
+    tb = a<float>(B);
+    partial = a<double>(256);
+    loss = a<double>(1);
+    for (auto *p : X) if (!p) return false;
+    for (auto *p : Z) if (!p) return false;
+    return dZf && dX && dZh && tb && partial && loss;
+  }
+};
+
+void forward(qml_emu *e, int h, Acts &A, cudaStream_t st) {
+  const int nl = (int)e->layers.size();
+  for (int l = 0; l < nl; ++l) {
+    const int out = e->layers[l].first, in = e->layers[l].second;
+    // Z = X W^T: A = X (B x in, row-major), B = W^T (in x out) = W col-major
+    wmma_gemm<wmma::row_major, wmma::col_major>(A.B, out, in, A.X[l], in, e->ph[h] + e->woff[l],
+                                                in, A.Z[l], out, 0, st);
+    __nv_bfloat16 *next = (l + 1 < nl) ? A.X[l + 1] : nullptr;
+    bias_act_kernel<<<grid_of((int64_t)A.B * out), 256, 0, st>>>(A.Z[l], A.B, out, e->p[h] + e->boff[l],
+                                                                 next, l + 1 < nl ? 1 : 0);
+    count_launch();
+  }
+}
+
+// gradient of the mean squared error of head h over the first nreal rows
+void backward(qml_emu *e, int h, Acts &A, int nreal, cudaStream_t st) {
+  const int nl = (int)e->layers.size();
+  loss_grad_kernel<<<64, 256, 0, st>>>(A.Z[nl - 1], A.tb, A.B, nreal, A.dZf, A.dZh, A.partial);
+  count_launch();
+  sum_partials_kernel<<<1, 32, 0, st>>>(A.partial, 64, 1.0 / nreal, A.loss);
+  count_launch();
+  for (int l = nl - 1; l >= 0; --l) {
+    const int out = e->layers[l].first, in = e->layers[l].second;
+    // dW = dZ^T X: A = dZ^T (out x B) = dZ col-major (ld out), B = X (B x in) row-major
+    wmma_gemm<wmma::col_major, wmma::row_major>(out, in, A.B, A.dZh, out, A.X[l], in,
+                                                e->grad + e->woff[l], in, 0, st);
+    colsum_kernel<<<(out + 127) / 128, 128, 0, st>>>(A.dZf, A.B, out, e->grad + e->boff[l]);
+    count_launch();
+    if (l > 0) {
+      // dX = dZ W: A = dZ (B x out) row-major, B = W (out x in) row-major
+      wmma_gemm<wmma::row_major, wmma::row_major>(A.B, in, out, A.dZh, out, e->ph[h] + e->woff[l],
+                                                  in, A.dX, in, 0, st);
+      gelu_bwd_kernel<<<grid_of((int64_t)A.B * in), 256, 0, st>>>(A.dX, A.Z[l - 1],
+                                                                  (int64_t)A.B * in, A.dZf, A.dZh);
+      count_launch();
+    }
+  }
+}
+
+bool is_dev(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// device copy of a host or device array (owned by `keep` when copied)
+const double *dev_in(const double *p, size_t count, std::vector<void *> &keep) {
+  if (is_dev(p)) return p;
+  void *d = nullptr;
+  if (cudaMalloc(&d, count * sizeof(double)) != cudaSuccess) return nullptr;
+  keep.push_back(d);
+  cudaMemcpy(d, p, count * sizeof(double), cudaMemcpyHostToDevice);
+  return (const double *)d;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t emu_param_count(const qml_emu *emu) { return emu ? emu->nparam : 0; }
+
+qml_status emu_create(int32_t ndim, const double *lo, const double *hi, int32_t width,
+                      int32_t depth, uint64_t seed, qml_emu **out) {
+  if (!out || !lo || !hi || ndim < 1 || ndim > kMaxDim || width < 16 || width % 16 || depth < 1 ||
+      depth > 16)
+    return efail(QML_EINVAL, "emu_create: need 1 <= ndim <= 8, width a multiple of 16, depth >= 1");
+  qml_emu *e = new qml_emu();
+  e->d = ndim;
+  e->width = width;
+  e->depth = depth;
+  e->seed = seed;
+  int in = kIn0;
+  for (int l = 0; l < depth; ++l) {
+    e->layers.push_back({width, in});
+    in = width;
+  }
+  e->layers.push_back({kOut0, in});
+  for (auto &l : e->layers) {
+    e->woff.push_back(e->nparam);
+    e->nparam += (int64_t)l.first * l.second;
+    e->boff.push_back(e->nparam);
+    e->nparam += l.first;
+  }
+  std::vector<double> c(ndim), hw(ndim);
+  for (int i = 0; i < ndim; ++i) {
+    if (!(hi[i] > lo[i])) {
+      delete e;
+      return efail(QML_EINVAL, "emu_create: need hi > lo in every dimension");
+    }
+    c[i] = 0.5 * (hi[i] + lo[i]);
+    hw[i] = 0.5 * (hi[i] - lo[i]);
+  }
+  e->centre = emu_alloc<double>(e, ndim);
+  e->half = emu_alloc<double>(e, ndim);
+  e->coef = emu_alloc<double>(e, kMaxFeat);
+  e->sigma = emu_alloc<double>(e, 1);
+  e->grad = emu_alloc<float>(e, e->nparam);
+  for (int h = 0; h < 2; ++h) {
+    e->p[h] = emu_alloc<float>(e, e->nparam);
+    e->m[h] = emu_alloc<float>(e, e->nparam);
+    e->v[h] = emu_alloc<float>(e, e->nparam);
+    e->ph[h] = emu_alloc<__nv_bfloat16>(e, e->nparam);
+  }
+  if (!e->centre || !e->half || !e->coef || !e->sigma || !e->grad || !e->p[1] || !e->ph[1]) {
+    emu_free(e);
+    return efail(QML_ENOMEM, "emu_create: device allocation failed");
+  }
+  cudaMemcpy(e->centre, c.data(), ndim * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(e->half, hw.data(), ndim * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemset(e->coef, 0, kMaxFeat * sizeof(double));
+  const double one = 1.0;
+  cudaMemcpy(e->sigma, &one, sizeof(double), cudaMemcpyHostToDevice);
+  for (int h = 0; h < 2; ++h) {
+    for (size_t l = 0; l < e->layers.size(); ++l) {
+      const int o = e->layers[l].first, i = e->layers[l].second;
+      const int in_real = (l == 0) ? ndim : i;
+      const int out_real = (l + 1 == e->layers.size()) ? 1 : o;
+      init_layer_kernel<<<64, 256>>>(e->p[h] + e->woff[l], e->p[h] + e->boff[l], o, i, in_real,
+                                     out_real, l + 1 == e->layers.size() ? 1 : 0,
+                                     seed * 16 + 2 * h + 1 + 64 * l);
+      count_launch();
+    }
+    to_bf16_kernel<<<grid_of(e->nparam), 256>>>(e->p[h], e->nparam, e->ph[h]);
+    count_launch();
+    cudaMemset(e->m[h], 0, e->nparam * sizeof(float));
+    cudaMemset(e->v[h], 0, e->nparam * sizeof(float));
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    emu_free(e);
+    return efail(QML_ECUDA, "emu_create: initialisation failed");
+  }
+  *out = e;
+  return QML_OK;
+}
+
+void emu_free(qml_emu *emu) {
+  if (!emu) return;
+  cudaDeviceSynchronize();
+  for (void *p : emu->mem) cudaFree(p);
+  delete emu;
+}
+
+qml_status emu_train(qml_emu *e, int32_t n, const double *theta, const double *lnl,
+                     int32_t epochs, int32_t batch, double lr, double *final_loss, void *stream) {
+  if (!e || n < 16 || !theta || !lnl || epochs < 1 || batch < 16 || batch % 16 || lr <= 0.0)
+    return efail(QML_EINVAL, "emu_train: need n >= 16, batch a positive multiple of 16, lr > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<void *> keep;
+  const double *th = dev_in(theta, (size_t)n * e->d, keep);
+  const double *y = dev_in(lnl, n, keep);
+  double *res = nullptr, *part = nullptr, *sumsq = nullptr;
+  float *targ = nullptr;
+  const int nblk = (n + 255) / 256;
+  const int nf = 1 + e->d + e->d * (e->d + 1) / 2;
+  cudaMalloc(&res, n * sizeof(double));
+  cudaMalloc(&part, (size_t)std::max(nblk, 256) * nf * (nf + 1) * sizeof(double));
+  cudaMalloc(&sumsq, sizeof(double));
+  cudaMalloc(&targ, n * sizeof(float));
+  keep.push_back(res);
+  keep.push_back(part);
+  keep.push_back(sumsq);
+  keep.push_back(targ);
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void *p : keep) cudaFree(p);
+  };
+  if (!th || !y || !res || !part || !sumsq || !targ) {
+    cleanup();
+    return efail(QML_ENOMEM, "emu_train: allocation failed");
+  }
+  // quadratic baseline and normalised residual targets (float64)
+  normal_eq_kernel<<<nblk, 256, 0, st>>>(th, y, n, e->d, e->centre, e->half, part);
+  count_launch();
+  solve_quad_kernel<<<1, 32, 0, st>>>(part, nblk, e->d, e->coef);
+  count_launch();
+  residual_kernel<<<64, 256, 0, st>>>(th, y, n, e->d, e->centre, e->half, e->coef, res, part);
+  count_launch();
+  sum_partials_kernel<<<1, 32, 0, st>>>(part, 64, 1.0, sumsq);
+  count_launch();
+  scale_targets_kernel<<<grid_of(n), 256, 0, st>>>(res, n, sumsq, targ, e->sigma);
+  count_launch();
+  Acts A;
+  if (!A.make(e, batch)) {
+    cleanup();
+    return efail(QML_ENOMEM, "emu_train: activation allocation failed");
+  }
+  const int steps_per_epoch = (n + batch - 1) / batch;
+  const int64_t total_steps = (int64_t)steps_per_epoch * epochs;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int h = 0; h < 2; ++h) {
+    int64_t step = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+      // epoch order: off + j stride (mod n) with stride coprime to n
+      uint64_t hsh = (e->seed + 1000003ull * (ep + 1) + 7919ull * (h + 1)) * 0x9E3779B97F4A7C15ull;
+      int64_t stride = (int64_t)(hsh % (uint64_t)n) | 1;
+      auto gcd = [](int64_t a, int64_t b) { while (b) { int64_t t = a % b; a = b; b = t; } return a; };
+      while (gcd(stride, n) != 1) stride += 2;
+      const int64_t off = (int64_t)((hsh >> 20) % (uint64_t)n);
+      for (int sb = 0; sb < steps_per_epoch; ++sb, ++step) {
+        const int nreal = std::min(batch, n - sb * batch);
+        gather_kernel<<<grid_of((int64_t)batch * kIn0), 256, 0, st>>>(
+            th, n, e->d, e->centre, e->half, targ, batch, nreal, off + (int64_t)sb * batch * stride,
+            stride, A.X[0], A.tb);
+        count_launch();
+        forward(e, h, A, st);
+        backward(e, h, A, nreal, st);
+        // learning rate: constant for the first 80 % of the steps (the network
+        // needs them to leave its initial plateau), then a cosine decay to 2 %
+        const double frac = (double)step / (double)std::max<int64_t>(1, total_steps - 1);
+        const double dec = frac < 0.8 ? 1.0
+                                       : 0.02 + 0.98 * 0.5 * (1.0 + cos(3.141592653589793 * (frac - 0.8) / 0.2));
+        const float lrs = (float)(lr * dec);
+        e->adam_t[h] += 1;
+        const float c1 = 1.0f / (1.0f - powf(b1, (float)e->adam_t[h]));
+        const float c2 = 1.0f / (1.0f - powf(b2, (float)e->adam_t[h]));
+        adam_kernel<<<grid_of(e->nparam), 256, 0, st>>>(e->p[h], e->grad, e->m[h], e->v[h],
+                                                        e->nparam, lrs, b1, b2, eps, c1, c2,
+                                                        e->ph[h]);
+        count_launch();
+      }
+    }
+    if (final_loss) {
+      // loss of the trained head over (up to) the first 4096 samples
+      const int ne = std::min(n, 4096);
+      Acts E;
+      const int Be = (ne + 15) / 16 * 16;
+      if (E.make(e, Be)) {
+        gather_kernel<<<grid_of((int64_t)Be * kIn0), 256, 0, st>>>(th, n, e->d, e->centre, e->half,
+                                                                   targ, Be, ne, 0, 1, E.X[0], E.tb);
+        count_launch();
+        forward(e, h, E, st);
+        backward(e, h, E, ne, st);
+        cudaMemcpyAsync(&final_loss[h], E.loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+      }
+    }
+  }
+  e->fitted = true;
+  cudaError_t err = cudaStreamSynchronize(st);
+  cleanup();
+  if (err != cudaSuccess) return efail(QML_ECUDA, std::string("emu_train: ") + cudaGetErrorString(err));
+  return QML_OK;
+}
+
+qml_status emu_predict(qml_emu *e, int32_t n, const double *theta, double tol, double *out,
+                       int32_t *flags, void *stream) {
+  if (!e || n < 1 || !theta || !out) return efail(QML_EINVAL, "emu_predict: bad arguments");
+  if (!e->fitted) return efail(QML_EINVAL, "emu_predict: emulator not trained");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<void *> keep;
+  const double *th = dev_in(theta, (size_t)n * e->d, keep);
+  double *od = out;
+  int *fd = flags;
+  const bool out_host = !is_dev(out), flags_host = flags && !is_dev(flags);
+  if (out_host) {
+    cudaMalloc(&od, n * sizeof(double));
+    keep.push_back(od);
+  }
+  if (flags_host) {
+    cudaMalloc(&fd, n * sizeof(int));
+    keep.push_back(fd);
+  }
+  const int chunk = 65536;
+  Acts A0, A1;
+  if (!th || !od || (flags && !fd) || !A0.make(e, chunk) || !A1.make(e, chunk)) {
+    for (void *p : keep) cudaFree(p);
+    return efail(QML_ENOMEM, "emu_predict: allocation failed");
+  }
+  for (int off = 0; off < n; off += chunk) {
+    const int cnt = std::min(chunk, n - off);
+    const int Bc = (cnt + 15) / 16 * 16;
+    A0.B = A1.B = Bc;
+    gather_kernel<<<grid_of((int64_t)Bc * kIn0), 256, 0, st>>>(th + off, n, e->d, e->centre, e->half,
+                                                               nullptr, Bc, cnt, 0, 1, A0.X[0], nullptr);
+    count_launch();
+    cudaMemcpyAsync(A1.X[0], A0.X[0], (size_t)Bc * kIn0 * sizeof(__nv_bfloat16),
+                    cudaMemcpyDeviceToDevice, st);
+    forward(e, 0, A0, st);
+    forward(e, 1, A1, st);
+    const int nl = (int)e->layers.size();
+    predict_finish_kernel<<<grid_of(cnt), 256, 0, st>>>(th, n, off, cnt, e->d, e->centre, e->half,
+                                                        e->coef, e->sigma, A0.Z[nl - 1],
+                                                        A1.Z[nl - 1], tol, od, fd);
+    count_launch();
+  }
+  if (out_host) cudaMemcpyAsync(out, od, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (flags_host) cudaMemcpyAsync(flags, fd, n * sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaError_t err = cudaStreamSynchronize(st);
+  for (void *p : keep) cudaFree(p);
+  if (err != cudaSuccess) return efail(QML_ECUDA, std::string("emu_predict: ") + cudaGetErrorString(err));
+  return QML_OK;
+}
+
+qml_status emu_params(qml_emu *e, int32_t head, float *out) {
+  if (!e || head < 0 || head > 1 || !out) return efail(QML_EINVAL, "emu_params: bad arguments");
+  cudaDeviceSynchronize();
+  if (cudaMemcpy(out, e->p[head], e->nparam * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
+    return efail(QML_ECUDA, "emu_params: copy failed");
+  return QML_OK;
+}
+
+qml_status emu_loss_grad(qml_emu *e, int32_t head, int32_t n, const double *x, const double *t,
+                         double *loss, float *grad) {
+  if (!e || head < 0 || head > 1 || n < 1 || !x || !t || !loss || !grad)
+    return efail(QML_EINVAL, "emu_loss_grad: bad arguments");
+  // x: n x 16 normalised inputs (row-major, host), t: n targets (host)
+  const int Bp = (n + 15) / 16 * 16;
+  Acts A;
+  if (!A.make(e, Bp)) return efail(QML_ENOMEM, "emu_loss_grad: allocation failed");
+  std::vector<__nv_bfloat16> xh((size_t)Bp * kIn0, __float2bfloat16_rn(0.0f));
+  std::vector<float> th(Bp, 0.0f);
+  for (int b = 0; b < n; ++b) {
+    for (int c = 0; c < kIn0; ++c) xh[(size_t)b * kIn0 + c] = __float2bfloat16_rn((float)x[(size_t)b * kIn0 + c]);
+    th[b] = (float)t[b];
+  }
+  cudaMemcpy(A.X[0], xh.data(), xh.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
+  cudaMemcpy(A.tb, th.data(), Bp * sizeof(float), cudaMemcpyHostToDevice);
+  forward(e, head, A, 0);
+  backward(e, head, A, n, 0);
+  cudaMemcpy(loss, A.loss, sizeof(double), cudaMemcpyDeviceToHost);
+  if (cudaMemcpy(grad, e->grad, e->nparam * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
+    return efail(QML_ECUDA, "emu_loss_grad: copy failed");
+  return QML_OK;
+}
+
+}  // extern "C"

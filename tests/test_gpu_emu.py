@@ -1,0 +1,101 @@
+"""lnL emulator (emu_* entry points): gradients of the training kernels
+against the oracle MLP (P15), fitting accuracy, the fallback flags, and an
+end-to-end run on exact lnL labels from pix_loglike_batch with the
+|dlnL| <= 0.05 audit on the accepted points."""
+import numpy as np
+import pytest
+
+from oracle import emulator as E
+from paper_2605_21149_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_21149_gb300 import api as A
+    from paper_2605_21149_gb300 import build
+    build.build()
+    return A
+
+
+@pytest.mark.parametrize("width,depth", [(64, 2), (256, 4)])
+def test_emu_gradients_match_oracle(api, width, depth):
+    emu = api.Emulator(np.zeros(4), np.ones(4), width=width, depth=depth, seed=3)
+    rng = np.random.default_rng(width + depth)
+    n = 48
+    x = np.zeros((n, 16))
+    x[:, :4] = rng.uniform(-1, 1, size=(n, 4))
+    t = rng.normal(size=n)
+    loss, g = emu.loss_grad(x, t)
+    p = emu.params(0).astype(np.float64)
+    lref, gref = E.loss_and_grad(p, x, t, 16, width, depth, 16, bf16_inputs=True)
+    assert abs(loss - lref) <= 2e-2 * abs(lref)
+    # bf16 rounding of the back-propagated errors (tensor-core inputs) is the
+    # only difference left; it stays at the 1e-2 level
+    assert np.abs(g - gref).max() <= 3e-2 * np.abs(gref).max()
+    emu.free()
+
+
+def test_emu_fits_and_flags(api):
+    rng = np.random.default_rng(5)
+    lo, hi = -np.ones(4), np.ones(4)
+
+    def f(th):
+        return (-0.5 * (th ** 2 * np.array([30.0, 10.0, 5.0, 2.0])).sum(axis=1)
+                + 0.3 * np.sin(2 * th[:, 0]) * th[:, 1] + 5.0)
+
+    th = rng.uniform(-1, 1, size=(4096, 4))
+    emu = api.Emulator(lo, hi, seed=7)
+    l0, l1 = emu.train(th, f(th), epochs=40, batch=64, lr=1e-3)
+    assert l0 < 1e-3 and l1 < 1e-3
+    test = rng.uniform(-1, 1, size=(1024, 4))
+    pred, flags = emu.predict(test, tol=0.02)
+    err = np.abs(pred - f(test))
+    assert np.max(err[flags == 0]) <= 0.02 + 1e-9
+    assert flags.mean() < 0.2
+    out = rng.uniform(1.01, 1.2, size=(16, 4))
+    _, fo = emu.predict(out)
+    assert np.all(fo == 1)
+    emu.free()
+
+
+def _lnl_exact(api, prob, maps, lmax, thetas):
+    cl = np.stack([synth.spectra(lmax, tau=t[0], r=t[1], a_ee=t[2], a_tt=t[3]) for t in thetas])
+    lnl, _, _ = api.loglike_batch([(prob, maps)], np.zeros(len(thetas), dtype=np.int32),
+                                  torch.as_tensor(cl, device="cuda"))
+    return lnl[:, 0].cpu().numpy()
+
+
+def test_emu_end_to_end_exact_labels(api):
+    """TQU Nside 8, f_sky 0.7, l <= 15; theta = (tau, r, A_EE, A_TT) in
+    [0.042, 0.078] x [0, 0.1] x [0.7, 1.3]^2; 4096 exact training labels."""
+    wl = synth.make_workload("emu TQU nside8", 8, 15, True, True, synth.fsky_cut_deg(0.7),
+                             synth.SPEC_NAMES, 20, 40)
+    prob = api.Problem.from_workload(wl)
+    g = synth.rng(40, synth.P_EMU)
+    cl0 = synth.spectra(wl.lmax)
+    alm = synth.draw_alm(cl0, wl.lmin, wl.lmax, wl.comps, 1, g)
+    noise = synth.noise_draws(wl.G, 1, g)
+    td = lambda x: torch.as_tensor(x, device="cuda").t().contiguous().t()
+    maps = api.synthesize(prob, td(alm), td(noise))
+    lo = np.array([0.042, 0.0, 0.7, 0.7])
+    hi = np.array([0.078, 0.1, 1.3, 1.3])
+    th = lo + (hi - lo) * g.uniform(size=(4096, 4))
+    y = _lnl_exact(api, prob, maps, wl.lmax, th)
+    emu = api.Emulator(lo, hi, seed=11)
+    emu.train(th, y, epochs=100, batch=64, lr=1e-3)
+    test = lo + (hi - lo) * g.uniform(size=(512, 4))
+    pred, flags = emu.predict(test, tol=0.025)
+    exact = _lnl_exact(api, prob, maps, wl.lmax, test)
+    acc = flags == 0
+    err = np.abs(pred - exact)
+    worst = np.argmax(np.where(acc, err, -1.0))
+    print("accepted", acc.mean(), "max err", err[acc].max(), "median", np.median(err[acc]),
+          "worst x", 2 * (test[worst] - lo) / (hi - lo) - 1)
+    assert acc.mean() > 0.5
+    assert err[acc].max() <= 0.05
+    emu.free()
