@@ -74,6 +74,20 @@ def oracle_inputs(wl, nsims):
     return Y, qml.simulate(Y, alm, noise)
 
 
+def aggregate(t_local, steps, world, device=None):
+    """Whole-job rate over `world` replicas: every rank timed `steps` steps;
+    the slowest rank's time counts (max over ranks, after a barrier)."""
+    t = t_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        t = float(tt.item())
+    return world * steps / t, t
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -246,13 +260,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     c1 = lib.qml_launch_count()
     clocks = sampler.stop()
-    t = e0.elapsed_time(e1) * 1e-3
-    if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        t = float(tt.item())
-    value = world * args.steps / t
+    value, t = aggregate(e0.elapsed_time(e1) * 1e-3, args.steps, world, device="cuda")
 
     # ---- lnL evals/s (single map, fiducial spectra) and the dominant kernel
     lnl_rate = None
@@ -358,6 +366,37 @@ def run_ours(args):
         forms["qu_nside32"] = f3
         del p3s, maps3
         torch.cuda.empty_cache()
+        # batched likelihood scan: 64 items of the 64 x 64 (tau, r) grid over the
+        # f_sky 0.5 / 0.7 / 0.9 TQU Nside 16 masks (item i on mask i mod 3)
+        bmasks, btaus, brs = synth.batch_workload(nside=16, lmax=47)
+        nb_items = 64
+        sel = np.linspace(0, len(btaus) - 1, nb_items).astype(int)
+        bcl = torch.as_tensor(synth.batch_item_spectra(47, btaus[sel], brs[sel]), device="cuda")
+        bim = sel % len(bmasks)
+        bres = {"workload": "lnL scan: TQU Nside 16 l=2..47 (k=6900), masks f_sky 0.5/0.7/0.9 "
+                            "(n=4800/6336/8256), 1 map per mask, 64 (tau, r) items per call, "
+                            "mask setup included"}
+        for prec, name in ((1, "split_bf16"), (0, "fp64")):
+            bprobs = []
+            for j, wl_b in enumerate(bmasks):
+                pb = api.Problem.from_workload(wl_b, device=True, precision=prec)
+                gb = synth.rng(30 + j, synth.P_MAPS)
+                ab = synth.draw_alm(wl_b.cl_fid, wl_b.lmin, wl_b.lmax, wl_b.comps, 1, gb)
+                nzb = synth.noise_draws(wl_b.G, 1, gb)
+                bprobs.append((pb, api.synthesize(pb, td(ab), td(nzb))))
+            api.loglike_batch(bprobs, bim[:4], bcl[:4])
+            torch.cuda.synchronize()
+            eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            eb0.record()
+            api.loglike_batch(bprobs, bim, bcl)
+            eb1.record()
+            eb1.synchronize()
+            tb = eb0.elapsed_time(eb1) * 1e-3
+            bres[name] = {"value": nb_items / tb, "unit": "lnL evals/s", "ms_per_call": 1e3 * tb}
+            del bprobs
+            torch.cuda.empty_cache()
+        bres["split_speedup_vs_fp64"] = bres["split_bf16"]["value"] / bres["fp64"]["value"]
+        forms["lnl_batch"] = bres
         # the split kernel against the measured bf16 tensor peak: W = X^T X
         # (k=6900, n=5952), 36 digit products of 2 k(k+1)/2 n flops each
         X = torch.randn(wl.k, wl.n, dtype=torch.float64, device="cuda").t()
