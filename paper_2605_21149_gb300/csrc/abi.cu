@@ -289,6 +289,21 @@ void trsm_blocked(Call &c, const double *L, int64_t n, int64_t lda, const double
   }
 }
 
+// X <- L^-1 from X = I: the blocked forward substitution above restricted to
+// the columns that can be nonzero (block row j of L^-1 ends at column j+jb).
+void trinv_blocked(Call &c, const double *L, int64_t n, int64_t lda, const double *Linv,
+                   double *X, int64_t ldx) {
+  for (int64_t j = 0; j < n; j += kNB) {
+    const int64_t jb = (n - j) < kNB ? (n - j) : kNB;
+    const int64_t w = j + jb;
+    const double *Lb = Linv + (j / kNB) * kNB * kNB;
+    launch_dgemm(0, 0, jb, w, jb, 1.0, Lb, kNB, X + j, ldx, 0.0, X + j, ldx, 0, c.status, c.st);
+    if (w < n)
+      launch_dgemm(0, 0, n - w, w, jb, -1.0, L + w + j * lda, lda, X + j, ldx, 1.0, X + w, ldx, 0,
+                   c.status, c.st);
+  }
+}
+
 // C = Y Lambda(cl) Y^T + N (lower triangle) from a scratch Y buffer (n x k),
 // which is left holding G = Y L_Lambda.
 void build_C(Call &c, const Staged &s, const Dims &d, double *Y, double *C) {
@@ -364,7 +379,7 @@ void potrf_split(Call &c, Split &sp, double *A, int64_t n, int64_t lda, double *
     // explicit inverse of the diagonal block: solve L_jj X = I (float64)
     double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
     launch_set_identity(Xinv, kNBS, jb, c.st);
-    trsm_blocked(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, jb, kNBS);
+    trinv_blocked(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, kNBS);
     if (j + jb < n) {
       const int64_t m2 = n - j - jb;
       double *A21 = A + (j + jb) + j * lda;

@@ -15,14 +15,19 @@ namespace qmlgb {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 
-template <bool TA, bool TB>
+// RM x RN outputs per thread: a (16 RM) x (16 RN) tile per CTA.  Small
+// products take small tiles so that the grid still covers the SMs: with a
+// float64 pipe this narrow the per-SM rate, not the operand traffic, sets
+// the time, so spreading the work over more SMs is what pays.
+template <bool TA, bool TB, int RM, int RN>
 __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
                                                     const double *A, int64_t lda, const double *B,
                                                     int64_t ldb, double beta, double *C,
                                                     int64_t ldc, int lower,
                                                     const DevStatus *status) {
+  constexpr int BM = 16 * RM, BN = 16 * RN;
   if (status && *((volatile const int *)&status->code) != 0) return;
   const int64_t m0 = (int64_t)blockIdx.x * BM;
   const int64_t n0 = (int64_t)blockIdx.y * BN;
@@ -31,19 +36,27 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
   __shared__ double Bs[2][BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  double acc[RM][RN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < RN; ++j) acc[i][j] = 0.0;
 
-  double ra[4], rb[4];
+  // tile element r of this thread: (mm, kk) of the BK x BM slab of op(A)
+  auto a_at = [&](int r, int &mm, int &kk) {
+    if (!TA) { mm = tid % BM; kk = tid / BM + (256 / BM) * r; }
+    else { kk = tid & 15; mm = (tid >> 4) + 16 * r; }
+  };
+  auto b_at = [&](int r, int &nn, int &kk) {
+    if (!TB) { kk = tid & 15; nn = (tid >> 4) + 16 * r; }
+    else { nn = tid % BN; kk = tid / BN + (256 / BN) * r; }
+  };
+  double ra[RM], rb[RN];
   auto load_a = [&](int64_t k0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RM; ++r) {
       int mm, kk;
-      if (!TA) { mm = tid & 63; kk = (tid >> 6) + 4 * r; }
-      else { kk = tid & 15; mm = (tid >> 4) + 16 * r; }
+      a_at(r, mm, kk);
       int64_t gm = m0 + mm, gk = k0 + kk;
       double v = 0.0;
       if (gm < M && gk < K) v = TA ? A[gk + gm * lda] : A[gm + gk * lda];
@@ -52,19 +65,17 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
   };
   auto store_a = [&](int buf) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RM; ++r) {
       int mm, kk;
-      if (!TA) { mm = tid & 63; kk = (tid >> 6) + 4 * r; }
-      else { kk = tid & 15; mm = (tid >> 4) + 16 * r; }
+      a_at(r, mm, kk);
       As[buf][kk][mm] = ra[r];
     }
   };
   auto load_b = [&](int64_t k0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RN; ++r) {
       int nn, kk;
-      if (!TB) { kk = tid & 15; nn = (tid >> 4) + 16 * r; }
-      else { nn = tid & 63; kk = (tid >> 6) + 4 * r; }
+      b_at(r, nn, kk);
       int64_t gn = n0 + nn, gk = k0 + kk;
       double v = 0.0;
       if (gn < N && gk < K) v = TB ? B[gn + gk * ldb] : B[gk + gn * ldb];
@@ -73,10 +84,9 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
   };
   auto store_b = [&](int buf) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RN; ++r) {
       int nn, kk;
-      if (!TB) { kk = tid & 15; nn = (tid >> 4) + 16 * r; }
-      else { nn = tid & 63; kk = (tid >> 6) + 4 * r; }
+      b_at(r, nn, kk);
       Bs[buf][kk][nn] = rb[r];
     }
   };
@@ -97,15 +107,15 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
     }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[RM], b[RN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tx + 16 * i];
+      for (int i = 0; i < RM; ++i) a[i] = As[buf][kk][tx + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][ty + 16 * j];
+      for (int j = 0; j < RN; ++j) b[j] = Bs[buf][kk][ty + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     if (t + 1 < nk) {
       store_a(buf ^ 1);
@@ -114,11 +124,11 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RM; ++i) {
     const int64_t gm = m0 + tx + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RN; ++j) {
       const int64_t gn = n0 + ty + 16 * j;
       if (gn >= N) continue;
       if (lower && gm < gn) continue;
@@ -133,20 +143,22 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
 // ------------------------------------------------ diagonal-block Cholesky --
 // The factor L lives in the lower triangle of the shared tile a; its inverse
 // is written into the strict upper triangle (inv[i][j] at a[j][i], i > j)
-// and its diagonal into invd, so one 64 x 65 tile (33 KB) holds both.
-// Column-parallel forward substitution: 256 threads = 64 columns x 4 partial
-// sums; every lane reaches the shuffles (inactive columns contribute zero).
-__device__ __forceinline__ double inv_at(double (*a)[kNB + 1], const double *invd, int k, int c) {
+// and the reciprocals of its diagonal into invd, so one tile holds both.
+// Row stride kLDA = 68 doubles: four consecutive rows x four consecutive
+// columns land in sixteen different 8-byte bank pairs.
+constexpr int kLDA = kNB + 4;
+
+__device__ __forceinline__ double inv_at(double (*a)[kLDA], const double *invd, int k, int c) {
   return k == c ? invd[c] : a[c][k];
 }
 
-// (float64 division is expensive on this part: one reciprocal per diagonal
-// entry, reused by every product)
-__device__ void invert_lower_shared(double (*a)[kNB + 1], double *invd, int jb) {
+// Column-parallel forward substitution L X = I: four lanes per column of X,
+// all eight columns of a warp in one warp, so the recurrence over rows only
+// needs the warp to be in step (every lane reaches the shuffles; inactive
+// columns contribute zero).  invd must hold 1 / L_cc on entry.
+__device__ void invert_lower_shared(double (*a)[kLDA], const double *invd, int jb) {
   const int tid = threadIdx.x;
   const int col = tid >> 2, part = tid & 3;
-  if (col < jb && part == 0) invd[col] = 1.0 / a[col][col];
-  __syncthreads();
   for (int i = 1; i < jb; ++i) {
     double s = 0.0;
     if (col < i)
@@ -154,22 +166,28 @@ __device__ void invert_lower_shared(double (*a)[kNB + 1], double *invd, int jb) 
     s += __shfl_down_sync(0xffffffffu, s, 2, 4);
     s += __shfl_down_sync(0xffffffffu, s, 1, 4);
     if (col < i && part == 0) a[col][i] = -s * invd[i];
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
 }
 
 // One CTA factors a jb x jb (jb <= 64) diagonal block in shared memory:
 // right-looking unblocked Cholesky with a pivot check, then the inverse of
 // the lower factor.  With factor == 0 the block already holds L and only the
 // inverse is formed (blockIdx.x selects the block: j0 = blockIdx.x * kNB).
+//
+// Column c of the working tile stays unscaled: the rank-1 update subtracts
+// a_ic a_jc / d_c with d_c = a_cc, and r_c = d_c^-1/2 (pivot check included)
+// is computed by the thread that makes the last change to a_cc, one column
+// ahead, so each column costs one barrier; L = a r_c column by column at
+// the end, and r_c doubles as 1 / L_cc for the inverse.
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda, int64_t n,
                                                          int64_t j0, double *Linv,
                                                          double *logdet_part,
                                                          DevStatus *status, int factor) {
-  __shared__ double a[kNB][kNB + 1];
+  __shared__ double a[kNB][kLDA];
   __shared__ double invd[kNB];
-  __shared__ double rpiv;
-  __shared__ int bad;
+  __shared__ double lg[kNB];
   const int tid = threadIdx.x;
   if (status && *((volatile int *)&status->code) != 0) return;
   if (!factor) {
@@ -178,53 +196,51 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
     Linv += (int64_t)blockIdx.x * kNB * kNB;
   }
   const int jb = (int)((n - j0) < kNB ? (n - j0) : kNB);
-  if (tid == 0) bad = 0;
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {
     int i = t % kNB, j = t / kNB;
     a[i][j] = (i < jb && j < jb && i >= j) ? A[i + j * lda] : 0.0;
   }
   __syncthreads();
   if (factor) {
+    if (tid == 0) invd[0] = rsqrt(a[0][0]);
+    __syncthreads();
+    const int row = tid >> 2, part = tid & 3;
     for (int c = 0; c < jb; ++c) {
-      if (tid == 0) {
-        double piv = a[c][c];
-        if (!(piv > 0.0) || !isfinite(piv)) {
-          bad = 1;
+      const double r = invd[c];
+      if (!(r > 0.0) || !isfinite(r)) {  // a_cc <= 0, infinite or NaN: uniform exit
+        if (tid == 0) {
           status->info = (int)(j0 + c + 1);
           atomicExch(&status->code, 2 /* QML_ENOTSPD */);
-        } else {
-          const double d = sqrt(piv);
-          a[c][c] = d;
-          rpiv = 1.0 / d;
         }
+        return;
       }
-      __syncthreads();
-      if (bad) return;
-      const double r = rpiv;
-      for (int i = c + 1 + tid; i < jb; i += blockDim.x) a[i][c] *= r;
-      __syncthreads();
-      // trailing rank-1 update: row i = c+1+(tid % 64), columns strided by 4
-      {
-        const int i = c + 1 + (tid & 63);
-        if (i < jb) {
-          const double aic = a[i][c];
-          for (int j = c + 1 + (tid >> 6); j <= i; j += 4) a[i][j] = fma(-aic, a[j][c], a[i][j]);
-        }
+      const int i = c + 1 + row;
+      if (i < jb) {
+        const double li = a[i][c] * (r * r);
+        for (int j = c + 1 + part; j <= i; j += 4) a[i][j] = fma(-li, a[j][c], a[i][j]);
+        if (tid == 0) invd[c + 1] = rsqrt(a[c + 1][c + 1]);  // thread 0 owns (c+1, c+1)
       }
       __syncthreads();
     }
     for (int t = tid; t < jb * jb; t += blockDim.x) {
       int i = t % jb, j = t / jb;
-      if (i >= j) A[i + j * lda] = a[i][j];
+      if (i >= j) {
+        const double v = a[i][j] * invd[j];
+        a[i][j] = v;
+        A[i + j * lda] = v;
+      }
     }
+    __syncthreads();
     // logs in parallel, summed in a fixed order
-    if (tid < jb) invd[tid] = log(a[tid][tid]);
+    if (tid < jb) lg[tid] = log(a[tid][tid]);
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int c = 0; c < jb; ++c) s += invd[c];
+      for (int c = 0; c < jb; ++c) s += lg[c];
       *logdet_part = 2.0 * s;
     }
+  } else {
+    if (tid < jb) invd[tid] = 1.0 / a[tid][tid];
     __syncthreads();
   }
   invert_lower_shared(a, invd, jb);
@@ -320,19 +336,80 @@ int grid_for(int64_t total) {
 
 }  // namespace
 
+namespace {
+
+// number of CTAs that do work for a bm x bn tiling
+int64_t dgemm_ctas(int64_t M, int64_t N, int bm, int bn, int lower) {
+  const int64_t gx = (M + bm - 1) / bm, gy = (N + bn - 1) / bn;
+  if (!lower) return gx * gy;
+  int64_t n = 0;
+  for (int64_t y = 0; y < gy; ++y) {
+    const int64_t first = (y * bn) / bm;  // first x with x*bm + bm - 1 >= y*bn
+    n += gx - (first > gx ? gx : first);
+  }
+  return n;
+}
+
+template <bool TA, bool TB, int RM, int RN>
+void dgemm_go(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+              const double *B, int64_t ldb, double beta, double *C, int64_t ldc, int lower,
+              const DevStatus *status, cudaStream_t st) {
+  dim3 grid((unsigned)((M + 16 * RM - 1) / (16 * RM)), (unsigned)((N + 16 * RN - 1) / (16 * RN)));
+  dgemm_kernel<TA, TB, RM, RN><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                     lower, status);
+  count_launch();
+}
+
+template <bool TA, bool TB>
+void dgemm_tile(int rm, int rn, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                int lower, const DevStatus *status, cudaStream_t st) {
+#define QMLGB_DG(R1, R2)                                                                      \
+  if (rm == R1 && rn == R2) {                                                                 \
+    dgemm_go<TA, TB, R1, R2>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st); \
+    return;                                                                                   \
+  }
+  QMLGB_DG(4, 4) QMLGB_DG(2, 2) QMLGB_DG(1, 1) QMLGB_DG(1, 4) QMLGB_DG(2, 4) QMLGB_DG(4, 1)
+  QMLGB_DG(4, 2)
+#undef QMLGB_DG
+}
+
+}  // namespace
+
+// Tile choice: the largest tile whose grid still gives every SM two CTAs,
+// else the smallest.  In-place products keep what makes them safe: C == A
+// (C's rows read only by their own CTA) needs the whole of N in one tile,
+// C == B the whole of M; callers only alias with N (resp. M) <= 64.
 void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                   double *C, int64_t ldc, int lower, const DevStatus *status, cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN));
-  if (!ta && !tb)
-    { dgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status); count_launch(); }
-  else if (!ta && tb)
-    { dgemm_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status); count_launch(); }
-  else if (ta && !tb)
-    { dgemm_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status); count_launch(); }
-  else
-    { dgemm_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status); count_launch(); }
+  static const int cand[7][2] = {{4, 4}, {2, 4}, {4, 2}, {2, 2}, {1, 4}, {4, 1}, {1, 1}};
+  const bool aliasA = (C == A), aliasB = (C == B);
+  const int64_t want = 2 * 152;
+  int rm = 4, rn = 4;
+  int64_t best = -1;
+  for (int i = 0; i < 7; ++i) {
+    const int r1 = cand[i][0], r2 = cand[i][1];
+    if (aliasA && r2 != 4) continue;
+    if (aliasB && r1 != 4) continue;
+    const int64_t n = dgemm_ctas(M, N, 16 * r1, 16 * r2, lower);
+    if (n >= want) {  // candidates run from the largest tile down
+      rm = r1;
+      rn = r2;
+      best = n;
+      break;
+    }
+    if (n > best) {
+      best = n;
+      rm = r1;
+      rn = r2;
+    }
+  }
+  if (!ta && !tb) dgemm_tile<false, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  else if (!ta && tb) dgemm_tile<false, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  else if (ta && !tb) dgemm_tile<true, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  else dgemm_tile<true, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
 }
 
 void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,
