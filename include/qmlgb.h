@@ -173,7 +173,8 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
 /* ---- lnL emulator (the learned part; the paper has none) ---------------- *
  * An MLP surrogate of lnL(theta) over a box of d <= 8 parameters, trained on
  * exact evaluations (e.g. from pix_loglike_batch): lnL = q(x) + sigma f(x),
- * x = theta mapped to [-1, 1]^d, q a float64 least-squares quadratic, f an MLP
+ * x = theta mapped to [-1, 1]^d, q a float64 least-squares polynomial (cubic
+ * for d <= 5, quadratic above), f an MLP
  * with `depth` hidden GELU layers of `width` units (bf16 weights, FP32
  * accumulation on tensor cores), two independently initialised heads.  All
  * training (forward, backward, Adam) runs in this library's kernels. */
@@ -185,17 +186,28 @@ qml_status emu_create(int32_t ndim, const double *lo, const double *hi, int32_t 
                       int32_t depth, uint64_t seed, qml_emu **emu);
 /* Train on n samples: theta n x ndim (column-major), lnl n; host or device.
  * epochs passes of minibatches of `batch` (a multiple of 16) with Adam at
- * learning rate lr (cosine decay).  final_loss (host, 2 doubles, may be NULL)
- * receives each head's mean squared error on the normalised targets. */
+ * learning rate lr (constant, then a cosine decay over the last 20 % of the
+ * steps).  When n >= 512 a seeded eighth of the samples is held out of
+ * training; after training the two heads' disagreement and prediction error
+ * on them calibrate the fallback threshold of emu_predict.  final_loss (host,
+ * 2 doubles, may be NULL) receives each head's mean squared error on the
+ * normalised targets of the training samples. */
 qml_status emu_train(qml_emu *emu, int32_t n, const double *theta, const double *lnl,
                      int32_t epochs, int32_t batch, double lr, double *final_loss, void *stream);
 /* Predict lnL at n points (theta n x ndim column-major; out n; flags n, may be
  * NULL; host or device).  flags[i] = 1 when point i lies outside the training
  * hull (the box without its outer 3 % shell in normalised coordinates) or the
- * two heads differ by more than tol: the caller evaluates those exactly
+ * two heads differ by more than a threshold derived from the accuracy target
+ * tol (|delta lnL|): tol / 2, lowered below the smallest held-out disagreement
+ * at which a held-out point (or one of lower disagreement) missed by more
+ * than 0.8 tol.  The caller evaluates flagged points exactly
  * (pix_loglike_batch). */
 qml_status emu_predict(qml_emu *emu, int32_t n, const double *theta, double tol, double *out,
                        int32_t *flags, void *stream);
+/* The head-disagreement threshold emu_predict applies for accuracy target
+ * tol (host outputs; nheld, may be NULL, receives the number of held-out
+ * points inside the hull that calibrated it). */
+qml_status emu_threshold(const qml_emu *emu, double tol, double *thr, int32_t *nheld);
 /* Number of parameters of one head and their float32 values (host or device;
  * layout: per layer W (out x in, row-major) then b, inputs padded to 16). */
 int64_t emu_param_count(const qml_emu *emu);
@@ -222,7 +234,7 @@ qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, doubl
 
 /* C <- alpha op(A) op(B) + beta C, op(X) = X or X^T (trans flags 0/1),
  * op(A) m x kk, op(B) kk x nn, C m x nn.  lower != 0 writes only the lower
- * triangle (i >= j) of a square C. */
+ * triangle (i >= j) of a square C.  C must not overlap A or B. */
 qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64_t kk,
                     double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
                     double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,

@@ -59,6 +59,7 @@ SIGNATURES = {
                             c_void_p, c_void_p]),
     "emu_predict": (c_int32, [c_void_p, c_int32, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "emu_param_count": (c_int64, [c_void_p]),
+    "emu_threshold": (c_int32, [c_void_p, c_double, c_void_p, c_void_p]),
     "emu_params": (c_int32, [c_void_p, c_int32, c_void_p]),
     "emu_loss_grad": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "emu_free": (None, [c_void_p]),

@@ -288,8 +288,9 @@ class Emulator:
                                 ctypes.cast(fl, ctypes.c_void_p), _stream(dev)))
         return float(fl[0]), float(fl[1])
 
-    def predict(self, theta, tol=0.025):
-        """(lnL prediction, flags) for theta (n x d); flag 1 = evaluate exactly."""
+    def predict(self, theta, tol=0.05):
+        """(lnL prediction, flags) for theta (n x d); tol is the accuracy target
+        |dlnL| that sets the fallback threshold; flag 1 = evaluate exactly."""
         keep = []
         n = theta.shape[0]
         th = _mat(theta, n, self.d, keep)
@@ -301,6 +302,13 @@ class Emulator:
             flags = np.empty(n, dtype=np.int32)
         _check(_lib().emu_predict(self._h, n, th, float(tol), _ptr(out), _ptr(flags), _stream(dev)))
         return out[:, 0], flags
+
+    def threshold(self, tol=0.05):
+        """(disagreement threshold, held-out points used) for accuracy target tol."""
+        thr = ctypes.c_double(0.0)
+        nh = ctypes.c_int32(0)
+        _check(_lib().emu_threshold(self._h, float(tol), ctypes.byref(thr), ctypes.byref(nh)))
+        return thr.value, nh.value
 
     def params(self, head=0):
         n = _lib().emu_param_count(self._h)

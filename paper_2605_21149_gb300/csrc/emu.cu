@@ -4,7 +4,8 @@
 //
 // Model: x = (theta - centre) / half_width in [-1, 1]^d (zero-padded to 16
 // inputs); lnL(theta) = q(x) + sigma_r f(x), where q is a float64 least-squares
-// quadratic in x fitted to the training labels and f is an MLP with `depth`
+// polynomial in x (cubic for d <= 5, else quadratic) fitted to the training
+// labels and f is an MLP with `depth`
 // hidden GELU layers of `width` units (gelu(z) = z Phi(z)) and a linear output,
 // trained on the normalised residuals (lnL - q) / sigma_r.  The residual is
 // small next to lnL itself, so bf16 weights with FP32 accumulation are enough.
@@ -22,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <mma.h>
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <string>
@@ -36,7 +38,13 @@ using namespace nvcuda;
 
 namespace {
 
-constexpr int kIn0 = 16, kOut0 = 16, kMaxDim = 8, kMaxFeat = 1 + kMaxDim + kMaxDim * (kMaxDim + 1) / 2;
+constexpr int kIn0 = 16, kOut0 = 16, kMaxDim = 8;
+// baseline polynomial: cubic up to kCubicDim parameters, quadratic above
+constexpr int kCubicDim = 5;
+__host__ __device__ constexpr int nfeat(int d) {
+  return 1 + d + d * (d + 1) / 2 + (d <= kCubicDim ? d * (d + 1) * (d + 2) / 6 : 0);
+}
+constexpr int kMaxFeat = nfeat(kCubicDim) > nfeat(kMaxDim) ? nfeat(kCubicDim) : nfeat(kMaxDim);
 // points in the outer 3 % shell of the box are treated as outside the
 // training hull: uniformly drawn samples thin out there and the two heads can
 // agree while both extrapolate
@@ -251,20 +259,25 @@ __global__ void gather_kernel(const double *theta, int n, int d, const double *c
   }
 }
 
-// quadratic features of normalised x: 1, x_i, x_i x_j (i <= j)
+// polynomial features of normalised x: 1, x_i, x_i x_j (i <= j) and, for
+// d <= kCubicDim, x_i x_j x_l (i <= j <= l)
 __device__ int features(const double *x, int d, double *f) {
   int k = 0;
   f[k++] = 1.0;
   for (int i = 0; i < d; ++i) f[k++] = x[i];
   for (int i = 0; i < d; ++i)
     for (int j = i; j < d; ++j) f[k++] = x[i] * x[j];
+  if (d <= kCubicDim)
+    for (int i = 0; i < d; ++i)
+      for (int j = i; j < d; ++j)
+        for (int l = j; l < d; ++l) f[k++] = x[i] * x[j] * x[l];
   return k;
 }
 
 // per-block partial normal equations A^T A, A^T y (float64)
 __global__ void normal_eq_kernel(const double *theta, const double *y, int n, int d,
                                  const double *centre, const double *half, double *partial) {
-  const int nf = 1 + d + d * (d + 1) / 2;
+  const int nf = nfeat(d);
   __shared__ double acc[kMaxFeat * (kMaxFeat + 1)];
   for (int t = threadIdx.x; t < nf * (nf + 1); t += blockDim.x) acc[t] = 0.0;
   __syncthreads();
@@ -291,7 +304,7 @@ __global__ void normal_eq_kernel(const double *theta, const double *y, int n, in
 // sum the partials, solve (A^T A + ridge) c = A^T y by Cholesky (one thread)
 __global__ void solve_quad_kernel(const double *partial, int nblocks, int d, double *coef) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int nf = 1 + d + d * (d + 1) / 2;
+  const int nf = nfeat(d);
   double A[kMaxFeat][kMaxFeat + 1];
   for (int r = 0; r < nf; ++r)
     for (int c = 0; c <= nf; ++c) {
@@ -360,11 +373,12 @@ __global__ void scale_targets_kernel(const double *res, int n, const double *sum
 }
 
 // prediction: q(x) + sigma (f0 + f1) / 2; flag outside the hull (box minus
-// its outer shell) or when the heads differ by more than tol (in lnL units)
+// its outer shell) or when the heads differ by more than thr (in lnL units)
 __global__ void predict_finish_kernel(const double *theta, int ntot, int off, int cnt, int d,
                                       const double *centre, const double *half,
                                       const double *coef, const double *sigma, const float *o0,
-                                      const float *o1, double tol, double *out, int *flags) {
+                                      const float *o1, double thr, double *out, int *flags,
+                                      double *dis) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += gridDim.x * blockDim.x) {
     const int s = off + j;
     double x[kMaxDim], f[kMaxFeat];
@@ -378,7 +392,9 @@ __global__ void predict_finish_kernel(const double *theta, int ntot, int off, in
     for (int k = 0; k < nf; ++k) q += coef[k] * f[k];
     const double a = o0[(int64_t)j * kOut0], b = o1[(int64_t)j * kOut0];
     out[s] = q + *sigma * 0.5 * (a + b);
-    if (flags) flags[s] = (outside || *sigma * fabs(a - b) > tol) ? 1 : 0;
+    const double dab = *sigma * fabs(a - b);
+    if (flags) flags[s] = (outside || dab > thr) ? 1 : 0;
+    if (dis) dis[s] = dab;
   }
 }
 
@@ -404,6 +420,9 @@ struct qml_emu {
   float *grad = nullptr;
   int adam_t[2] = {0, 0};
   bool fitted = false;
+  // held-out labels, sorted by head disagreement: disagreement and the
+  // running maximum of the prediction error up to it
+  std::vector<double> val_dis, val_maxerr;
   std::vector<void *> mem;
 };
 
@@ -519,6 +538,64 @@ const double *dev_in(const double *p, size_t count, std::vector<void *> &keep) {
   return (const double *)d;
 }
 
+// Predictions (and flags / disagreements when given) at n device points.
+qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *od, int *fd,
+                       double *dis, cudaStream_t st) {
+  const int chunk = 65536;
+  Acts A0, A1;
+  if (!A0.make(e, std::min(chunk, (n + 15) / 16 * 16)) ||
+      !A1.make(e, std::min(chunk, (n + 15) / 16 * 16)))
+    return QML_ENOMEM;
+  for (int off = 0; off < n; off += chunk) {
+    const int cnt = std::min(chunk, n - off);
+    const int Bc = (cnt + 15) / 16 * 16;
+    A0.B = A1.B = Bc;
+    gather_kernel<<<grid_of((int64_t)Bc * kIn0), 256, 0, st>>>(th + off, n, e->d, e->centre, e->half,
+                                                               nullptr, Bc, cnt, 0, 1, A0.X[0], nullptr);
+    count_launch();
+    cudaMemcpyAsync(A1.X[0], A0.X[0], (size_t)Bc * kIn0 * sizeof(__nv_bfloat16),
+                    cudaMemcpyDeviceToDevice, st);
+    forward(e, 0, A0, st);
+    forward(e, 1, A1, st);
+    const int nl = (int)e->layers.size();
+    predict_finish_kernel<<<grid_of(cnt), 256, 0, st>>>(th, n, off, cnt, e->d, e->centre, e->half,
+                                                        e->coef, e->sigma, A0.Z[nl - 1],
+                                                        A1.Z[nl - 1], thr, od, fd, dis);
+    count_launch();
+  }
+  return QML_OK;
+}
+
+// Disagreement threshold for accuracy target tol: at most tol / 2, and below
+// the smallest held-out disagreement whose running maximum error exceeds
+// 0.8 tol (so every held-out point that would be accepted is within 0.8 tol).
+double flag_threshold(const qml_emu *e, double tol) {
+  double thr = 0.5 * tol;
+  for (size_t i = 0; i < e->val_dis.size(); ++i)
+    if (e->val_maxerr[i] > 0.8 * tol) {
+      thr = std::min(thr, std::nextafter(e->val_dis[i], 0.0));
+      break;
+    }
+  return thr;
+}
+
+// seeded permutation of 0..n-1 (splitmix64 stream, Fisher-Yates)
+std::vector<int> permutation(int n, uint64_t seed) {
+  std::vector<int> p(n);
+  for (int i = 0; i < n; ++i) p[i] = i;
+  uint64_t z = seed * 0xD1B54A32D192ED03ull + 0x8CB92BA72F3D8DD7ull;
+  for (int i = n - 1; i > 0; --i) {
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    const int j = (int)(x % (uint64_t)(i + 1));
+    std::swap(p[i], p[j]);
+  }
+  return p;
+}
+
 }  // namespace
 
 extern "C" {
@@ -612,12 +689,38 @@ qml_status emu_train(qml_emu *e, int32_t n, const double *theta, const double *l
     return efail(QML_EINVAL, "emu_train: need n >= 16, batch a positive multiple of 16, lr > 0");
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<void *> keep;
-  const double *th = dev_in(theta, (size_t)n * e->d, keep);
-  const double *y = dev_in(lnl, n, keep);
+  // a seeded eighth of the labels (n >= 512) is held out of training and
+  // calibrates the fallback threshold afterwards
+  const int n_all = n;
+  const int n_val = n_all >= 512 ? n_all / 8 : 0;
+  n = n_all - n_val;
+  std::vector<double> th_h((size_t)n_all * e->d), y_h(n_all);
+  cudaStreamSynchronize(st);
+  if (cudaMemcpy(th_h.data(), theta, th_h.size() * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(y_h.data(), lnl, y_h.size() * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+    return efail(QML_ECUDA, "emu_train: reading theta / lnl failed");
+  {
+    const std::vector<int> perm = permutation(n_all, e->seed ^ 0x5EEDull);
+    std::vector<double> tp(th_h.size()), yp(n_all);
+    for (int s2 = 0; s2 < n_all; ++s2) {
+      yp[s2] = y_h[perm[s2]];
+      for (int i = 0; i < e->d; ++i) {
+        // training rows first (0..n-1), held-out rows after; each block
+        // column-major with its own row count
+        const int64_t dst = s2 < n ? s2 + (int64_t)i * n
+                                   : (int64_t)n * e->d + (s2 - n) + (int64_t)i * n_val;
+        tp[dst] = th_h[perm[s2] + (size_t)i * n_all];
+      }
+    }
+    th_h.swap(tp);
+    y_h.swap(yp);
+  }
+  const double *th = dev_in(th_h.data(), (size_t)n_all * e->d, keep);
+  const double *y = dev_in(y_h.data(), n_all, keep);
   double *res = nullptr, *part = nullptr, *sumsq = nullptr;
   float *targ = nullptr;
   const int nblk = (n + 255) / 256;
-  const int nf = 1 + e->d + e->d * (e->d + 1) / 2;
+  const int nf = nfeat(e->d);
   cudaMalloc(&res, n * sizeof(double));
   cudaMalloc(&part, (size_t)std::max(nblk, 256) * nf * (nf + 1) * sizeof(double));
   cudaMalloc(&sumsq, sizeof(double));
@@ -634,7 +737,7 @@ qml_status emu_train(qml_emu *e, int32_t n, const double *theta, const double *l
     cleanup();
     return efail(QML_ENOMEM, "emu_train: allocation failed");
   }
-  // quadratic baseline and normalised residual targets (float64)
+  // polynomial baseline and normalised residual targets (float64)
   normal_eq_kernel<<<nblk, 256, 0, st>>>(th, y, n, e->d, e->centre, e->half, part);
   count_launch();
   solve_quad_kernel<<<1, 32, 0, st>>>(part, nblk, e->d, e->coef);
@@ -702,6 +805,42 @@ qml_status emu_train(qml_emu *e, int32_t n, const double *theta, const double *l
     }
   }
   e->fitted = true;
+  e->val_dis.clear();
+  e->val_maxerr.clear();
+  if (n_val > 0) {
+    // flags with an infinite threshold mark the held-out points outside the
+    // hull: those are always evaluated exactly and do not calibrate
+    double *vd = nullptr, *vo = nullptr;
+    int *vf = nullptr;
+    cudaMalloc(&vd, n_val * sizeof(double));
+    cudaMalloc(&vo, n_val * sizeof(double));
+    cudaMalloc(&vf, n_val * sizeof(int));
+    keep.push_back(vd);
+    keep.push_back(vo);
+    keep.push_back(vf);
+    if (!vd || !vo || !vf ||
+        run_predict(e, n_val, th + (int64_t)n * e->d, INFINITY, vo, vf, vd, st) != QML_OK) {
+      cleanup();
+      e->fitted = false;
+      return efail(QML_ENOMEM, "emu_train: held-out evaluation failed");
+    }
+    std::vector<double> dh(n_val), oh(n_val);
+    std::vector<int> fh(n_val);
+    cudaMemcpyAsync(dh.data(), vd, n_val * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(oh.data(), vo, n_val * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(fh.data(), vf, n_val * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    std::vector<int> ord;
+    for (int i = 0; i < n_val; ++i)
+      if (!fh[i]) ord.push_back(i);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return dh[a] < dh[b]; });
+    double mx = 0.0;
+    for (int i : ord) {
+      mx = std::max(mx, std::fabs(oh[i] - y_h[n + i]));
+      e->val_dis.push_back(dh[i]);
+      e->val_maxerr.push_back(mx);
+    }
+  }
   cudaError_t err = cudaStreamSynchronize(st);
   cleanup();
   if (err != cudaSuccess) return efail(QML_ECUDA, std::string("emu_train: ") + cudaGetErrorString(err));
@@ -726,34 +865,24 @@ qml_status emu_predict(qml_emu *e, int32_t n, const double *theta, double tol, d
     cudaMalloc(&fd, n * sizeof(int));
     keep.push_back(fd);
   }
-  const int chunk = 65536;
-  Acts A0, A1;
-  if (!th || !od || (flags && !fd) || !A0.make(e, chunk) || !A1.make(e, chunk)) {
+  if (!th || !od || (flags && !fd) ||
+      run_predict(e, n, th, flag_threshold(e, tol), od, fd, nullptr, st) != QML_OK) {
     for (void *p : keep) cudaFree(p);
     return efail(QML_ENOMEM, "emu_predict: allocation failed");
-  }
-  for (int off = 0; off < n; off += chunk) {
-    const int cnt = std::min(chunk, n - off);
-    const int Bc = (cnt + 15) / 16 * 16;
-    A0.B = A1.B = Bc;
-    gather_kernel<<<grid_of((int64_t)Bc * kIn0), 256, 0, st>>>(th + off, n, e->d, e->centre, e->half,
-                                                               nullptr, Bc, cnt, 0, 1, A0.X[0], nullptr);
-    count_launch();
-    cudaMemcpyAsync(A1.X[0], A0.X[0], (size_t)Bc * kIn0 * sizeof(__nv_bfloat16),
-                    cudaMemcpyDeviceToDevice, st);
-    forward(e, 0, A0, st);
-    forward(e, 1, A1, st);
-    const int nl = (int)e->layers.size();
-    predict_finish_kernel<<<grid_of(cnt), 256, 0, st>>>(th, n, off, cnt, e->d, e->centre, e->half,
-                                                        e->coef, e->sigma, A0.Z[nl - 1],
-                                                        A1.Z[nl - 1], tol, od, fd);
-    count_launch();
   }
   if (out_host) cudaMemcpyAsync(out, od, n * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (flags_host) cudaMemcpyAsync(flags, fd, n * sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaError_t err = cudaStreamSynchronize(st);
   for (void *p : keep) cudaFree(p);
   if (err != cudaSuccess) return efail(QML_ECUDA, std::string("emu_predict: ") + cudaGetErrorString(err));
+  return QML_OK;
+}
+
+qml_status emu_threshold(const qml_emu *e, double tol, double *thr, int32_t *nheld) {
+  if (!e || !thr || !(tol > 0.0)) return efail(QML_EINVAL, "emu_threshold: bad arguments");
+  if (!e->fitted) return efail(QML_EINVAL, "emu_threshold: emulator not trained");
+  *thr = flag_threshold(e, tol);
+  if (nheld) *nheld = (int32_t)e->val_dis.size();
   return QML_OK;
 }
 
