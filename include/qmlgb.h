@@ -240,6 +240,32 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
                     double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,
                     void *stream);
 
+/* ---- tuning table ----------------------------------------------------
+ * One process-wide table of named integer settings; the paper has no
+ * counterpart (it concerns how this library schedules its kernels, not what
+ * they compute).  Keys:
+ *   dgemm_autotune  1 (default) / 0: time every float64 GEMM tile candidate
+ *                   the first time a small or medium product shape is met
+ *                   (C at most 2^24 entries, K at most 4096, C not aliasing A
+ *                   or B, the stream not capturing) and keep the fastest.  The
+ *                   first call with a new shape synchronises its stream.
+ *                   Every tile gives bit-identical results.
+ *   dgemm:<ta>,<tb>,<lower>,<M>,<N>,<K>,<alias>  a measured tile (10 RM + RN,
+ *                   tile 16 RM x 16 RN); unknown values are ignored
+ *   batch_streams   worker streams of pix_loglike_batch (default 4, 1..16)
+ *   batch_graphs    1 (default) / 0: pix_loglike_batch replays each worker's
+ *                   per-item kernel sequence as a captured CUDA graph
+ * qml_tune_set / qml_tune_get: one entry (key without white space; get
+ * returns QML_EINVAL when absent).  qml_tune_table writes the table as text,
+ * one "key value" line per entry, into buf (capacity cap bytes, NUL
+ * included) and returns the size it needs (nothing is written when cap is
+ * smaller).  qml_tune_load merges such text into the table (lines starting
+ * with '#' are comments); a malformed line leaves the table unchanged. */
+qml_status qml_tune_set(const char *key, int64_t value);
+qml_status qml_tune_get(const char *key, int64_t *value);
+int64_t qml_tune_table(char *buf, int64_t cap);
+qml_status qml_tune_load(const char *text);
+
 /* qml_potrf without any device allocation.  The paper has no counterpart:
  * this exists for callers that cannot allocate device memory (code running
  * inside a host runtime that owns all GPU memory and hands its callees

@@ -11,6 +11,7 @@ import os
 from .build import LIB
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+c_char_p = ctypes.c_char_p
 
 QML_OK, QML_EINVAL, QML_ENOTSPD, QML_ENOMEM, QML_ECUDA, QML_ETIMEOUT = range(6)
 QML_FP64, QML_SPLIT_BF16 = 0, 1
@@ -59,6 +60,10 @@ SIGNATURES = {
                             c_void_p, c_void_p]),
     "emu_predict": (c_int32, [c_void_p, c_int32, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "emu_param_count": (c_int64, [c_void_p]),
+    "qml_tune_set": (c_int32, [c_char_p, c_int64]),
+    "qml_tune_get": (c_int32, [c_char_p, c_void_p]),
+    "qml_tune_table": (c_int64, [c_void_p, c_int64]),
+    "qml_tune_load": (c_int32, [c_char_p]),
     "emu_threshold": (c_int32, [c_void_p, c_double, c_void_p, c_void_p]),
     "emu_params": (c_int32, [c_void_p, c_int32, c_void_p]),
     "emu_loss_grad": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -262,6 +262,32 @@ def loglike_batch(masks, item_mask, item_cl):
     return lnl.T, chi2.T, ld[:, 0]
 
 
+def tune_set(key, value):
+    """Set one entry of the library's tuning table (qml_tune_set)."""
+    _check(_lib().qml_tune_set(key.encode(), int(value)))
+
+
+def tune_get(key, default=None):
+    """One entry of the tuning table, or `default` when absent."""
+    v = ctypes.c_int64(0)
+    if _lib().qml_tune_get(key.encode(), ctypes.byref(v)) != 0:
+        return default
+    return v.value
+
+
+def tune_table():
+    """The tuning table as text ("key value" per line)."""
+    need = _lib().qml_tune_table(None, 0)
+    buf = ctypes.create_string_buffer(int(need))
+    _lib().qml_tune_table(buf, need)
+    return buf.value.decode()
+
+
+def tune_load(text):
+    """Merge a saved tuning table (the text of tune_table) into the library's."""
+    _check(_lib().qml_tune_load(text.encode()))
+
+
 class Emulator:
     """MLP surrogate of lnL(theta) with a two-head ensemble (emu_* entry points)."""
 

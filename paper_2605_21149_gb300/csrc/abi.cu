@@ -10,6 +10,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -759,13 +760,20 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
   }
 
   // ---- per-item work, round-robin over worker streams
-  const int NS = nitems < 4 ? nitems : 4;
+  const int ns_max = (int)std::max<int64_t>(1, std::min<int64_t>(16, tune_get("batch_streams", 4)));
+  const int NS = nitems < ns_max ? nitems : ns_max;
+  // CUDA graphs: item 0 runs as plain launches (so that the tile autotuner
+  // can time its shapes), then each (worker, mask) pair captures its per-item
+  // sequence once -- reading the spectrum from a fixed per-worker slot and
+  // writing its results to fixed slots -- and replays it for every later item
+  bool graphs = tune_get("batch_graphs", 1) != 0 && nitems > NS;
   bool any_split = false;
   for (int m = 0; m < nmask; ++m) any_split |= (masks[m].prob.precision == QML_SPLIT_BF16);
   struct Worker {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
     double *K, *lamL, *z, *rr, *Linv, *LinvB, *ldp;
+    double *cl, *lnK, *lnl, *chi, *ld;  // fixed slots of the captured sequence
     void *ws;
     size_t ws_bytes;
   };
@@ -788,6 +796,11 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
     wk[w].Linv = c.alloc<double>((size_t)nbk * kNB * kNB);
     wk[w].LinvB = any_split ? c.alloc<double>((size_t)nbbk * kNBS * kNBS) : nullptr;
     wk[w].ldp = c.alloc<double>(nbk);
+    wk[w].cl = c.alloc<double>(6 * L);
+    wk[w].lnK = c.alloc<double>(1);
+    wk[w].lnl = c.alloc<double>(maxmaps);
+    wk[w].chi = c.alloc<double>(maxmaps);
+    wk[w].ld = c.alloc<double>(1);
     wk[w].ws = any_split ? (void *)c.alloc<unsigned char>(wsb, "split workspace") : nullptr;
     wk[w].ws_bytes = wsb;
   }
@@ -806,32 +819,81 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
     wc[w] = new Call(wk[w].st);
     wc[w]->status = c.status;
   }
-  for (int i = 0; i < nitems && c.err == QML_OK; ++i) {
-    const int w = i % NS, m = imask[i];
+  // the per-item sequence of worker w on mask m: spectrum cl, outputs
+  auto item_body = [&](int w, int m, const double *cl, double *lnKp, double *ol, double *oc,
+                       double *od) {
     Call &cw = *wc[w];
     Worker &W = wk[w];
     const int nm = masks[m].nmaps;
-    const bool split = masks[m].prob.precision == QML_SPLIT_BF16;
-    launch_lambda_factor(cl_d + (size_t)i * 6 * L, d0.lmin, d0.lmax, d0.nc, d0.comps, W.lamL, W.st);
+    launch_lambda_factor(cl, d0.lmin, d0.lmax, d0.nc, d0.comps, W.lamL, W.st);
     launch_form_ktilde(ms[m].M, k, d0.nc, d0.k0, d0.lmin, W.lamL, W.K, k, W.st);
     launch_lambda_t_apply(ms[m].v, k, d0.nc, d0.k0, d0.lmin, W.lamL, nm, W.z, k, W.st);
-    if (split) {
+    if (masks[m].prob.precision == QML_SPLIT_BF16) {
       Split spl{&cw, masks[m].prob.nslices};
       spl.preset(W.ws, W.ws_bytes);
-      potrf_split(cw, spl, W.K, k, k, W.Linv, W.LinvB, W.ldp, lnK + i);
+      potrf_split(cw, spl, W.K, k, k, W.Linv, W.LinvB, W.ldp, lnKp);
       trsm_split(cw, spl, W.K, k, k, W.LinvB, W.z, nm, k);
     } else {
-      potrf_blocked(cw, W.K, k, k, W.Linv, W.ldp, lnK + i);
+      potrf_blocked(cw, W.K, k, k, W.Linv, W.ldp, lnKp);
       trsm_blocked(cw, W.K, k, k, W.Linv, W.z, nm, k);
     }
     launch_colnorm2(W.z, k, k, nm, W.rr, W.st);
-    launch_batch_finish(W.rr, ms[m].dnd, ms[m].lnN, lnK + i, nm,
-                        o_lnl ? o_lnl + (size_t)i * ld_out : nullptr,
-                        o_chi ? o_chi + (size_t)i * ld_out : nullptr, o_ld ? o_ld + i : nullptr,
-                        W.st);
-    if (cw.err != QML_OK && c.err == QML_OK) {
-      c.err = cw.err;
+    launch_batch_finish(W.rr, ms[m].dnd, ms[m].lnN, lnKp, nm, ol, oc, od, W.st);
+  };
+  std::vector<cudaGraphExec_t> gexec((size_t)NS * nmask, nullptr);
+  std::vector<long long> glaunch((size_t)NS * nmask, 0);
+  for (int i = 0; i < nitems && c.err == QML_OK; ++i) {
+    const int w = i % NS, m = imask[i];
+    Worker &W = wk[w];
+    const int nm = masks[m].nmaps;
+    double *ol = o_lnl ? o_lnl + (size_t)i * ld_out : nullptr;
+    double *oc = o_chi ? o_chi + (size_t)i * ld_out : nullptr;
+    double *od = o_ld ? o_ld + i : nullptr;
+    const double *cli = cl_d + (size_t)i * 6 * L;
+    const size_t g = (size_t)w * nmask + m;
+    if (graphs && i > 0 && !gexec[g]) {
+      const long long before = qml_launch_count();
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(W.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        item_body(w, m, W.cl, W.lnK, W.lnl, W.chi, W.ld);
+        ok = cudaStreamEndCapture(W.st, &graph) == cudaSuccess && graph != nullptr;
+      }
+      const long long captured = qml_launch_count() - before;
+      count_launch((int)-captured);  // recorded, not launched
+      if (ok && cudaGraphInstantiate(&gexec[g], graph, 0) == cudaSuccess) {
+        glaunch[g] = captured;
+      } else {
+        gexec[g] = nullptr;
+        graphs = false;  // plain launches from here on
+        cudaGetLastError();
+      }
+      if (graph) cudaGraphDestroy(graph);
+      if (wc[w]->err != QML_OK) {  // an error while recording: report it
+        c.err = wc[w]->err;
+        break;
+      }
     }
+    if (graphs && gexec[g]) {
+      c.cuda_ok(cudaMemcpyAsync(W.cl, cli, 6 * L * sizeof(double), cudaMemcpyDeviceToDevice, W.st),
+                "item spectrum");
+      c.cuda_ok(cudaGraphLaunch(gexec[g], W.st), "graph launch");
+      count_launch((int)glaunch[g]);
+      c.cuda_ok(cudaMemcpyAsync(lnK + i, W.lnK, sizeof(double), cudaMemcpyDeviceToDevice, W.st),
+                "item result");
+      if (ol)
+        c.cuda_ok(cudaMemcpyAsync(ol, W.lnl, nm * sizeof(double), cudaMemcpyDeviceToDevice, W.st),
+                  "item result");
+      if (oc)
+        c.cuda_ok(cudaMemcpyAsync(oc, W.chi, nm * sizeof(double), cudaMemcpyDeviceToDevice, W.st),
+                  "item result");
+      if (od)
+        c.cuda_ok(cudaMemcpyAsync(od, W.ld, sizeof(double), cudaMemcpyDeviceToDevice, W.st),
+                  "item result");
+    } else {
+      item_body(w, m, cli, lnK + i, ol, oc, od);
+    }
+    if (wc[w]->err != QML_OK && c.err == QML_OK) c.err = wc[w]->err;
   }
   for (int w = 0; w < NS; ++w) {
     if (wk[w].st && wk[w].done) {
@@ -840,6 +902,8 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
     }
   }
   qml_status res = c.finish();
+  for (cudaGraphExec_t ge : gexec)
+    if (ge) cudaGraphExecDestroy(ge);
   for (int w = 0; w < NS; ++w) {
     delete wc[w];
     if (wk[w].done) cudaEventDestroy(wk[w].done);

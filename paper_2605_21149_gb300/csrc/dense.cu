@@ -11,6 +11,8 @@
 
 #include <math.h>
 
+#include <string>
+
 namespace qmlgb {
 
 namespace {
@@ -372,25 +374,111 @@ void dgemm_tile(int rm, int rn, int64_t M, int64_t N, int64_t K, double alpha, c
   QMLGB_DG(4, 4) QMLGB_DG(2, 2) QMLGB_DG(1, 1) QMLGB_DG(1, 4) QMLGB_DG(2, 4) QMLGB_DG(4, 1)
   QMLGB_DG(4, 2)
 #undef QMLGB_DG
+  // any other pair: the full tile, which is safe for every aliasing
+  dgemm_go<TA, TB, 4, 4>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+}
+
+void dgemm_dispatch(int ta, int tb, int rm, int rn, int64_t M, int64_t N, int64_t K,
+                    double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double beta, double *C, int64_t ldc, int lower, const DevStatus *status,
+                    cudaStream_t st) {
+  if (!ta && !tb) dgemm_tile<false, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  else if (!ta && tb) dgemm_tile<false, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  else if (ta && !tb) dgemm_tile<true, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  else dgemm_tile<true, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+}
+
+const int kCand[7][2] = {{4, 4}, {2, 4}, {4, 2}, {2, 2}, {1, 4}, {4, 1}, {1, 1}};
+
+// Autotuner: time every candidate tile on this shape (output into a scratch
+// matrix, beta = 0, so the caller's C is untouched) and keep the fastest.
+// Every tile computes each output as the same in-order fused sum over k, so
+// the choice changes the time, never the result.  Returns false (no entry)
+// when the measurement could not be made.
+bool dgemm_autotune(int ta, int tb, int64_t M, int64_t N, int64_t K, const double *A,
+                    int64_t lda, const double *B, int64_t ldb, int lower,
+                    const DevStatus *status, cudaStream_t st, int &rm, int &rn) {
+  double *scratch = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaMalloc(&scratch, (size_t)M * N * sizeof(double)) == cudaSuccess &&
+            cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  float best = 0.0f;
+  int found = -1;
+  for (int i = 0; ok && i < 7; ++i) {
+    const int r1 = kCand[i][0], r2 = kCand[i][1];
+    dgemm_dispatch(ta, tb, r1, r2, M, N, K, 1.0, A, lda, B, ldb, 0.0, scratch, M, lower, status, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r)
+      dgemm_dispatch(ta, tb, r1, r2, M, N, K, 1.0, A, lda, B, ldb, 0.0, scratch, M, lower, status,
+                     st);
+    cudaEventRecord(e1, st);
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    if (found < 0 || ms < best) {
+      best = ms;
+      found = i;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (scratch) cudaFree(scratch);
+  if (!ok || found < 0) {
+    cudaGetLastError();
+    return false;
+  }
+  rm = kCand[found][0];
+  rn = kCand[found][1];
+  return true;
 }
 
 }  // namespace
 
-// Tile choice: the largest tile whose grid still gives every SM two CTAs,
-// else the smallest.  In-place products keep what makes them safe: C == A
-// (C's rows read only by their own CTA) needs the whole of N in one tile,
-// C == B the whole of M; callers only alias with N (resp. M) <= 64.
+// Tile choice: a measured entry of the tuning table for this shape (tuned
+// on first use when allowed), else the largest tile whose grid still gives
+// every SM two CTAs, else the smallest.  In-place products keep what makes
+// them safe: C == A (C's rows read only by their own CTA) needs the whole of
+// N in one tile, C == B the whole of M; callers only alias with N (resp. M)
+// <= 64, and those shapes are never timed.
 void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                   double *C, int64_t ldc, int lower, const DevStatus *status, cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
-  static const int cand[7][2] = {{4, 4}, {2, 4}, {4, 2}, {2, 2}, {1, 4}, {4, 1}, {1, 1}};
   const bool aliasA = (C == A), aliasB = (C == B);
+  const std::string key = "dgemm:" + std::to_string(ta) + "," + std::to_string(tb) + "," +
+                          std::to_string(lower) + "," + std::to_string(M) + "," +
+                          std::to_string(N) + "," + std::to_string(K) + "," +
+                          std::to_string((aliasA ? 1 : 0) + (aliasB ? 2 : 0));
+  int64_t tv;
+  bool known = false;
+  if (tune_find(key, tv))
+    for (int i = 0; i < 7; ++i)
+      known |= (tv == 10 * kCand[i][0] + kCand[i][1]);
+  if (known && !(aliasA && tv % 10 != 4) && !(aliasB && tv / 10 != 4)) {
+    dgemm_dispatch(ta, tb, (int)(tv / 10), (int)(tv % 10), M, N, K, alpha, A, lda, B, ldb, beta,
+                   C, ldc, lower, status, st);
+    return;
+  }
+  if (!aliasA && !aliasB && M * N <= (1 << 24) && K <= 4096 && tune_get("dgemm_autotune", 1)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      int rm = 4, rn = 4;
+      if (dgemm_autotune(ta, tb, M, N, K, A, lda, B, ldb, lower, status, st, rm, rn)) {
+        tune_put(key, 10 * rm + rn);
+        dgemm_dispatch(ta, tb, rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status,
+                       st);
+        return;
+      }
+    }
+    cudaGetLastError();
+  }
   const int64_t want = 2 * 152;
   int rm = 4, rn = 4;
   int64_t best = -1;
   for (int i = 0; i < 7; ++i) {
-    const int r1 = cand[i][0], r2 = cand[i][1];
+    const int r1 = kCand[i][0], r2 = kCand[i][1];
     if (aliasA && r2 != 4) continue;
     if (aliasB && r1 != 4) continue;
     const int64_t n = dgemm_ctas(M, N, 16 * r1, 16 * r2, lower);
@@ -406,10 +494,7 @@ void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
       rn = r2;
     }
   }
-  if (!ta && !tb) dgemm_tile<false, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
-  else if (!ta && tb) dgemm_tile<false, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
-  else if (ta && !tb) dgemm_tile<true, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
-  else dgemm_tile<true, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  dgemm_dispatch(ta, tb, rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
 }
 
 void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,

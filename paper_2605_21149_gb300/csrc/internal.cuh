@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace qmlgb {
 
 // Device status word written by kernels (first int: qml_status code,
@@ -17,6 +19,11 @@ struct DevStatus {
 
 // Count of kernel launches made by this library (reported by qml_launch_count).
 void count_launch(int n = 1);
+
+// Tuning table (tune.cu): named integer settings and measured tile shapes.
+int64_t tune_get(const std::string &key, int64_t dflt);
+bool tune_find(const std::string &key, int64_t &value);
+void tune_put(const std::string &key, int64_t value);
 
 // Iteration budget of every device-side spin wait (~1 s with 64 ns sleeps).
 constexpr long long kSpinLimit = 1LL << 24;

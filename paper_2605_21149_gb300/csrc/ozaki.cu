@@ -8,13 +8,14 @@
 // exactly; the same for the columns of op(B) with exponents f_j.  Then
 //   C_ij = 2^(e_i+f_j) sum_{s+t <= S+1} 2^(-beta(s+t)) (A_s B_t^T)_ij
 // (products below the truncation level are dropped).  Every digit product
-// A_s B_t^T is an integer matrix; over a K-chunk of 2^(24 - 2 beta) its
-// entries stay below 2^24, so the FP32 tensor-core accumulation in TMEM is
-// exact whatever the accumulation order or rounding mode.  Each exact chunk
-// is converted to int32 and added, shifted left by shift_L = shift_top -
-// beta (L - 2) bits (right, rounded, when negative) for its level L = s + t,
+// A_s B_t^T is an integer matrix, and all pairs of one level L = s + t carry
+// the same weight, so they accumulate into one FP32 TMEM accumulator; over a
+// K-chunk of kChunkK elements the level sum stays below 2^24, so the
+// tensor-core accumulation is exact whatever its order or rounding mode.
+// Each exact (level, chunk) sum is converted to int32 and added, shifted left
+// by shift_L = shift_top - beta (L - 2) bits (right, rounded, when negative),
 // into one int64 fixed-point accumulator per output held in registers; the
-// top level fills at most 62 bits.  One float64 conversion per output remains.
+// total stays below 2^62.  One float64 conversion per output remains.
 //
 // Kernel layout: one CTA per 128 x 128 output tile, 320 threads.
 //   warp 0   TMA producer (one lane): bf16 digit tiles 128 x 64 of op(A) and
@@ -39,9 +40,15 @@ namespace qmlgb {
 
 namespace {
 
-constexpr int OBM = 128, OBN = 128, OBK = 64, OSTAGES = 4;
+constexpr int OBM = 128, OBN = 128, OBK = 64;
 constexpr int kTileBytes = OBM * OBK * 2;  // 16 KB per operand tile
 constexpr int kThreads = 320;
+// K elements per exact chunk.  All digit pairs (s, t) of one level L = s + t
+// accumulate in the same FP32 accumulator: with beta = 6, |a_1|, |b_1| <= 2^6
+// and the other digits <= 2^5, so a level-L sum over kChunkK elements is at
+// most kChunkK 2^10 (n_L + 2) <= 2^10 2^10 12 < 2^24 for the n_L <= 10 pairs a
+// level has (S <= 10), and level 2 at most kChunkK 2^12 = 2^22: exact.
+constexpr int kChunkK = 1024;
 
 // ------------------------------------------------------------ PTX helpers --
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -186,6 +193,7 @@ __device__ __forceinline__ void tile_of(const OzParams &p, int bid, int &tm, int
   tn = bid - r * (r + 1) / 2;
 }
 
+template <int OSTAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, OzParams p) {
@@ -239,17 +247,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int q = 0; q < OSTAGES; ++q) last_phase[q] = -1;
       bool ok = (*((volatile int *)&st->code) == 0);
       for (int L = 2; L <= S + 1 && ok; ++L) {
-        for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
-          const int t = L - s;
-          for (int ks = 0; ks < p.nk && ok; ++ks) {
-            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st)) { ok = false; break; }
-            mbar_expect_tx(full0 + 8 * stage, 2 * kTileBytes);
-            tma_load_2d(smem_u32(tilesA + stage * kTileBytes), &tmA, full0 + 8 * stage, ks * OBK,
-                        (s - 1) * p.Mpad + m0);
-            tma_load_2d(smem_u32(tilesB + stage * kTileBytes), &tmB, full0 + 8 * stage, ks * OBK,
-                        (t - 1) * p.Npad + n0);
-            last_phase[stage] = (int)phase;
-            if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
+        for (int c = 0; c < nchunks && ok; ++c) {
+          const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
+          for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
+            const int t = L - s;
+            for (int ks = k0; ks < k1 && ok; ++ks) {
+              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st)) { ok = false; break; }
+              mbar_expect_tx(full0 + 8 * stage, 2 * kTileBytes);
+              tma_load_2d(smem_u32(tilesA + stage * kTileBytes), &tmA, full0 + 8 * stage, ks * OBK,
+                          (s - 1) * p.Mpad + m0);
+              tma_load_2d(smem_u32(tilesB + stage * kTileBytes), &tmB, full0 + 8 * stage, ks * OBK,
+                          (t - 1) * p.Npad + n0);
+              last_phase[stage] = (int)phase;
+              if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
+            }
           }
         }
       }
@@ -270,14 +281,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t q = 0;  // chunk accumulations so far; buffer q & 1
       bool ok = (*((volatile int *)&st->code) == 0);
       for (int L = 2; L <= S + 1 && ok; ++L) {
-        for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
-          for (int c = 0; c < nchunks && ok; ++c) {
-            const uint32_t b = q & 1;
-            // the epilogue must have read this buffer's previous chunk
-            if (q >= 2 && !mbar_wait(acce0 + 8 * b, ((q >> 1) - 1) & 1, st)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t dacc = tbase + 128 * b;
-            const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
+        for (int c = 0; c < nchunks && ok; ++c) {
+          const uint32_t b = q & 1;
+          // the epilogue must have read this buffer's previous chunk
+          if (q >= 2 && !mbar_wait(acce0 + 8 * b, ((q >> 1) - 1) & 1, st)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dacc = tbase + 128 * b;
+          const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
+          uint32_t acc_on = 0;  // the first MMA of the (level, chunk) sum overwrites
+          // every digit pair of this level adds into the same accumulator
+          for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
             for (int ks = k0; ks < k1; ++ks) {
               if (!mbar_wait(full0 + 8 * stage, phase, st)) { ok = false; break; }
               tc_fence_after();
@@ -286,15 +299,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int kk = 0; kk < OBK / 16; ++kk) {
                 mma_bf16(dacc, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk), kIdesc,
-                         (ks > k0 || kk > 0) ? 1u : 0u);
+                         acc_on);
+                acc_on = 1u;
               }
               mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
               if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
             }
-            if (!ok) break;
-            mma_commit(accf0 + 8 * b);  // chunk result ready for the epilogue
-            ++q;
           }
+          if (!ok) break;
+          mma_commit(accf0 + 8 * b);  // (level, chunk) sum ready for the epilogue
+          ++q;
         }
       }
       // wait for every MMA this thread issued before TMEM is released
@@ -314,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int L = 2; L <= S + 1 && ok; ++L) {
       const int sh = p.shift_top - p.beta * (L - 2);
-      for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
+      {
         for (int c = 0; c < nchunks; ++c) {
           const uint32_t b = q & 1;
           int okw = 1;
@@ -495,6 +509,22 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K, int nslices, bool 
   return b;
 }
 
+template <int OSTAGES>
+cudaError_t launch_oz(int ntiles, const CUtensorMap &mA, const CUtensorMap &mB, const OzParams &p,
+                      cudaStream_t st) {
+  const size_t smem = 1024 + 2 * OSTAGES * kTileBytes + (2 * OSTAGES + 5) * 8 + 16 + OBN * 4;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<OSTAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  ozaki_gemm_kernel<OSTAGES><<<ntiles, kThreads, smem, st>>>(mA, mB, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta_c,
                        double *C, int64_t ldc, int lower, int nslices, void *work,
@@ -549,14 +579,16 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.nk = (int)(Kpad / OBK);
   p.S = S;
   p.beta = beta;
-  p.chunk = (1 << (24 - 2 * beta)) / OBK;
+  p.chunk = kChunkK / OBK;
   {
-    // level-2 chunk sums are < 2^24 each; nchunks of them (plus the smaller
-    // lower levels, < 6 % extra) must fit in 62 bits after the shift
+    // level-2 chunk sums are below 2^(2 beta) kChunkK = 2^22, level L >= 3
+    // sums below 2^20 (L + 1) (a shift of beta (L - 2) bits further down):
+    // with nchunks chunks the int64 total stays below 2^(shift_top + 22 +
+    // lg) x 1.02 <= 2^61.03
     const int nchunks = (p.nk + p.chunk - 1) / p.chunk;
     int lg = 0;
     while ((1 << lg) < nchunks) ++lg;
-    p.shift_top = 37 - lg;
+    p.shift_top = 39 - lg;
   }
   p.tiles_n = (int)(Npad / OBN);
   p.lower = lower;
@@ -569,17 +601,9 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.status = status;
   const int tiles_m = (int)(Mpad / OBM);
   int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
-  const size_t smem = 1024 + 2 * OSTAGES * kTileBytes + (2 * OSTAGES + 5) * 8 + 16 + OBN * 4;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  ozaki_gemm_kernel<<<ntiles, kThreads, smem, st>>>(mA, mB, p);
-  count_launch();
-  return cudaGetLastError();
+  // ring depth: 6 stages by default (the tuning table may pick 4)
+  if (tune_get("ozaki_stages", 6) == 4) return launch_oz<4>(ntiles, mA, mB, p, st);
+  return launch_oz<6>(ntiles, mA, mB, p, st);
 }
 
 }  // namespace qmlgb

@@ -2,6 +2,8 @@
 
     python -m paper_2605_21149_gb300.profile_cases syrk     # W = X^T X, k=6900, n=5952
     python -m paper_2605_21149_gb300.profile_cases syrk_split  # the same, split precision
+    python -m paper_2605_21149_gb300.profile_cases trail_split
+        # split Cholesky trailing update: C (6400 x 6400, lower) -= P P^T, K = 512
     python -m paper_2605_21149_gb300.profile_cases ybuild   # Y, 5952 x 6900
     python -m paper_2605_21149_gb300.profile_cases fisher   # one full qml_fisher
     python -m paper_2605_21149_gb300.profile_cases step --precision 1
@@ -21,7 +23,7 @@ def main():
     from . import api, build, synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=("syrk", "syrk_split", "ybuild", "fisher", "step"))
+    ap.add_argument("case", choices=("syrk", "syrk_split", "trail_split", "ybuild", "fisher", "step"))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--precision", type=int, default=0)
     args = ap.parse_args()
@@ -33,6 +35,10 @@ def main():
         W = torch.empty(wl.k, wl.k, dtype=torch.float64, device="cuda").t()
         prec = 1 if args.case == "syrk_split" else 0
         fn = lambda: api.gemm(X, X, W, transA=True, lower=True, precision=prec)
+    elif args.case == "trail_split":
+        P = torch.randn(512, 6400, dtype=torch.float64, device="cuda").t()
+        T = torch.zeros(6400, 6400, dtype=torch.float64, device="cuda").t()
+        fn = lambda: api.gemm(P, P, T, transB=True, lower=True, alpha=-1.0, beta=1.0, precision=1)
     elif args.case == "ybuild":
         fn = lambda: api.ybuild(prob)
     elif args.case == "fisher":

@@ -90,3 +90,24 @@ def test_null_problem(lib):
     assert lib.qml_ybuild(None, None, 0, None) == nat.QML_EINVAL
     assert lib.qml_estimate(None, None, 0, None, None, None, None, None, None) == nat.QML_EINVAL
     assert lib.qml_potrf(0, None, 0, None, 0, None) == nat.QML_EINVAL
+
+
+def test_tuning_table_round_trip(lib):
+    """The tuning table (qml_tune_*) is host state: set, get, dump, reload."""
+    from paper_2605_21149_gb300 import api
+    api.tune_set("test_key_alpha", 17)
+    assert api.tune_get("test_key_alpha") == 17
+    assert api.tune_get("no_such_key_for_sure") is None
+    text = api.tune_table()
+    assert "test_key_alpha 17\n" in text
+    api.tune_set("test_key_alpha", 3)
+    api.tune_load("# comment\ntest_key_alpha 17\ntest_key_beta -5\n")
+    assert api.tune_get("test_key_alpha") == 17 and api.tune_get("test_key_beta") == -5
+    # malformed text is rejected and leaves the table unchanged
+    assert lib.qml_tune_load(b"test_key_alpha 1\nbroken line here\n") != 0
+    assert api.tune_get("test_key_alpha") == 17
+    assert lib.qml_tune_set(b"bad key", 1) != 0
+    # a too-small buffer is left untouched and the needed size returned
+    need = lib.qml_tune_table(None, 0)
+    buf = ctypes.create_string_buffer(b"x" * 4)
+    assert lib.qml_tune_table(buf, 4) == need and buf.raw[:4] == b"xxxx"

@@ -84,3 +84,34 @@ def test_batch_rejects_mixed_bands(api):
     with pytest.raises(api.QMLError) as ei:
         api.loglike_batch([(p1, d1), (p2, d2)], [0, 1], torch.zeros(2, 6, 16, dtype=torch.float64, device="cuda"))
     assert ei.value.status == 1
+
+
+def test_batch_schedules_agree_bitwise(api):
+    """Worker count, CUDA-graph replay and the GEMM tile autotuner change the
+    schedule only: every item's results are bit-identical across them."""
+    masks, item_mask, item_cl, mapss, refs = _oracle(8, 15, 9, 2, 8)
+    cl = torch.as_tensor(item_cl, device="cuda")
+    outs = []
+    saved = {k: api.tune_get(k) for k in ("batch_streams", "batch_graphs", "dgemm_autotune")}
+    try:
+        for precision in (0, 1):
+            probs = [(api.Problem.from_workload(wl, precision=precision), td(mp))
+                     for wl, mp in zip(masks, mapss)]
+            res = []
+            for streams, graphs, tune in ((1, 0, 0), (4, 1, 1), (3, 1, 1), (2, 0, 1)):
+                api.tune_set("batch_streams", streams)
+                api.tune_set("batch_graphs", graphs)
+                api.tune_set("dgemm_autotune", tune)
+                res.append([P.to_np(x) for x in api.loglike_batch(probs, item_mask, cl)])
+            for r in res[1:]:
+                for a, b in zip(res[0], r):
+                    assert np.array_equal(a, b)
+            outs.append(res[0])
+    finally:
+        for k, v in saved.items():
+            api.tune_set(k, {"batch_streams": 4, "batch_graphs": 1, "dgemm_autotune": 1}[k]
+                         if v is None else v)
+    # and the graph-replayed results still match the oracle
+    for i in range(len(refs)):
+        assert np.abs(outs[0][0][i, :2] - refs[i][0]).max() <= 1e-10 * np.abs(refs[i][0]).max()
+    assert "dgemm:" in api.tune_table()
