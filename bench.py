@@ -442,6 +442,15 @@ def run_ours(args):
                 ab = synth.draw_alm(wl_b.cl_fid, wl_b.lmin, wl_b.lmax, wl_b.comps, 1, gb)
                 nzb = synth.noise_draws(wl_b.G, 1, gb)
                 bprobs.append((pb, api.synthesize(pb, td(ab), td(nzb))))
+            if prec == 1:
+                # schedule autotuner (worker streams x graph replay) on 32 items;
+                # the float64 form reuses the choice
+                rates = api.autotune_batch(bprobs, bim, bcl)
+                bres["autotune"] = {"candidates": {f"streams={k[0]},graphs={k[1]}": v
+                                                   for k, v in rates.items()},
+                                    "chosen": {"batch_streams": api.tune_get("batch_streams"),
+                                               "batch_graphs": api.tune_get("batch_graphs")},
+                                    "tuned_gemm_shapes": api.tune_table().count("dgemm:")}
             api.loglike_batch(bprobs, bim[:4], bcl[:4])
             torch.cuda.synchronize()
             eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -455,6 +464,30 @@ def run_ours(args):
             torch.cuda.empty_cache()
         bres["split_speedup_vs_fp64"] = bres["split_bf16"]["value"] / bres["fp64"]["value"]
         forms["lnl_batch"] = bres
+        # Monte Carlo right-hand sides: 1000 simulated maps through one plan
+        # (TQU Nside 16), float64 and split precision
+        nmc = 1000
+        gmc = synth.rng(1, synth.P_SIMS)
+        mc_maps = api.synthesize(prob, td(synth.draw_alm(wl.cl_fid, wl.lmin, wl.lmax, wl.comps, nmc, gmc)),
+                                 td(synth.noise_draws(wl.G, nmc, gmc)))
+        mres = {"workload": "TQU Nside 16 l=2..47, 1000 simulated maps per qml_estimate call "
+                            "(plan from one qml_fisher)"}
+        for prec, name in ((0, "fp64"), (1, "split_bf16")):
+            pm = api.Problem.from_workload(wl, device=True, precision=prec)
+            _, plan_mc = api.fisher(pm)
+            plan_mc.estimate(mc_maps[:, :8])
+            torch.cuda.synchronize()
+            em0, em1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            em0.record()
+            plan_mc.estimate(mc_maps)
+            em1.record()
+            em1.synchronize()
+            tmc = em0.elapsed_time(em1) * 1e-3
+            mres[name] = {"value": nmc / tmc, "unit": "sims/s", "ms_per_call": 1e3 * tmc}
+            plan_mc.free()
+        forms["mc_rhs_1000"] = mres
+        del mc_maps
+        torch.cuda.empty_cache()
         # lnL emulator: exact labels from the batched scan (TQU Nside 8,
         # f_sky 0.7, l <= 15), training of the two-head MLP, then inference with
         # the fallback flags over 2^20 points and an audit of accepted points

@@ -288,6 +288,33 @@ def tune_load(text):
     _check(_lib().qml_tune_load(text.encode()))
 
 
+def autotune_batch(probs, item_mask, item_cl, streams=(4, 8, 16), graphs=(0, 1), sample=32):
+    """Schedule autotuner of loglike_batch: time every (worker streams, graph
+    replay) pair on the first `sample` items (CUDA events on the current
+    stream, one untimed call first), store the fastest in the tuning table
+    (batch_streams, batch_graphs) and return {(streams, graphs): evals/s}."""
+    import torch
+    item_mask = np.asarray(item_mask)[:sample]
+    item_cl = item_cl[:sample]
+    rates = {}
+    for ns in streams:
+        for gr in graphs:
+            tune_set("batch_streams", ns)
+            tune_set("batch_graphs", gr)
+            loglike_batch(probs, item_mask, item_cl)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            loglike_batch(probs, item_mask, item_cl)
+            e1.record()
+            e1.synchronize()
+            rates[(ns, gr)] = len(item_mask) / (e0.elapsed_time(e1) * 1e-3)
+    best = max(rates, key=rates.get)
+    tune_set("batch_streams", best[0])
+    tune_set("batch_graphs", best[1])
+    return rates
+
+
 class Emulator:
     """MLP surrogate of lnL(theta) with a two-head ensemble (emu_* entry points)."""
 

@@ -143,54 +143,95 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
 }
 
 // ------------------------------------------------ diagonal-block Cholesky --
-// The factor L lives in the lower triangle of the shared tile a; its inverse
-// is written into the strict upper triangle (inv[i][j] at a[j][i], i > j)
-// and the reciprocals of its diagonal into invd, so one tile holds both.
-// Row stride kLDA = 68 doubles: four consecutive rows x four consecutive
-// columns land in sixteen different 8-byte bank pairs.
-constexpr int kLDA = kNB + 4;
+// One CTA (256 threads, 8 warps) factors a jb x jb (jb <= 64) diagonal block
+// in shared memory and inverts the lower factor, in panels of kPW = 8
+// columns: the float64 pipe of one SM is narrow, so the design cuts block
+// barriers and serial latency rather than arithmetic.
+//
+// Layout in the tile a (row stride kLDA = 65 doubles, so a warp reading a
+// column touches 32 different banks): the factor L in the lower triangle,
+// the strictly lower part of X = L^-1 transposed into the strict upper
+// triangle (X_ij at a[j][i], i > j), and X_ii = 1 / L_ii in invd.
+constexpr int kLDA = kNB + 1;
+constexpr int kPW = 8;
 
-__device__ __forceinline__ double inv_at(double (*a)[kLDA], const double *invd, int k, int c) {
-  return k == c ? invd[c] : a[c][k];
+// X = L^-1 entry (row, col) from the packed tile
+__device__ __forceinline__ double xval(double (*a)[kLDA], const double *invd, int row, int col) {
+  return row == col ? invd[row] : (row > col ? a[col][row] : 0.0);
 }
 
-// Column-parallel forward substitution L X = I: four lanes per column of X,
-// all eight columns of a warp in one warp, so the recurrence over rows only
-// needs the warp to be in step (every lane reaches the shuffles; inactive
-// columns contribute zero).  invd must hold 1 / L_cc on entry.
-__device__ void invert_lower_shared(double (*a)[kLDA], const double *invd, int jb) {
-  const int tid = threadIdx.x;
-  const int col = tid >> 2, part = tid & 3;
-  for (int i = 1; i < jb; ++i) {
-    double s = 0.0;
-    if (col < i)
-      for (int k = col + part; k < i; k += 4) s = fma(a[i][k], inv_at(a, invd, k, col), s);
-    s += __shfl_down_sync(0xffffffffu, s, 2, 4);
-    s += __shfl_down_sync(0xffffffffu, s, 1, 4);
-    if (col < i && part == 0) a[col][i] = -s * invd[i];
-    __syncwarp();
+// Inverse of the lower factor held in a (invd must hold 1 / L_cc):
+//  1. every warp inverts one 8 x 8 diagonal block D_I = L_II^-1 by forward
+//     substitution (lane c < 8 owns column c);
+//  2. block rows I = 1 .. 7 in turn: T_IJ = sum_{J <= K < I} L_IK X_KJ for all
+//     J < I in parallel, then X_IJ = -D_I T_IJ (X_IJ depends only on block rows
+//     above I, so one step per block row).
+__device__ void invert_lower_blocked(double (*a)[kLDA], const double *invd, int jb,
+                                     double *tmp /* >= 7 * 64 doubles */) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nbk = (jb + kPW - 1) / kPW;
+  if (warp < nbk && lane < kPW) {
+    const int b0 = warp * kPW, col = b0 + lane;
+    const int bend = (b0 + kPW < jb) ? b0 + kPW : jb;
+    if (col < bend) {
+      double xk[kPW];
+#pragma unroll
+      for (int q = 0; q < kPW; ++q) xk[q] = 0.0;
+      xk[lane] = invd[col];
+      for (int r = col + 1; r < bend; ++r) {
+        double s2 = 0.0;
+        for (int q = lane; q < r - b0; ++q) s2 = fma(a[r][b0 + q], xk[q], s2);
+        const double v = -s2 * invd[r];
+        xk[r - b0] = v;
+        a[col][r] = v;
+      }
+    }
   }
   __syncthreads();
+  for (int I = 1; I < nbk; ++I) {
+    const int rI = I * kPW, rend = (rI + kPW < jb) ? rI + kPW : jb;
+    // phase A: T_IJ (rows r of block I, columns c of block J), J < I
+    for (int t = tid; t < I * kPW * kPW; t += blockDim.x) {
+      const int J = t / (kPW * kPW), r = (t / kPW) % kPW, c = t % kPW;
+      const int row = rI + r, xc = J * kPW + c;
+      double s2 = 0.0;
+      if (row < rend)
+        for (int k = J * kPW; k < rI; ++k) s2 = fma(a[row][k], xval(a, invd, k, xc), s2);
+      tmp[t] = s2;
+    }
+    __syncthreads();
+    // phase B: X_IJ = -D_I T_IJ, written transposed into the upper triangle
+    for (int t = tid; t < I * kPW * kPW; t += blockDim.x) {
+      const int J = t / (kPW * kPW), r = (t / kPW) % kPW, c = t % kPW;
+      const int row = rI + r;
+      if (row < rend) {
+        double s2 = 0.0;
+        for (int q = 0; q <= r; ++q)
+          s2 = fma(xval(a, invd, row, rI + q), tmp[J * kPW * kPW + q * kPW + c], s2);
+        a[J * kPW + c][row] = -s2;
+      }
+    }
+    __syncthreads();
+  }
 }
 
-// One CTA factors a jb x jb (jb <= 64) diagonal block in shared memory:
-// right-looking unblocked Cholesky with a pivot check, then the inverse of
-// the lower factor.  With factor == 0 the block already holds L and only the
-// inverse is formed (blockIdx.x selects the block: j0 = blockIdx.x * kNB).
+// With factor == 0 the block already holds L and only the inverse is formed
+// (blockIdx.x selects the block: j0 = blockIdx.x * kNB).
 //
-// Column c of the working tile stays unscaled: the rank-1 update subtracts
-// a_ic a_jc / d_c with d_c = a_cc, and r_c = d_c^-1/2 (pivot check included)
-// is computed by the thread that makes the last change to a_cc, one column
-// ahead, so each column costs one barrier; L = a r_c column by column at
-// the end, and r_c doubles as 1 / L_cc for the inverse.
+// Factor: for each panel of 8 columns, warp 0 factors the panel rows alone
+// (lane l owns rows c0 + l and c0 + l + 32; the pivot's d^-1/2 is computed by
+// every lane from the shared value, so no barrier is needed inside the
+// panel), then all warps apply the rank-8 update to the trailing triangle,
+// its elements spread evenly over the threads.
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda, int64_t n,
                                                          int64_t j0, double *Linv,
                                                          double *logdet_part,
                                                          DevStatus *status, int factor) {
   __shared__ double a[kNB][kLDA];
   __shared__ double invd[kNB];
-  __shared__ double lg[kNB];
-  const int tid = threadIdx.x;
+  __shared__ double tmp[(kNB / kPW - 1) * kPW * kPW];
+  __shared__ int bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (status && *((volatile int *)&status->code) != 0) return;
   if (!factor) {
     j0 = (int64_t)blockIdx.x * kNB;
@@ -202,50 +243,77 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
     int i = t % kNB, j = t / kNB;
     a[i][j] = (i < jb && j < jb && i >= j) ? A[i + j * lda] : 0.0;
   }
+  if (tid == 0) bad = 0;
   __syncthreads();
   if (factor) {
-    if (tid == 0) invd[0] = rsqrt(a[0][0]);
-    __syncthreads();
-    const int row = tid >> 2, part = tid & 3;
-    for (int c = 0; c < jb; ++c) {
-      const double r = invd[c];
-      if (!(r > 0.0) || !isfinite(r)) {  // a_cc <= 0, infinite or NaN: uniform exit
-        if (tid == 0) {
-          status->info = (int)(j0 + c + 1);
-          atomicExch(&status->code, 2 /* QML_ENOTSPD */);
+    for (int c0 = 0; c0 < jb; c0 += kPW) {
+      const int cend = (c0 + kPW < jb) ? c0 + kPW : jb;
+      if (warp == 0) {
+        const int i0 = c0 + lane, i1 = c0 + lane + 32;
+        for (int c = c0; c < cend; ++c) {
+          const double d = a[c][c];
+          const double r = rsqrt(d);
+          if (!(r > 0.0) || !isfinite(r)) {  // d <= 0, infinite or NaN
+            if (lane == 0) {
+              bad = 1;
+              status->info = (int)(j0 + c + 1);
+              atomicExch(&status->code, 2 /* QML_ENOTSPD */);
+            }
+            break;
+          }
+          __syncwarp();  // every lane has read a_cc before lane 0 replaces it
+          if (lane == 0) {
+            invd[c] = r;
+            a[c][c] = d * r;
+          }
+          if (i0 > c && i0 < jb) a[i0][c] *= r;
+          if (i1 > c && i1 < jb) a[i1][c] *= r;
+          __syncwarp();
+          // update the panel's remaining columns
+          for (int j = c + 1; j < cend; ++j) {
+            const double ljc = a[j][c];
+            if (i0 >= j && i0 < jb) a[i0][j] = fma(-a[i0][c], ljc, a[i0][j]);
+            if (i1 >= j && i1 < jb) a[i1][j] = fma(-a[i1][c], ljc, a[i1][j]);
+          }
+          __syncwarp();
         }
-        return;
       }
-      const int i = c + 1 + row;
-      if (i < jb) {
-        const double li = a[i][c] * (r * r);
-        for (int j = c + 1 + part; j <= i; j += 4) a[i][j] = fma(-li, a[j][c], a[i][j]);
-        if (tid == 0) invd[c + 1] = rsqrt(a[c + 1][c + 1]);  // thread 0 owns (c+1, c+1)
+      __syncthreads();
+      if (bad) return;
+      // rank-(cend - c0) update of the trailing triangle cend <= j <= i < jb
+      const int m = jb - cend;
+      const int T = m * (m + 1) / 2;
+      for (int t = tid; t < T; t += blockDim.x) {
+        int r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= t) ++r;
+        while (r * (r + 1) / 2 > t) --r;
+        const int i = cend + r, j = cend + (t - r * (r + 1) / 2);
+        double v = a[i][j];
+#pragma unroll
+        for (int q = 0; q < kPW; ++q)
+          if (c0 + q < cend) v = fma(-a[i][c0 + q], a[j][c0 + q], v);
+        a[i][j] = v;
       }
       __syncthreads();
     }
     for (int t = tid; t < jb * jb; t += blockDim.x) {
       int i = t % jb, j = t / jb;
-      if (i >= j) {
-        const double v = a[i][j] * invd[j];
-        a[i][j] = v;
-        A[i + j * lda] = v;
-      }
+      if (i >= j) A[i + j * lda] = a[i][j];
     }
-    __syncthreads();
-    // logs in parallel, summed in a fixed order
-    if (tid < jb) lg[tid] = log(a[tid][tid]);
+    // logs in parallel, summed in a fixed order (tmp is free until the inverse)
+    if (tid < jb) tmp[tid] = log(a[tid][tid]);
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int c = 0; c < jb; ++c) s += lg[c];
+      for (int c = 0; c < jb; ++c) s += tmp[c];
       *logdet_part = 2.0 * s;
     }
+    __syncthreads();
   } else {
     if (tid < jb) invd[tid] = 1.0 / a[tid][tid];
     __syncthreads();
   }
-  invert_lower_shared(a, invd, jb);
+  invert_lower_blocked(a, invd, jb, tmp);
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {
     int i = t % kNB, j = t / kNB;
     double v = 0.0;

@@ -100,4 +100,35 @@ def test_emu_end_to_end_exact_labels(api):
           "worst x", 2 * (test[worst] - lo) / (hi - lo) - 1)
     assert acc.mean() > 0.5
     assert err[acc].max() <= 0.05
+
+    # what the network gains over the method without it
+    # (1) accuracy: the same float64 least-squares cubic the emulator starts
+    #     from, alone, misses by far more than the trained network
+    def cubic_features(t):
+        x = 2 * (t - lo) / (hi - lo) - 1
+        cols = [np.ones(len(x))] + [x[:, i] for i in range(4)]
+        cols += [x[:, i] * x[:, j] for i in range(4) for j in range(i, 4)]
+        cols += [x[:, i] * x[:, j] * x[:, l] for i in range(4) for j in range(i, 4) for l in range(j, 4)]
+        return np.stack(cols, axis=1)
+
+    coef, *_ = np.linalg.lstsq(cubic_features(th), y, rcond=None)
+    err_poly = np.abs(cubic_features(test) @ coef - exact)
+    print("median |dlnL| network", np.median(err), "cubic alone", np.median(err_poly))
+    assert np.median(err) * 10 <= np.median(err_poly)
+    # (2) cost: emulating with the exact fallback beats evaluating every point
+    import time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _lnl_exact(api, prob, maps, wl.lmax, test)
+    torch.cuda.synchronize()
+    t_exact = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pred2, flags2 = emu.predict(test, tol=0.05)
+    fb = np.flatnonzero(flags2)
+    if len(fb):
+        _lnl_exact(api, prob, maps, wl.lmax, test[fb])
+    torch.cuda.synchronize()
+    t_emu = time.perf_counter() - t0
+    print("exact", t_exact, "s; emulator with fallback", t_emu, "s")
+    assert t_emu < t_exact
     emu.free()
