@@ -144,71 +144,77 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
 
 // ------------------------------------------------ diagonal-block Cholesky --
 // One CTA (256 threads, 8 warps) factors a jb x jb (jb <= 64) diagonal block
-// in shared memory and inverts the lower factor, in panels of kPW = 8
-// columns: the float64 pipe of one SM is narrow, so the design cuts block
-// barriers and serial latency rather than arithmetic.
+// in shared memory and inverts the lower factor.  On this part a float64
+// operation that depends on the previous one waits tens of clocks and one
+// SM retires under two float64 lanes per clock, so the kernel is built
+// around short dependency chains: panels of kPW = 8 columns factored by one
+// warp in registers (pivots and column entries travel by shuffle), rank-8
+// trailing updates and the blocked inverse with independent partial sums.
 //
-// Layout in the tile a (row stride kLDA = 65 doubles, so a warp reading a
-// column touches 32 different banks): the factor L in the lower triangle,
-// the strictly lower part of X = L^-1 transposed into the strict upper
-// triangle (X_ij at a[j][i], i > j), and X_ii = 1 / L_ii in invd.
+// Dynamic shared memory: the tile a (factor L in its lower triangle), the
+// dense inverse x (zeros above the diagonal), 1 / L_cc, a scratch block;
+// row stride kLDA = 65 doubles keeps column reads free of bank conflicts.
 constexpr int kLDA = kNB + 1;
 constexpr int kPW = 8;
+constexpr size_t kDiagSmem =
+    (size_t)(2 * kNB * kLDA + kNB + (kNB / kPW - 1) * kPW * kPW) * sizeof(double) + 16;
 
-// X = L^-1 entry (row, col) from the packed tile
-__device__ __forceinline__ double xval(double (*a)[kLDA], const double *invd, int row, int col) {
-  return row == col ? invd[row] : (row > col ? a[col][row] : 0.0);
-}
-
-// Inverse of the lower factor held in a (invd must hold 1 / L_cc):
-//  1. every warp inverts one 8 x 8 diagonal block D_I = L_II^-1 by forward
-//     substitution (lane c < 8 owns column c);
+// Inverse X = L^-1 into x (invd holds 1 / L_cc; x zeroed by the caller):
+//  1. warp I inverts the 8 x 8 diagonal block I by forward substitution
+//     (lane c < 8 owns column c);
 //  2. block rows I = 1 .. 7 in turn: T_IJ = sum_{J <= K < I} L_IK X_KJ for all
-//     J < I in parallel, then X_IJ = -D_I T_IJ (X_IJ depends only on block rows
-//     above I, so one step per block row).
-__device__ void invert_lower_blocked(double (*a)[kLDA], const double *invd, int jb,
-                                     double *tmp /* >= 7 * 64 doubles */) {
+//     J < I (four interleaved partial sums), then X_IJ = -D_I T_IJ (X_IJ needs
+//     only block rows above I, so one step per block row).
+__device__ void invert_lower_blocked(double (*a)[kLDA], double (*x)[kLDA], const double *invd,
+                                     int jb, double *tmp /* >= 7 * 64 doubles */) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nbk = (jb + kPW - 1) / kPW;
   if (warp < nbk && lane < kPW) {
     const int b0 = warp * kPW, col = b0 + lane;
     const int bend = (b0 + kPW < jb) ? b0 + kPW : jb;
     if (col < bend) {
-      double xk[kPW];
-#pragma unroll
-      for (int q = 0; q < kPW; ++q) xk[q] = 0.0;
-      xk[lane] = invd[col];
+      x[col][col] = invd[col];
       for (int r = col + 1; r < bend; ++r) {
-        double s2 = 0.0;
-        for (int q = lane; q < r - b0; ++q) s2 = fma(a[r][b0 + q], xk[q], s2);
-        const double v = -s2 * invd[r];
-        xk[r - b0] = v;
-        a[col][r] = v;
+        double s0 = 0.0, s1 = 0.0;
+        int k = col;
+        for (; k + 1 < r; k += 2) {
+          s0 = fma(a[r][k], x[k][col], s0);
+          s1 = fma(a[r][k + 1], x[k + 1][col], s1);
+        }
+        if (k < r) s0 = fma(a[r][k], x[k][col], s0);
+        x[r][col] = -(s0 + s1) * invd[r];
       }
     }
   }
   __syncthreads();
   for (int I = 1; I < nbk; ++I) {
     const int rI = I * kPW, rend = (rI + kPW < jb) ? rI + kPW : jb;
-    // phase A: T_IJ (rows r of block I, columns c of block J), J < I
     for (int t = tid; t < I * kPW * kPW; t += blockDim.x) {
       const int J = t / (kPW * kPW), r = (t / kPW) % kPW, c = t % kPW;
       const int row = rI + r, xc = J * kPW + c;
-      double s2 = 0.0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
       if (row < rend)
-        for (int k = J * kPW; k < rI; ++k) s2 = fma(a[row][k], xval(a, invd, k, xc), s2);
-      tmp[t] = s2;
+        for (int k = J * kPW; k < rI; k += 4) {  // rI - J kPW is a multiple of 4
+          s0 = fma(a[row][k], x[k][xc], s0);
+          s1 = fma(a[row][k + 1], x[k + 1][xc], s1);
+          s2 = fma(a[row][k + 2], x[k + 2][xc], s2);
+          s3 = fma(a[row][k + 3], x[k + 3][xc], s3);
+        }
+      tmp[t] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
-    // phase B: X_IJ = -D_I T_IJ, written transposed into the upper triangle
     for (int t = tid; t < I * kPW * kPW; t += blockDim.x) {
       const int J = t / (kPW * kPW), r = (t / kPW) % kPW, c = t % kPW;
       const int row = rI + r;
       if (row < rend) {
-        double s2 = 0.0;
-        for (int q = 0; q <= r; ++q)
-          s2 = fma(xval(a, invd, row, rI + q), tmp[J * kPW * kPW + q * kPW + c], s2);
-        a[J * kPW + c][row] = -s2;
+        double s0 = 0.0, s1 = 0.0;
+        int q = 0;
+        for (; q + 1 <= r; q += 2) {
+          s0 = fma(x[row][rI + q], tmp[J * kPW * kPW + q * kPW + c], s0);
+          s1 = fma(x[row][rI + q + 1], tmp[J * kPW * kPW + (q + 1) * kPW + c], s1);
+        }
+        if (q <= r) s0 = fma(x[row][rI + q], tmp[J * kPW * kPW + q * kPW + c], s0);
+        x[row][J * kPW + c] = -(s0 + s1);
       }
     }
     __syncthreads();
@@ -217,20 +223,16 @@ __device__ void invert_lower_blocked(double (*a)[kLDA], const double *invd, int 
 
 // With factor == 0 the block already holds L and only the inverse is formed
 // (blockIdx.x selects the block: j0 = blockIdx.x * kNB).
-//
-// Factor: for each panel of 8 columns, warp 0 factors the panel rows alone
-// (lane l owns rows c0 + l and c0 + l + 32; the pivot's d^-1/2 is computed by
-// every lane from the shared value, so no barrier is needed inside the
-// panel), then all warps apply the rank-8 update to the trailing triangle,
-// its elements spread evenly over the threads.
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda, int64_t n,
                                                          int64_t j0, double *Linv,
                                                          double *logdet_part,
                                                          DevStatus *status, int factor) {
-  __shared__ double a[kNB][kLDA];
-  __shared__ double invd[kNB];
-  __shared__ double tmp[(kNB / kPW - 1) * kPW * kPW];
-  __shared__ int bad;
+  extern __shared__ __align__(16) double dsm[];
+  double(*a)[kLDA] = (double(*)[kLDA])dsm;
+  double(*x)[kLDA] = (double(*)[kLDA])(dsm + kNB * kLDA);
+  double *invd = dsm + 2 * kNB * kLDA;
+  double *tmp = invd + kNB;
+  int *bad = (int *)(tmp + (kNB / kPW - 1) * kPW * kPW);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (status && *((volatile int *)&status->code) != 0) return;
   if (!factor) {
@@ -242,57 +244,98 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {
     int i = t % kNB, j = t / kNB;
     a[i][j] = (i < jb && j < jb && i >= j) ? A[i + j * lda] : 0.0;
+    x[i][j] = 0.0;
   }
-  if (tid == 0) bad = 0;
+  if (tid == 0) *bad = 0;
   __syncthreads();
   if (factor) {
     for (int c0 = 0; c0 < jb; c0 += kPW) {
       const int cend = (c0 + kPW < jb) ? c0 + kPW : jb;
       if (warp == 0) {
-        const int i0 = c0 + lane, i1 = c0 + lane + 32;
-        for (int c = c0; c < cend; ++c) {
-          const double d = a[c][c];
-          const double r = rsqrt(d);
-          if (!(r > 0.0) || !isfinite(r)) {  // d <= 0, infinite or NaN
-            if (lane == 0) {
-              bad = 1;
-              status->info = (int)(j0 + c + 1);
-              atomicExch(&status->code, 2 /* QML_ENOTSPD */);
+        // lane l holds rows i0 = c0 + l and i1 = c0 + 32 + l of the panel
+        const int i0 = c0 + lane, i1 = c0 + 32 + lane;
+        double v0[kPW], v1[kPW];
+#pragma unroll
+        for (int q = 0; q < kPW; ++q) {
+          v0[q] = (c0 + q < cend && i0 < jb) ? a[i0][c0 + q] : 0.0;
+          v1[q] = (c0 + q < cend && i1 < jb) ? a[i1][c0 + q] : 0.0;
+        }
+        int fail_col = -1;
+#pragma unroll
+        for (int q = 0; q < kPW; ++q) {
+          const int c = c0 + q;
+          if (c < cend && fail_col < 0) {
+            const double d = __shfl_sync(0xffffffffu, v0[q], q);  // a_cc (row c is lane q)
+            const double r = rsqrt(d);
+            if (!(r > 0.0) || !isfinite(r)) {  // a_cc <= 0, infinite or NaN
+              fail_col = c;
+            } else {
+              if (i0 > c) v0[q] *= r;
+              else if (i0 == c) v0[q] = d * r;
+              v1[q] *= r;  // i1 > c always
+              if (lane == 0) invd[c] = r;
+#pragma unroll
+              for (int qj = q + 1; qj < kPW; ++qj) {
+                const double ljc = __shfl_sync(0xffffffffu, v0[q], qj);  // row c0 + qj
+                if (i0 >= c0 + qj) v0[qj] = fma(-v0[q], ljc, v0[qj]);
+                v1[qj] = fma(-v1[q], ljc, v1[qj]);
+              }
             }
-            break;
           }
-          __syncwarp();  // every lane has read a_cc before lane 0 replaces it
+        }
+        if (fail_col >= 0) {
           if (lane == 0) {
-            invd[c] = r;
-            a[c][c] = d * r;
+            *bad = 1;
+            status->info = (int)(j0 + fail_col + 1);
+            atomicExch(&status->code, 2 /* QML_ENOTSPD */);
           }
-          if (i0 > c && i0 < jb) a[i0][c] *= r;
-          if (i1 > c && i1 < jb) a[i1][c] *= r;
-          __syncwarp();
-          // update the panel's remaining columns
-          for (int j = c + 1; j < cend; ++j) {
-            const double ljc = a[j][c];
-            if (i0 >= j && i0 < jb) a[i0][j] = fma(-a[i0][c], ljc, a[i0][j]);
-            if (i1 >= j && i1 < jb) a[i1][j] = fma(-a[i1][c], ljc, a[i1][j]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < kPW; ++q) {
+            if (c0 + q < cend) {
+              if (i0 < jb && i0 >= c0 + q) a[i0][c0 + q] = v0[q];
+              if (i1 < jb) a[i1][c0 + q] = v1[q];
+            }
           }
-          __syncwarp();
         }
       }
       __syncthreads();
-      if (bad) return;
-      // rank-(cend - c0) update of the trailing triangle cend <= j <= i < jb
+      if (*bad) return;
+      // rank-(cend - c0) update of the trailing triangle cend <= j <= i < jb,
+      // two elements per pass, each with two partial sums
       const int m = jb - cend;
       const int T = m * (m + 1) / 2;
-      for (int t = tid; t < T; t += blockDim.x) {
-        int r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-        while ((r + 1) * (r + 2) / 2 <= t) ++r;
-        while (r * (r + 1) / 2 > t) --r;
-        const int i = cend + r, j = cend + (t - r * (r + 1) / 2);
-        double v = a[i][j];
+      for (int t = tid; t < T; t += 2 * blockDim.x) {
+        int ii[2], jj[2];
+        bool on[2];
 #pragma unroll
-        for (int q = 0; q < kPW; ++q)
-          if (c0 + q < cend) v = fma(-a[i][c0 + q], a[j][c0 + q], v);
-        a[i][j] = v;
+        for (int u = 0; u < 2; ++u) {
+          const int tu = t + u * (int)blockDim.x;
+          on[u] = tu < T;
+          int r = (int)((sqrtf(8.0f * tu + 1.0f) - 1.0f) * 0.5f);
+          while ((r + 1) * (r + 2) / 2 <= tu) ++r;
+          while (r * (r + 1) / 2 > tu) --r;
+          ii[u] = cend + r;
+          jj[u] = cend + (tu - r * (r + 1) / 2);
+          if (!on[u]) ii[u] = jj[u] = cend;  // harmless in-range indices
+        }
+        double v[2], w[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          v[u] = a[ii[u]][jj[u]];
+          w[u] = 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kPW; q += 2) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (c0 + q < cend) v[u] = fma(-a[ii[u]][c0 + q], a[jj[u]][c0 + q], v[u]);
+            if (c0 + q + 1 < cend) w[u] = fma(-a[ii[u]][c0 + q + 1], a[jj[u]][c0 + q + 1], w[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (on[u]) a[ii[u]][jj[u]] = v[u] + w[u];
       }
       __syncthreads();
     }
@@ -300,25 +343,31 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
       int i = t % jb, j = t / jb;
       if (i >= j) A[i + j * lda] = a[i][j];
     }
-    // logs in parallel, summed in a fixed order (tmp is free until the inverse)
-    if (tid < jb) tmp[tid] = log(a[tid][tid]);
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int c = 0; c < jb; ++c) s += tmp[c];
-      *logdet_part = 2.0 * s;
+    // log det part: logs in parallel, a fixed-order shuffle tree over them
+    if (warp == 0) {
+      double s = (lane < jb ? log(a[lane][lane]) : 0.0) +
+                 (lane + 32 < jb ? log(a[lane + 32][lane + 32]) : 0.0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) *logdet_part = 2.0 * s;
     }
-    __syncthreads();
   } else {
     if (tid < jb) invd[tid] = 1.0 / a[tid][tid];
     __syncthreads();
   }
-  invert_lower_blocked(a, invd, jb, tmp);
+  invert_lower_blocked(a, x, invd, jb, tmp);
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {
     int i = t % kNB, j = t / kNB;
-    double v = 0.0;
-    if (i < jb && j < jb && i >= j) v = (i == j) ? invd[i] : a[j][i];
-    Linv[i + j * kNB] = v;
+    Linv[i + j * kNB] = (i < jb && j < jb) ? x[i][j] : 0.0;
+  }
+}
+
+void set_diag_smem() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kDiagSmem);
+    done = true;
   }
 }
 
@@ -567,13 +616,15 @@ void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
 
 void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,
                        double *logdet_part, DevStatus *status, cudaStream_t st) {
-  { potrf_diag_kernel<<<1, 256, 0, st>>>(A, lda, n, j0, Linv, logdet_part, status, 1); count_launch(); }
+  set_diag_smem();
+  { potrf_diag_kernel<<<1, 256, kDiagSmem, st>>>(A, lda, n, j0, Linv, logdet_part, status, 1); count_launch(); }
 }
 
 void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,
                          DevStatus *status, cudaStream_t st) {
   const int nb = (int)((n + kNB - 1) / kNB);
-  { potrf_diag_kernel<<<nb, 256, 0, st>>>(const_cast<double *>(L), lda, n, 0, Linv, nullptr,
+  set_diag_smem();
+  { potrf_diag_kernel<<<nb, 256, kDiagSmem, st>>>(const_cast<double *>(L), lda, n, 0, Linv, nullptr,
                                         status, 0); count_launch(); }
 }
 
