@@ -15,11 +15,15 @@
 // Each exact (level, chunk) sum is converted to int32 and added, shifted left
 // by shift_L = shift_top - beta (L - 2) bits (right, rounded, when negative),
 // into one int64 fixed-point accumulator per output held in registers; the
-// total stays below 2^62.  One float64 conversion per output remains.
+// total stays below 2^62.  One int64 -> float64 conversion per output; the
+// scaling by a power of two is an integer add to the exponent field, and the
+// digit slicing reads the float64 bit patterns with integer operations (the
+// float64 pipe of this part is narrow).
 //
 // Kernel layout: one CTA per 128 x 128 output tile, 320 threads.
 //   warp 0   TMA producer (one lane): bf16 digit tiles 128 x 64 of op(A) and
-//            op(B), 128-byte swizzle, 4-stage ring guarded by mbarriers;
+//            op(B), 128-byte swizzle, 6-stage ring guarded by mbarriers (4
+//            when the tuning table's ozaki_stages says so);
 //   warp 1   TMEM allocator and MMA issuer (one lane): tcgen05.mma kind::f16
 //            M=128 N=128 K=16 into one of two FP32 accumulators in TMEM
 //            (columns [0,128) and [128,256)), so a flush of one overlaps the
@@ -42,7 +46,11 @@ namespace {
 
 constexpr int OBM = 128, OBN = 128, OBK = 64;
 constexpr int kTileBytes = OBM * OBK * 2;  // 16 KB per operand tile
-constexpr int kThreads = 320;
+// warps 0 and 1: TMA producer and MMA issuer; kEpiWarps epilogue warps, each
+// one TMEM lane quarter (32 tile rows) by kEpiCols columns, so a thread holds
+// kEpiCols int64 accumulators
+constexpr int kEpiWarps = 8, kEpiCols = 128 * 4 / kEpiWarps;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 // K elements per exact chunk.  All digit pairs (s, t) of one level L = s + t
 // accumulate in the same FP32 accumulator: with beta = 6, |a_1|, |b_1| <= 2^6
 // and the other digits <= 2^5, so a level-L sum over kChunkK elements is at
@@ -173,11 +181,29 @@ struct OzParams {
   int shift_top;           // left shift of level-2 chunk sums in the int64 accumulator
   int tiles_n, lower;
   double alpha, betac;
+  int alpha_pow2, alpha_exp, alpha_neg;  // alpha = (-1)^neg 2^exp when alpha_pow2
   double *C;
   int64_t ldc;
   const int *ea, *eb;
   DevStatus *status;
 };
+
+// acc 2^E as a float64, sign flipped when neg: one int64 -> float64
+// conversion (rounded to nearest even), then E added to the exponent field and
+// the sign bit flipped with integer operations.  Returns false when the
+// result would leave the normal range; the caller then uses ldexp.
+__device__ __forceinline__ bool fixed_to_double(long long acc, int E, bool neg, double &out) {
+  const long long b = __double_as_longlong((double)acc);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) {  // acc == 0
+    out = neg ? -0.0 : 0.0;
+    return true;
+  }
+  const int nex = ex + E;
+  if (nex <= 0 || nex >= 2047) return false;
+  out = __longlong_as_double((b + ((long long)E << 52)) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+  return true;
+}
 
 __device__ __forceinline__ void tile_of(const OzParams &p, int bid, int &tm, int &tn) {
   if (!p.lower) {
@@ -223,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 256);
+      mbar_init(acce0 + 8 * b, 32 * kEpiWarps);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -318,12 +344,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------------------------------------------------- epilogue
     const int quad = warp & 3;            // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;     // which 64 columns of the tile
+    const int half = (warp - 2) >> 2;     // which kEpiCols columns of the tile
     const int row = quad * 32 + lane;
-    const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16) + 64 * half;
-    long long acc[64];
+    const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16) + kEpiCols * half;
+    long long acc[kEpiCols];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
     uint32_t q = 0;
     bool ok = true;
     for (int L = 2; L <= S + 1 && ok; ++L) {
@@ -338,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!okw) { ok = false; break; }
           tc_fence_after();
 #pragma unroll
-          for (int cb = 0; cb < 4; ++cb) {
+          for (int cb = 0; cb < kEpiCols / 16; ++cb) {
             uint32_t a[16];
             tmem_ld16(lane_base + 128 * b + 16 * cb, a);
             if (sh >= 0) {
@@ -364,15 +390,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t gi = m0 + row;
       if (gi < p.M) {
         const int ebase = p.ea[gi] - 2 * p.beta - p.shift_top;
+        const int eshift = p.alpha_pow2 ? p.alpha_exp : 0;
+        const bool aneg = p.alpha_pow2 && p.alpha_neg;
+        // C is read in groups of 8 before any of them is written, so the
+        // loads are in flight together instead of one DRAM round trip each
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
-          const int jl = 64 * half + j;
-          const int64_t gj = n0 + jl;
-          if (gj >= p.N || (p.lower && gi < gj)) continue;
-          double v = p.alpha * ldexp((double)acc[j], ebase + s_eb[jl]);
-          double *cp = p.C + gi + gj * p.ldc;
-          if (p.betac != 0.0) v = fma(p.betac, *cp, v);
-          *cp = v;
+        for (int g = 0; g < kEpiCols / 8; ++g) {
+          double cv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int jl = kEpiCols * half + 8 * g + u;
+            const int64_t gj = n0 + jl;
+            const bool live = gj < p.N && !(p.lower && gi < gj);
+            cv[u] = (live && p.betac != 0.0) ? p.C[gi + gj * p.ldc] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int j = 8 * g + u;
+            const int jl = kEpiCols * half + j;
+            const int64_t gj = n0 + jl;
+            if (gj >= p.N || (p.lower && gi < gj)) continue;
+            double v;
+            if (fixed_to_double(acc[j], ebase + s_eb[jl] + eshift, aneg, v)) {
+              if (!p.alpha_pow2) v *= p.alpha;
+            } else {
+              v = p.alpha * ldexp((double)acc[j], ebase + s_eb[jl]);
+            }
+            if (p.betac == 1.0) v += cv[u];
+            else if (p.betac != 0.0) v = fma(p.betac, cv[u], v);
+            p.C[gi + gj * p.ldc] = v;
+          }
         }
       }
     }
@@ -391,15 +438,49 @@ __global__ void row_exponent_kernel(const double *X, int64_t R, int64_t K, int64
   const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= Rpad) return;
-  double mx = 0.0;
+  // max |x| on the bit patterns with the sign cleared (for non-negative
+  // float64 values the integer order is the numeric order)
+  long long mb = 0;
   if (r < R)
-    for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[r * sr + k * sk]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int64_t k = lane; k < K; k += 32) {
+      const long long b = __double_as_longlong(X[r * sr + k * sk]) & 0x7FFFFFFFFFFFFFFFll;
+      mb = b > mb ? b : mb;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = t > mb ? t : mb;
+  }
   if (lane == 0) {
     int ex = 0;
+    const double mx = __longlong_as_double(mb);
     if (mx > 0.0) frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1): mx < 2^ex
     e[r] = ex;
   }
+}
+
+// round(x 2^sh) to the nearest integer, ties to even (as __double2ll_rn of
+// ldexp(x, sh) would), by integer operations on the float64 bit pattern; the
+// caller guarantees |x| 2^sh < 2^62
+__device__ __forceinline__ long long scaled_round(double x, int sh) {
+  const long long bits = __double_as_longlong(x);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = (unsigned long long)(bits & ((1ll << 52) - 1));
+  if (bexp == 0 && m == 0) return 0;
+  if (bexp != 0) m |= 1ull << 52;
+  // x = m 2^(e2), e2 = max(bexp, 1) - 1075
+  const int t = (bexp != 0 ? bexp : 1) - 1075 + sh;
+  unsigned long long q;
+  if (t >= 0) {
+    q = m << t;
+  } else if (t < -63) {
+    q = 0;
+  } else {
+    const int d = -t;
+    q = m >> d;
+    const unsigned long long rem = m & ((1ull << d) - 1ull), half = 1ull << (d - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return bits < 0 ? -(long long)q : (long long)q;
 }
 
 // digits of one logical matrix X (R x K, element (r,k) at X[r sr + k sk]) into
@@ -435,7 +516,7 @@ __global__ void slice_kernel(const double *X, int64_t R, int64_t K, int64_t sr, 
     if (r >= Rpad) continue;
     const int er = (r < R) ? e[r] : 0;
     long long F[2];
-    for (int h = 0; h < 2; ++h) F[h] = __double2ll_rn(ldexp(tile[rq][kp + h], beta * S - er));
+    for (int h = 0; h < 2; ++h) F[h] = scaled_round(tile[rq][kp + h], beta * S - er);
     const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
     for (int s = S; s >= 1; --s) {
       float d[2];
@@ -594,6 +675,13 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.lower = lower;
   p.alpha = alpha;
   p.betac = beta_c;
+  {
+    int ax = 0;
+    const double fr = frexp(alpha, &ax);  // alpha = fr 2^ax, |fr| in [0.5, 1)
+    p.alpha_pow2 = (fr == 0.5 || fr == -0.5) ? 1 : 0;
+    p.alpha_exp = ax - 1;
+    p.alpha_neg = alpha < 0.0 ? 1 : 0;
+  }
   p.C = C;
   p.ldc = ldc;
   p.ea = ea;
