@@ -26,6 +26,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Fisher+Cl solves/s (TQU Nside16 l2-47, 100 sims)"
+# DRAM bytes (read + write) of one W = X^T X launch of dgemm_kernel<1,0,4,4>
+# at this workload, from one ncu capture of that kernel (set to None when the
+# kernel changes until it is captured again)
+DGEMM_SYRK_TRAFFIC = 8.545804e9 + 0.187486e9
+DGEMM_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                             "profiles/dgemm_syrk_tqu_nside16_fp64.md")
 UNIT = "solves/s"
 
 
@@ -356,7 +362,8 @@ def run_ours(args):
                 "frac": achieved / fp64_peak,
                 "peak_source": "cuBLAS DGEMM (torch.matmul float64 8192^3, best of 4) "
                                "measured in this run; MEASURED_PEAKS.json has no float64 entry",
-                "traffic": None, "flops_per_launch": flops, "ms_per_launch": dur * 1e3}
+                "traffic": DGEMM_SYRK_TRAFFIC, "traffic_source": DGEMM_SYRK_TRAFFIC_SOURCE,
+                "flops_per_launch": flops, "ms_per_launch": dur * 1e3}
 
     # ---- split-precision form (bf16 digits on tcgen05, float64 recombination;
     # 1e-8 against the float64 oracle in tests/test_gpu_split_pipeline.py)
