@@ -129,7 +129,8 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan, void 
  * bias, Eq. noise_bias), cl_deconv = F^-1 (y - b) (Eq. deconvolved),
  * cl_decorr = F^-1/2 (y - b) with eigenvalues below 1e-12 x max dropped
  * (Eq. decorrelated), q_conv = y - b whose window matrix is F itself
- * (Eq. convolved).  Any output pointer may be NULL to skip it. */
+ * (Eq. convolved).  Any output pointer may be NULL to skip it.  nsims = 0
+ * (maps may then be NULL) only writes b. */
 qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims,
                         double *y, double *b, double *cl_deconv, double *cl_decorr,
                         double *q_conv, void *stream);
@@ -224,17 +225,23 @@ void emu_free(qml_emu *emu);
 /* In-place lower Cholesky A = L L^T of an n x n SPD matrix (lower triangle
  * read and overwritten; the strict upper triangle is left untouched).
  * *logdet (host or device, may be NULL) receives ln|A| = 2 sum ln L_ii.
+ * precision QML_FP64: float64 throughout; QML_SPLIT_BF16: 512-wide panels
+ * whose diagonal blocks (and ln|A|) are factored in float64, panel solves and
+ * trailing updates as split-precision products (the scheme of qml_fisher).
  * Errors: QML_ENOTSPD with the failing column in the message. */
 qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t precision,
                      void *stream);
 
-/* B <- L^-1 B for lower-triangular L (n x n, from qml_potrf) and B n x nrhs. */
+/* B <- L^-1 B for lower-triangular L (n x n, from qml_potrf) and B n x nrhs.
+ * QML_SPLIT_BF16: the inverses of the 512-wide diagonal blocks are formed in
+ * float64, every product with them and with the off-diagonal blocks is split. */
 qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, double *B,
                     int64_t ldb, int32_t precision, void *stream);
 
 /* C <- alpha op(A) op(B) + beta C, op(X) = X or X^T (trans flags 0/1),
  * op(A) m x kk, op(B) kk x nn, C m x nn.  lower != 0 writes only the lower
- * triangle (i >= j) of a square C.  C must not overlap A or B. */
+ * triangle (i >= j) of a square C.  C must not overlap A or B.  m = 0 or
+ * nn = 0 is a no-op; with kk = 0, C <- beta C and A, B may be NULL. */
 qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64_t kk,
                     double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
                     double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,

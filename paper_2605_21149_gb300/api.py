@@ -422,7 +422,7 @@ def gemm(A, B, C=None, transA=False, transB=False, alpha=1.0, beta=0.0, lower=Fa
             C.zero_()
         else:
             C[:] = 0.0
-    _check(_lib().qml_gemm(int(transA), int(transB), m, nn, kk, alpha, _ptr(A), A.shape[0],
-                           _ptr(B), B.shape[0], beta, _ptr(C), C.shape[0], int(lower),
+    _check(_lib().qml_gemm(int(transA), int(transB), m, nn, kk, alpha, _ptr(A), max(1, A.shape[0]),
+                           _ptr(B), max(1, B.shape[0]), beta, _ptr(C), max(1, C.shape[0]), int(lower),
                            precision, _stream(dev)))
     return C

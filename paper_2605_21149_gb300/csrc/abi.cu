@@ -597,10 +597,15 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
 qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims, double *y, double *b,
                         double *cl_deconv, double *cl_decorr, double *q_conv, void *stream) {
   if (!plan) return fail(QML_EINVAL, "plan is NULL");
-  if (!maps || nsims <= 0) return fail(QML_EINVAL, "need maps and nsims > 0");
+  if (nsims < 0 || (nsims > 0 && !maps)) return fail(QML_EINVAL, "need maps and nsims >= 0");
   const Dims &d = plan->d;
   const int na = plan->na;
   Call c(stream);
+  if (nsims == 0) {  // no maps: only the noise bias, which belongs to the plan
+    double *bd = c.out(b, na, "b");
+    if (bd) c.cuda_ok(cudaMemcpyAsync(bd, plan->b, na * sizeof(double), cudaMemcpyDeviceToDevice, c.st), "b");
+    return c.finish();
+  }
   const double *D = c.in(maps, (size_t)d.n * nsims, "maps");
   double *U = c.alloc<double>((size_t)d.n * nsims, "U");
   double *w = c.alloc<double>((size_t)d.k * nsims, "w");
@@ -916,7 +921,8 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
 qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t precision,
                      void *stream) {
   if (n <= 0 || !A || lda < n) return fail(QML_EINVAL, "bad potrf arguments");
-  if (precision != QML_FP64) return fail(QML_EINVAL, "precision: only QML_FP64 in this build");
+  if (precision != QML_FP64 && precision != QML_SPLIT_BF16)
+    return fail(QML_EINVAL, "precision must be QML_FP64 or QML_SPLIT_BF16");
   Call c(stream);
   double *Ad = c.out(A, (size_t)lda * n, "A");
   if (Ad != A && Ad) {
@@ -928,7 +934,14 @@ qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t 
   double *Linv = c.alloc<double>((size_t)nblocks * kNB * kNB);
   double *ldparts = c.alloc<double>(nblocks);
   if (!c.make_status()) return c.finish();
-  potrf_blocked(c, Ad, n, lda, Linv, ldparts, ld);
+  if (precision == QML_SPLIT_BF16) {
+    double *LinvB = c.alloc<double>((size_t)((n + kNBS - 1) / kNBS) * kNBS * kNBS);
+    if (!LinvB) return c.finish();
+    Split spl{&c, 0};
+    potrf_split(c, spl, Ad, n, lda, Linv, LinvB, ldparts, ld);
+  } else {
+    potrf_blocked(c, Ad, n, lda, Linv, ldparts, ld);
+  }
   return c.finish();
 }
 
@@ -936,7 +949,8 @@ qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, doubl
                     int32_t precision, void *stream) {
   if (n <= 0 || nrhs < 0 || !L || !B || lda < n || ldb < n)
     return fail(QML_EINVAL, "bad trsm arguments");
-  if (precision != QML_FP64) return fail(QML_EINVAL, "precision: only QML_FP64 in this build");
+  if (precision != QML_FP64 && precision != QML_SPLIT_BF16)
+    return fail(QML_EINVAL, "precision must be QML_FP64 or QML_SPLIT_BF16");
   if (nrhs == 0) return QML_OK;
   Call c(stream);
   const double *Ld = c.in(L, (size_t)lda * n, "L");
@@ -948,7 +962,21 @@ qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, doubl
   double *Linv = c.alloc<double>((size_t)nblocks * kNB * kNB);
   if (!c.make_status()) return c.finish();
   launch_trtri_blocks(Ld, lda, n, Linv, c.status, c.st);
-  trsm_blocked(c, Ld, n, lda, Linv, Bd, nrhs, ldb);
+  if (precision == QML_SPLIT_BF16) {
+    // explicit inverses of the kNBS diagonal blocks (float64), then split products
+    double *LinvB = c.alloc<double>((size_t)((n + kNBS - 1) / kNBS) * kNBS * kNBS);
+    if (!LinvB) return c.finish();
+    for (int64_t j = 0; j < n; j += kNBS) {
+      const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
+      double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
+      launch_set_identity(Xinv, kNBS, jb, c.st);
+      trinv_blocked(c, Ld + j + j * lda, jb, lda, Linv + (j / kNB) * kNB * kNB, Xinv, kNBS);
+    }
+    Split spl{&c, 0};
+    trsm_split(c, spl, Ld, n, lda, LinvB, Bd, nrhs, ldb);
+  } else {
+    trsm_blocked(c, Ld, n, lda, Linv, Bd, nrhs, ldb);
+  }
   return c.finish();
 }
 
@@ -956,15 +984,16 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
                     double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
                     double beta, double *C, int64_t ldc, int32_t lower, int32_t precision,
                     void *stream) {
-  if (m < 0 || nn < 0 || kk < 0 || !A || !B || !C) return fail(QML_EINVAL, "bad gemm arguments");
+  if (m < 0 || nn < 0 || kk < 0) return fail(QML_EINVAL, "bad gemm arguments");
   if (precision != QML_FP64 && precision != QML_SPLIT_BF16)
     return fail(QML_EINVAL, "precision must be QML_FP64 or QML_SPLIT_BF16");
+  if (m == 0 || nn == 0) return QML_OK;
+  if (!C || (kk > 0 && (!A || !B))) return fail(QML_EINVAL, "bad gemm arguments");
   const int64_t ar = transA ? kk : m, ac = transA ? m : kk;
   const int64_t br = transB ? nn : kk, bc = transB ? kk : nn;
   if (lda < (ar > 0 ? ar : 1) || ldb < (br > 0 ? br : 1) || ldc < (m > 0 ? m : 1))
     return fail(QML_EINVAL, "leading dimension too small");
   if (lower && m != nn) return fail(QML_EINVAL, "lower needs a square C");
-  if (m == 0 || nn == 0) return QML_OK;
   Call c(stream);
   const double *Ad = c.in(A, (size_t)lda * ac, "A");
   const double *Bd = c.in(B, (size_t)ldb * bc, "B");
@@ -973,7 +1002,7 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
     c.cuda_ok(cudaMemcpyAsync(Cd, C, (size_t)ldc * nn * sizeof(double), cudaMemcpyHostToDevice, c.st),
               "C");
   if (!c.make_status()) return c.finish();
-  if (precision == QML_SPLIT_BF16) {
+  if (precision == QML_SPLIT_BF16 && kk > 0) {  // (kk == 0: C <- beta C, no digits)
     const bool shared = (A == B && lda == ldb && transA != transB && m == nn);
     void *ws = c.alloc<unsigned char>(ozaki_workspace_bytes(m, nn, kk, 0, shared), "split workspace");
     if (!ws) return c.finish();
