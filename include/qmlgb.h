@@ -120,8 +120,9 @@ qml_status qml_synthesize(const qml_problem *prob, const double *alm, const doub
  * C = Y Lambda_fid Y^T + N, C = L L^T, X = L^-1 Y, W = X^T X, block sums.
  * If plan is not NULL, *plan receives a plan holding L, X, F, the noise bias
  * and the normalisation matrices for qml_estimate (the analogue of handing a
- * Fisher object to the spectra stage).  Errors: QML_ENOTSPD if C is not
- * positive definite. */
+ * Fisher object to the spectra stage).  na = nspec (lmax - lmin + 1) must
+ * not exceed 2048 (QML_EINVAL).  Errors: QML_ENOTSPD if C is not positive
+ * definite. */
 qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan, void *stream);
 
 /* Quadratic estimates for nsims maps (n x nsims) against a plan from

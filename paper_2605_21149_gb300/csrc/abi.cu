@@ -493,6 +493,8 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
   if (plan_out) *plan_out = nullptr;
   const int na = prob->nspec * d.nl;
   const int naf = d.nspec_full * d.nl;
+  if (na + (na & 1) > 2048)
+    return fail(QML_EINVAL, "Fisher matrix larger than 2048 (nspec x (lmax - lmin + 1))");
   Call c(stream);
   Staged sp;
   if (!stage_problem(c, prob, d, sp, prob->cl_fid, true)) return c.finish();

@@ -35,6 +35,9 @@ constexpr int kJacobiThreads = 512;
 // sums (2 doubles per block): 4096 doubles hold 256 flag lines
 constexpr int kFlagOffset = 4096;
 constexpr int kMaxJacobiBlocks = 256;
+// largest matrix the schedule tables hold (na = nspec * nl <= 6 * 94 at
+// l <= 95, padded to even)
+constexpr int kMaxJacobiN = 2048;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   unsigned v;
@@ -154,6 +157,9 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
       ((int64_t)blockIdx.x + (int64_t)nblocks * (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
   double prev_off = 0.0;
   __shared__ double sred[2][kJacobiThreads / 32];
+  // the round-robin schedule of the current and the next round, rebuilt by
+  // each block at the start of a round: slot -> player and player -> slot
+  __shared__ short s_p0[kMaxJacobiN], s_p1[kMaxJacobiN], s_s1[kMaxJacobiN];
   unsigned *flags = (unsigned *)(red + kFlagOffset);
   unsigned epoch = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -204,6 +210,12 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
 
     for (int r = 0; r < n - 1; ++r) {
       const bool more = (r + 1 < n - 1);
+      for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        s_p0[x] = (short)player(x, r, n);
+        s_p1[x] = (short)player(x, r + 1, n);
+        s_s1[x] = (short)slot_of(x, r + 1, n);
+      }
+      __syncthreads();
       // tasks dealt out warp by warp across the blocks (warp w of block b takes
       // tasks 32 (b + nblocks w) ..), so every SM gets the same share of the
       // float64-heavy 2 x 2 blocks and of the eigenvector rows, and a warp's
@@ -215,8 +227,8 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
           while ((int64_t)(a + 1) * (a + 2) / 2 <= task) ++a;
           while ((int64_t)a * (a + 1) / 2 > task) --a;
           const int bb = (int)(task - (int64_t)a * (a + 1) / 2);
-          const int pa = player(bb, r, n), qa = player(n - 1 - bb, r, n);
-          const int pb = player(a, r, n), qb = player(n - 1 - a, r, n);
+          const int pa = s_p0[bb], qa = s_p0[n - 1 - bb];
+          const int pb = s_p0[a], qb = s_p0[n - 1 - a];
           const double ca = rcur[4 * bb], sa = rcur[4 * bb + 1];
           if (a == bb) {
             // J^T B J on the pair's own block; the residual off-diagonal kept
@@ -242,10 +254,10 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
               const int xs[4] = {pa, pa, qa, qa}, ys[4] = {pb, qb, pb, qb};
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                const int sx = slot_of(xs[e], r + 1, n);
+                const int sx = s_s1[xs[e]];
                 const int a2 = sx < h ? sx : n - 1 - sx;  // pair index in round r+1
-                if (player(n - 1 - a2, r + 1, n) == (sx < h ? ys[e] : -1) ||
-                    (sx >= h && player(a2, r + 1, n) == ys[e])) {
+                if (s_p1[n - 1 - a2] == (sx < h ? ys[e] : -1) ||
+                    (sx >= h && s_p1[a2] == ys[e])) {
                   if (m0 < 0) { m0 = e; a20 = a2; } else { m1 = e; a21 = a2; }
                 }
               }
@@ -284,7 +296,7 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
               auto diag_pair = [&](int e, int a2, double &dpp, double &dqq) {
                 const int x = (e >> 1) ? qa : pa;
                 const double dx = dp[e >> 1], dy = dq[e & 1];
-                const bool x_is_p = (player(a2, r + 1, n) == x);
+                const bool x_is_p = (s_p1[a2] == x);
                 dpp = x_is_p ? dx : dy;
                 dqq = x_is_p ? dy : dx;
               };
@@ -306,7 +318,7 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
         } else {
           const int vt = (int)(task - nblk);
           const int a = vt / n, row = vt - a * n;
-          const int pa = player(a, r, n), qa = player(n - 1 - a, r, n);
+          const int pa = s_p0[a], qa = s_p0[n - 1 - a];
           const double ca = rcur[4 * a], sa = rcur[4 * a + 1];
           const double vp = V[row + (int64_t)pa * n], vq = V[row + (int64_t)qa * n];
           V[row + (int64_t)pa * n] = ca * vp - sa * vq;
@@ -398,6 +410,7 @@ size_t fisher_eig_work_doubles(int na) {
 cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, double *Fm12,
                            double *eig_minmax, DevStatus *status, cudaStream_t st) {
   const int n = na + (na & 1);
+  if (n > kMaxJacobiN) return cudaErrorInvalidValue;  // callers check this first
   const size_t nn = (size_t)n * n;
   double *A0 = work, *A1 = work + nn, *V = work + 2 * nn, *S1 = work + 3 * nn,
          *S2 = work + 4 * nn, *red = work + 5 * nn, *rot = red + 2 * 4096;
