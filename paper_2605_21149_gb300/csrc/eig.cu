@@ -157,9 +157,18 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
       ((int64_t)blockIdx.x + (int64_t)nblocks * (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
   double prev_off = 0.0;
   __shared__ double sred[2][kJacobiThreads / 32];
-  // the round-robin schedule of the current and the next round, rebuilt by
-  // each block at the start of a round: slot -> player and player -> slot
-  __shared__ short s_p0[kMaxJacobiN], s_p1[kMaxJacobiN], s_s1[kMaxJacobiN];
+  // the round-robin schedule in shared memory, three rounds deep (buffer
+  // r mod 3): slot -> player and player -> slot.  Round r reads its own and
+  // round r+1's tables; the tables of round r+2 are written while the block
+  // waits at round r's barrier, into the buffer round r-1 used.
+  __shared__ short s_pt[3][kMaxJacobiN], s_sl[3][kMaxJacobiN];
+  auto fill_tables = [&](int r) {
+    short *pt = s_pt[r % 3], *sl = s_sl[r % 3];
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+      pt[x] = (short)player(x, r, n);
+      sl[x] = (short)slot_of(x, r, n);
+    }
+  };
   unsigned *flags = (unsigned *)(red + kFlagOffset);
   unsigned epoch = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -199,6 +208,8 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
     if (to <= 1e-32 * td) break;
     if (sweep > 0 && to > 0.25 * prev_off && to <= 1e-20 * td) break;
     prev_off = to;
+    fill_tables(0);
+    fill_tables(1);
     // rotations of round 0, one per block
     if (threadIdx.x == 0)
       for (int a = blockIdx.x; a < h; a += nblocks) {
@@ -210,12 +221,7 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
 
     for (int r = 0; r < n - 1; ++r) {
       const bool more = (r + 1 < n - 1);
-      for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        s_p0[x] = (short)player(x, r, n);
-        s_p1[x] = (short)player(x, r + 1, n);
-        s_s1[x] = (short)slot_of(x, r + 1, n);
-      }
-      __syncthreads();
+      const short *s_p0 = s_pt[r % 3], *s_p1 = s_pt[(r + 1) % 3], *s_s1 = s_sl[(r + 1) % 3];
       // tasks dealt out warp by warp across the blocks (warp w of block b takes
       // tasks 32 (b + nblocks w) ..), so every SM gets the same share of the
       // float64-heavy 2 x 2 blocks and of the eigenvector rows, and a warp's
@@ -247,6 +253,11 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
             const double cb = rcur[4 * a], sb = rcur[4 * a + 1];
             const double x00 = Aold[pa + (int64_t)pb * n], x01 = Aold[pa + (int64_t)qb * n];
             const double x10 = Aold[qa + (int64_t)pb * n], x11 = Aold[qa + (int64_t)qb * n];
+            // diagonal blocks of both old pairs, read with the entries above
+            // (needed only when a rotation of round r+1 is formed here)
+            const double g00 = Aold[pa + (int64_t)pa * n], g01 = Aold[pa + (int64_t)qa * n];
+            const double g11 = Aold[qa + (int64_t)qa * n], h00 = Aold[pb + (int64_t)pb * n];
+            const double h01 = Aold[pb + (int64_t)qb * n], h11 = Aold[qb + (int64_t)qb * n];
             // pairs of round r+1 among the four entries: at most two (the
             // pairs of a round are disjoint), found with integer tests only
             int m0 = -1, m1 = -1, a20 = 0, a21 = 0;
@@ -261,16 +272,6 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
                   if (m0 < 0) { m0 = e; a20 = a2; } else { m1 = e; a21 = a2; }
                 }
               }
-            }
-            // diagonal blocks of both old pairs (read only when a rotation is due)
-            double g00 = 0.0, g01 = 0.0, g11 = 0.0, h00 = 0.0, h01 = 0.0, h11 = 0.0;
-            if (m0 >= 0) {
-              g00 = Aold[pa + (int64_t)pa * n];
-              g01 = Aold[pa + (int64_t)qa * n];
-              g11 = Aold[qa + (int64_t)qa * n];
-              h00 = Aold[pb + (int64_t)pb * n];
-              h01 = Aold[pb + (int64_t)qb * n];
-              h11 = Aold[qb + (int64_t)qb * n];
             }
             // X J_b, J = [[c, s], [-s, c]]
             const double y00 = cb * x00 - sb * x01, y01 = sb * x00 + cb * x01;
@@ -325,6 +326,7 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
           V[row + (int64_t)qa * n] = sa * vp + ca * vq;
         }
       }
+      fill_tables(r + 2);  // made visible by the barrier's __syncthreads
       if (!grid_barrier(st, flags, epoch, nblocks)) return;
       double *tmp = Aold;
       Aold = Anew;
