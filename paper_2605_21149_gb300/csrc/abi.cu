@@ -290,18 +290,34 @@ void trsm_blocked(Call &c, const double *L, int64_t n, int64_t lda, const double
   }
 }
 
-// X <- L^-1 from X = I: the blocked forward substitution above restricted to
-// the columns that can be nonzero (block row j of L^-1 ends at column j+jb).
-void trinv_blocked(Call &c, const double *L, int64_t n, int64_t lda, const double *Linv,
-                   double *X, int64_t ldx) {
-  for (int64_t j = 0; j < n; j += kNB) {
-    const int64_t jb = (n - j) < kNB ? (n - j) : kNB;
-    const int64_t w = j + jb;
-    const double *Lb = Linv + (j / kNB) * kNB * kNB;
-    launch_dgemm(0, 0, jb, w, jb, 1.0, Lb, kNB, X + j, ldx, 0.0, X + j, ldx, 0, c.status, c.st);
-    if (w < n)
-      launch_dgemm(0, 0, n - w, w, jb, -1.0, L + w + j * lda, lda, X + j, ldx, 1.0, X + w, ldx, 0,
-                   c.status, c.st);
+// X <- L^-1 for a lower-triangular jb x jb block L (ld lda) by recursive
+// doubling, from the inverses Linv of its kNB-wide diagonal blocks:
+//   [[P, 0], [Q, R]]^-1 = [[P^-1, 0], [-R^-1 Q P^-1, R^-1]].
+// The kNB-block inverses go on the diagonal of X (zeros elsewhere); then for
+// b = kNB, 2 kNB, ... every pair of b-blocks gets T = Q P^-1 and its lower
+// left block -R^-1 T, each one batched product over the pairs (a last pair
+// whose second block is shorter than b gets its own two products).  log2 of
+// the block count steps instead of one per block row; T (scratch) holds
+// (kNBS/2)^2 doubles.
+void trinv_doubling(Call &c, const double *L, int64_t jb, int64_t lda, const double *Linv,
+                    double *X, int64_t ldx, double *T) {
+  launch_place_diag_inverses(Linv, jb, X, ldx, c.st);
+  for (int64_t b = kNB; b < jb; b *= 2) {
+    const int64_t full = jb / (2 * b);  // pairs with both blocks b long
+    if (full > 0) {
+      const int64_t sL = 2 * b + 2 * b * lda, sX = 2 * b + 2 * b * ldx;
+      launch_dgemm_batched(0, 0, b, b, b, 1.0, L + b, lda, sL, X, ldx, sX, 0.0, T, b, b * b,
+                           (int)full, c.status, c.st);
+      launch_dgemm_batched(0, 0, b, b, b, -1.0, X + b + b * ldx, ldx, sX, T, b, b * b, 0.0, X + b,
+                           ldx, sX, (int)full, c.status, c.st);
+    }
+    const int64_t r0 = full * 2 * b, b2 = jb - r0 - b;  // a last pair with a short R
+    if (b2 > 0) {
+      launch_dgemm(0, 0, b2, b, b, 1.0, L + (r0 + b) + r0 * lda, lda, X + r0 + r0 * ldx, ldx, 0.0,
+                   T, b2, 0, c.status, c.st);
+      launch_dgemm(0, 0, b2, b, b2, -1.0, X + (r0 + b) + (r0 + b) * ldx, ldx, T, b2, 0.0,
+                   X + (r0 + b) + r0 * ldx, ldx, 0, c.status, c.st);
+    }
   }
 }
 
@@ -329,7 +345,12 @@ struct Split {
   int nslices;
   void *ws = nullptr;
   size_t ws_bytes = 0;
-  double *eye = nullptr;  // kNBS x kNBS scratch for block inverses
+  double *tinv = nullptr;  // (kNBS/2)^2 scratch of the block-inverse doubling
+  // the doubling scratch, allocated on first use unless preset
+  double *tinv_scratch() {
+    if (!tinv) tinv = c->alloc<double>((size_t)(kNBS / 2) * (kNBS / 2), "inverse scratch");
+    return tinv;
+  }
   // use a caller-provided workspace (no allocation later)
   void preset(void *p, size_t bytes) {
     ws = p;
@@ -377,10 +398,11 @@ void potrf_split(Call &c, Split &sp, double *A, int64_t n, int64_t lda, double *
         launch_dgemm(0, 1, m2, m2, ib, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1, c.status, c.st);
       }
     }
-    // explicit inverse of the diagonal block: solve L_jj X = I (float64)
+    // explicit inverse of the diagonal block (float64)
     double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
-    launch_set_identity(Xinv, kNBS, jb, c.st);
-    trinv_blocked(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, kNBS);
+    double *T = sp.tinv_scratch();
+    if (!T) return;
+    trinv_doubling(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, kNBS, T);
     if (j + jb < n) {
       const int64_t m2 = n - j - jb;
       double *A21 = A + (j + jb) + j * lda;
@@ -781,6 +803,7 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
     cudaEvent_t done = nullptr;
     double *K, *lamL, *z, *rr, *Linv, *LinvB, *ldp;
     double *cl, *lnK, *lnl, *chi, *ld;  // fixed slots of the captured sequence
+    double *tinv;                       // block-inverse scratch (split)
     void *ws;
     size_t ws_bytes;
   };
@@ -809,6 +832,7 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
     wk[w].chi = c.alloc<double>(maxmaps);
     wk[w].ld = c.alloc<double>(1);
     wk[w].ws = any_split ? (void *)c.alloc<unsigned char>(wsb, "split workspace") : nullptr;
+    wk[w].tinv = any_split ? c.alloc<double>((size_t)(kNBS / 2) * (kNBS / 2)) : nullptr;
     wk[w].ws_bytes = wsb;
   }
   if (c.err != QML_OK) return c.finish();
@@ -838,6 +862,7 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
     if (masks[m].prob.precision == QML_SPLIT_BF16) {
       Split spl{&cw, masks[m].prob.nslices};
       spl.preset(W.ws, W.ws_bytes);
+      spl.tinv = W.tinv;
       potrf_split(cw, spl, W.K, k, k, W.Linv, W.LinvB, W.ldp, lnKp);
       trsm_split(cw, spl, W.K, k, k, W.LinvB, W.z, nm, k);
     } else {
@@ -968,13 +993,14 @@ qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, doubl
     // explicit inverses of the kNBS diagonal blocks (float64), then split products
     double *LinvB = c.alloc<double>((size_t)((n + kNBS - 1) / kNBS) * kNBS * kNBS);
     if (!LinvB) return c.finish();
+    Split spl{&c, 0};
+    double *T = spl.tinv_scratch();
+    if (!T) return c.finish();
     for (int64_t j = 0; j < n; j += kNBS) {
       const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
       double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
-      launch_set_identity(Xinv, kNBS, jb, c.st);
-      trinv_blocked(c, Ld + j + j * lda, jb, lda, Linv + (j / kNB) * kNB * kNB, Xinv, kNBS);
+      trinv_doubling(c, Ld + j + j * lda, jb, lda, Linv + (j / kNB) * kNB * kNB, Xinv, kNBS, T);
     }
-    Split spl{&c, 0};
     trsm_split(c, spl, Ld, n, lda, LinvB, Bd, nrhs, ldb);
   } else {
     trsm_blocked(c, Ld, n, lda, Linv, Bd, nrhs, ldb);

@@ -19,6 +19,12 @@ namespace {
 
 constexpr int BK = 16;
 
+// strided batch of products: blockIdx.z selects A + z sA, B + z sB, C + z sC
+struct DgBatch {
+  int count;
+  int64_t sA, sB, sC;
+};
+
 // RM x RN outputs per thread: a (16 RM) x (16 RN) tile per CTA.  Small
 // products take small tiles so that the grid still covers the SMs: with a
 // float64 pipe this narrow the per-SM rate, not the operand traffic, sets
@@ -28,8 +34,11 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
                                                     const double *A, int64_t lda, const double *B,
                                                     int64_t ldb, double beta, double *C,
                                                     int64_t ldc, int lower,
-                                                    const DevStatus *status) {
+                                                    const DevStatus *status, DgBatch bt) {
   constexpr int BM = 16 * RM, BN = 16 * RN;
+  A += (int64_t)blockIdx.z * bt.sA;
+  B += (int64_t)blockIdx.z * bt.sB;
+  C += (int64_t)blockIdx.z * bt.sC;
   if (status && *((volatile const int *)&status->code) != 0) return;
   const int64_t m0 = (int64_t)blockIdx.x * BM;
   const int64_t n0 = (int64_t)blockIdx.y * BN;
@@ -438,14 +447,6 @@ __global__ void loglike_finish_kernel(const double *chi2, const double *logdet, 
   if (j < nmaps) lnL[j] = -0.5 * (chi2[j] + *logdet);
 }
 
-__global__ void set_identity_kernel(double *X, int64_t ld, int64_t n) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ld * ld;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t % ld, j = t / ld;
-    X[t] = (i == j && i < n) ? 1.0 : 0.0;
-  }
-}
-
 int grid_for(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
@@ -472,37 +473,38 @@ int64_t dgemm_ctas(int64_t M, int64_t N, int bm, int bn, int lower) {
 template <bool TA, bool TB, int RM, int RN>
 void dgemm_go(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
               const double *B, int64_t ldb, double beta, double *C, int64_t ldc, int lower,
-              const DevStatus *status, cudaStream_t st) {
-  dim3 grid((unsigned)((M + 16 * RM - 1) / (16 * RM)), (unsigned)((N + 16 * RN - 1) / (16 * RN)));
+              const DevStatus *status, cudaStream_t st, DgBatch bt) {
+  dim3 grid((unsigned)((M + 16 * RM - 1) / (16 * RM)), (unsigned)((N + 16 * RN - 1) / (16 * RN)),
+            (unsigned)bt.count);
   dgemm_kernel<TA, TB, RM, RN><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
-                                                     lower, status);
+                                                     lower, status, bt);
   count_launch();
 }
 
 template <bool TA, bool TB>
 void dgemm_tile(int rm, int rn, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
                 int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
-                int lower, const DevStatus *status, cudaStream_t st) {
-#define QMLGB_DG(R1, R2)                                                                      \
-  if (rm == R1 && rn == R2) {                                                                 \
-    dgemm_go<TA, TB, R1, R2>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st); \
-    return;                                                                                   \
+                int lower, const DevStatus *status, cudaStream_t st, DgBatch bt) {
+#define QMLGB_DG(R1, R2)                                                                          \
+  if (rm == R1 && rn == R2) {                                                                     \
+    dgemm_go<TA, TB, R1, R2>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, bt); \
+    return;                                                                                       \
   }
   QMLGB_DG(4, 4) QMLGB_DG(2, 2) QMLGB_DG(1, 1) QMLGB_DG(1, 4) QMLGB_DG(2, 4) QMLGB_DG(4, 1)
   QMLGB_DG(4, 2)
 #undef QMLGB_DG
   // any other pair: the full tile, which is safe for every aliasing
-  dgemm_go<TA, TB, 4, 4>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+  dgemm_go<TA, TB, 4, 4>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, bt);
 }
 
 void dgemm_dispatch(int ta, int tb, int rm, int rn, int64_t M, int64_t N, int64_t K,
                     double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
                     double beta, double *C, int64_t ldc, int lower, const DevStatus *status,
-                    cudaStream_t st) {
-  if (!ta && !tb) dgemm_tile<false, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
-  else if (!ta && tb) dgemm_tile<false, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
-  else if (ta && !tb) dgemm_tile<true, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
-  else dgemm_tile<true, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+                    cudaStream_t st, DgBatch bt = DgBatch{1, 0, 0, 0}) {
+  if (!ta && !tb) dgemm_tile<false, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, bt);
+  else if (!ta && tb) dgemm_tile<false, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, bt);
+  else if (ta && !tb) dgemm_tile<true, false>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, bt);
+  else dgemm_tile<true, true>(rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, bt);
 }
 
 const int kCand[7][2] = {{4, 4}, {2, 4}, {4, 2}, {2, 2}, {1, 4}, {4, 1}, {1, 1}};
@@ -614,6 +616,25 @@ void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
   dgemm_dispatch(ta, tb, rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
 }
 
+// count products C_z <- alpha op(A_z) op(B_z) + beta C_z, X_z = X + z sX; the
+// tile is the largest whose grid (over all products) gives every SM two CTAs
+void launch_dgemm_batched(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                          const double *A, int64_t lda, int64_t sA, const double *B,
+                          int64_t ldb, int64_t sB, double beta, double *C, int64_t ldc,
+                          int64_t sC, int count, const DevStatus *status, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || count <= 0) return;
+  int rm = 1, rn = 1;
+  for (int i = 0; i < 7; ++i) {
+    if (dgemm_ctas(M, N, 16 * kCand[i][0], 16 * kCand[i][1], 0) * count >= 2 * 152) {
+      rm = kCand[i][0];
+      rn = kCand[i][1];
+      break;
+    }
+  }
+  dgemm_dispatch(ta, tb, rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, status, st,
+                 DgBatch{count, sA, sB, sC});
+}
+
 void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,
                        double *logdet_part, DevStatus *status, cudaStream_t st) {
   set_diag_smem();
@@ -661,8 +682,22 @@ void launch_loglike_finish(const double *chi2, const double *logdet, int nmaps, 
   { loglike_finish_kernel<<<(nmaps + 127) / 128, 128, 0, st>>>(chi2, logdet, nmaps, lnL); count_launch(); }
 }
 
-void launch_set_identity(double *X, int64_t ld, int64_t n, cudaStream_t st) {
-  { set_identity_kernel<<<grid_for(ld * ld), 256, 0, st>>>(X, ld, n); count_launch(); }
+// X (ld x ld, first n rows / columns used) <- block diagonal of the kNB x kNB
+// inverses Dinv (consecutive blocks of kNB * kNB), zeros elsewhere
+__global__ void place_diag_kernel(const double *Dinv, int64_t n, double *X, int64_t ld) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ld * ld;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t % ld, c = t / ld;
+    double v = 0.0;
+    if (r < n && c < n && r / kNB == c / kNB)
+      v = Dinv[(r / kNB) * kNB * kNB + (r % kNB) + (c % kNB) * kNB];
+    X[t] = v;
+  }
+}
+
+void launch_place_diag_inverses(const double *Dinv, int64_t n, double *X, int64_t ld,
+                                cudaStream_t st) {
+  { place_diag_kernel<<<grid_for(ld * ld), 256, 0, st>>>(Dinv, n, X, ld); count_launch(); }
 }
 
 }  // namespace qmlgb

@@ -53,6 +53,11 @@ void launch_mix_lambda(double *Y, int64_t ldy, int n, int nc, int k0, int lmin, 
 void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                   double *C, int64_t ldc, int lower, const DevStatus *status, cudaStream_t st);
+// strided batch: product z uses A + z sA, B + z sB, C + z sC (no aliasing)
+void launch_dgemm_batched(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                          const double *A, int64_t lda, int64_t sA, const double *B,
+                          int64_t ldb, int64_t sB, double beta, double *C, int64_t ldc,
+                          int64_t sC, int count, const DevStatus *status, cudaStream_t st);
 
 constexpr int kNB = 64;  // Cholesky / TRSM block size
 
@@ -66,8 +71,11 @@ void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Li
 // (block b at Linv + b kNB^2, ld kNB), one CTA per block.
 void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,
                          DevStatus *status, cudaStream_t st);
-// ld x ld matrix with the n x n identity in its top-left corner, zeros elsewhere
-void launch_set_identity(double *X, int64_t ld, int64_t n, cudaStream_t st);
+// X <- block diagonal of the kNB x kNB inverses Dinv (first n rows), zeros
+// elsewhere in its ld x ld
+void launch_place_diag_inverses(const double *Dinv, int64_t n, double *X, int64_t ld,
+                                cudaStream_t st);
+
 void launch_sum_logdet(const double *parts, int nparts, double *out, cudaStream_t st);
 void launch_copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t n,
                        cudaStream_t st);
