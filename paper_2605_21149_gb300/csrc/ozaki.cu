@@ -57,6 +57,8 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 // most kChunkK 2^10 (n_L + 2) <= 2^10 2^10 12 < 2^24 for the n_L <= 10 pairs a
 // level has (S <= 10), and level 2 at most kChunkK 2^12 = 2^22: exact.
 constexpr int kChunkK = 1024;
+// most digits per operand element (beta S <= 62 with beta = 6)
+constexpr int kMaxSlices = 10;
 
 // ------------------------------------------------------------ PTX helpers --
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -431,31 +433,63 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------- digits ----
-// exponent e with max |x| <= 2^e over one logical row (frexp convention)
-__global__ void row_exponent_kernel(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk,
-                                    int *e, int Rpad) {
-  // one warp per row; lanes stride over k
+// Row maxima of |x| as float64 bit patterns with the sign cleared (for
+// non-negative float64 values the integer order is the numeric order).
+// Rows strided, k contiguous: one warp per row, lanes stride over k.
+__global__ void rowmax_kcontig_kernel(const double *X, int64_t R, int64_t K, int64_t sr,
+                                      unsigned long long *bits, int Rpad) {
   const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= Rpad) return;
-  // max |x| on the bit patterns with the sign cleared (for non-negative
-  // float64 values the integer order is the numeric order)
-  long long mb = 0;
+  unsigned long long mb = 0;
   if (r < R)
     for (int64_t k = lane; k < K; k += 32) {
-      const long long b = __double_as_longlong(X[r * sr + k * sk]) & 0x7FFFFFFFFFFFFFFFll;
+      const unsigned long long b = (unsigned long long)__double_as_longlong(X[r * sr + k]) &
+                                   0x7FFFFFFFFFFFFFFFull;
       mb = b > mb ? b : mb;
     }
   for (int o = 16; o > 0; o >>= 1) {
-    const long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o);
     mb = t > mb ? t : mb;
   }
-  if (lane == 0) {
-    int ex = 0;
-    const double mx = __longlong_as_double(mb);
-    if (mx > 0.0) frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1): mx < 2^ex
-    e[r] = ex;
+  if (lane == 0) bits[r] = mb;
+}
+
+// Rows contiguous (column-major operand): block (x, y) covers 32 rows and 256
+// values of k; a warp reads 32 consecutive rows at one k (coalesced), the 8
+// warps take every 8th k, and the block's maximum per row joins the others
+// with atomicMax (bits zeroed beforehand).
+__global__ void rowmax_rcontig_kernel(const double *X, int64_t R, int64_t K, int64_t sk,
+                                      unsigned long long *bits) {
+  __shared__ unsigned long long part[8][32];
+  const int rl = threadIdx.x & 31, kg = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * 32 + rl;
+  const int64_t kc0 = (int64_t)blockIdx.y * 256, kc1 = (kc0 + 256 < K) ? kc0 + 256 : K;
+  unsigned long long mb = 0;
+  if (r < R)
+    for (int64_t k = kc0 + kg; k < kc1; k += 8) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(X[r + k * sk]) &
+                                   0x7FFFFFFFFFFFFFFFull;
+      mb = b > mb ? b : mb;
+    }
+  part[kg][rl] = mb;
+  __syncthreads();
+  if (kg == 0 && r < R) {
+    for (int q = 1; q < 8; ++q) mb = part[q][rl] > mb ? part[q][rl] : mb;
+    if (mb) atomicMax(&bits[r], mb);
   }
+}
+
+// exponent e of a row maximum m (frexp convention: m < 2^e, 0 for m = 0)
+__device__ __forceinline__ int exponent_of(unsigned long long m) {
+  if (m == 0) return 0;
+  const int E = (int)(m >> 52);
+  if (E == 0) {  // subnormal maximum
+    int ex = 0;
+    frexp(__longlong_as_double((long long)m), &ex);
+    return ex;
+  }
+  return E - 1022;  // m = 1.f 2^(E-1023) = (1.f / 2) 2^(E-1022)
 }
 
 // round(x 2^sh) to the nearest integer, ties to even (as __double2ll_rn of
@@ -489,7 +523,8 @@ __device__ __forceinline__ long long scaled_round(double x, int sh) {
 // [-2^(beta-1), 2^(beta-1)), the top one in [-2^beta, 2^beta].  Tile 32 x 64 via
 // shared memory so both the read and the K-contiguous write coalesce.
 __global__ void slice_kernel(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk,
-                             const int *e, int S, int beta, __nv_bfloat16 *D, int Rpad, int Kpad) {
+                             const unsigned long long *bits, int *e, int S, int beta,
+                             __nv_bfloat16 *D, int Rpad, int Kpad) {
   __shared__ double tile[32][65];
   const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
   const int tid = threadIdx.x;  // 256 threads
@@ -514,24 +549,40 @@ __global__ void slice_kernel(const double *X, int64_t R, int64_t K, int64_t sr, 
   for (int rq = rr; rq < 32; rq += 8) {
     const int64_t r = r0 + rq;
     if (r >= Rpad) continue;
-    const int er = (r < R) ? e[r] : 0;
-    long long F[2];
-    for (int h = 0; h < 2; ++h) F[h] = scaled_round(tile[rq][kp + h], beta * S - er);
-    const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
-    for (int s = S; s >= 1; --s) {
-      float d[2];
+    const int er = (r < R) ? exponent_of(bits[r]) : 0;
+    if (blockIdx.x == 0 && kp == 0) e[r] = er;
+    // digit i (from the bottom, i < S - 1): the signed base-2^beta recurrence
+    // d = ((F + 2^(beta-1)) mod 2^beta) - 2^(beta-1), F <- (F - d) / 2^beta,
+    // run on chunks of up to 4 digits in 32-bit arithmetic (the chunk's carry
+    // joins the rest of F at its end); digit S - 1 is what remains
+    long long Fh[2];
+    int lo[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) Fh[h] = scaled_round(tile[rq][kp + h], beta * S - er);
+    const int half = 1 << (beta - 1), mask = (1 << beta) - 1;
+#pragma unroll
+    for (int i = 0; i < kMaxSlices; ++i) {
+      if (i >= S) break;
+      int d[2];
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
-        long long dig;
-        if (s > 1) {
-          dig = ((F[h] + half) & mask) - half;
-          F[h] = (F[h] - dig) >> beta;
+        if (i < S - 1) {
+          if ((i & 3) == 0) {
+            const int nd = (S - 1 - i) < 4 ? (S - 1 - i) : 4;
+            const int nb = beta * nd;
+            lo[h] = (int)(Fh[h] & ((1LL << nb) - 1));
+            Fh[h] >>= nb;
+          }
+          d[h] = ((lo[h] + half) & mask) - half;
+          lo[h] = (lo[h] - d[h]) >> beta;
+          if ((i & 3) == 3 || i == S - 2) Fh[h] += lo[h];
         } else {
-          dig = F[h];
+          d[h] = (int)Fh[h];
         }
-        d[h] = (float)dig;
       }
-      __nv_bfloat162 v = __floats2bfloat162_rn(d[0], d[1]);
-      *(__nv_bfloat162 *)(D + ((int64_t)(s - 1) * Rpad + r) * Kpad + k0 + kp) = v;
+      // digit i from the bottom is digit s = S - i of the expansion
+      __nv_bfloat162 v = __floats2bfloat162_rn((float)d[0], (float)d[1]);
+      *(__nv_bfloat162 *)(D + ((int64_t)(S - i - 1) * Rpad + r) * Kpad + k0 + kp) = v;
     }
   }
 }
@@ -585,9 +636,24 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K, int nslices, bool 
   int S, beta;
   ozaki_choose(K, nslices, S, beta);
   const int64_t Mpad = rup(M, OBM), Npad = rup(N, OBN), Kpad = rup(K, OBK);
-  size_t b = rup((size_t)S * Mpad * Kpad * 2, 1024) + rup(4 * (size_t)Mpad, 1024);
-  if (!shared_operand) b += rup((size_t)S * Npad * Kpad * 2, 1024) + rup(4 * (size_t)Npad, 1024);
+  size_t b = rup((size_t)S * Mpad * Kpad * 2, 1024) + rup(12 * (size_t)Mpad, 1024);
+  if (!shared_operand) b += rup((size_t)S * Npad * Kpad * 2, 1024) + rup(12 * (size_t)Npad, 1024);
   return b;
+}
+
+// row maxima of one operand (element (r, k) at X[r sr + k sk], one of the
+// strides 1) into bits[0 .. Rpad), padding rows 0
+void launch_rowmax(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+                   unsigned long long *bits, int64_t Rpad, cudaStream_t st) {
+  if (sr == 1) {
+    cudaMemsetAsync(bits, 0, (size_t)Rpad * sizeof(unsigned long long), st);
+    dim3 g((unsigned)((Rpad + 31) / 32), (unsigned)((K + 255) / 256));
+    rowmax_rcontig_kernel<<<g, 256, 0, st>>>(X, R, K, sk, bits);
+  } else {
+    rowmax_kcontig_kernel<<<(unsigned)((Rpad + 7) / 8), 256, 0, st>>>(X, R, K, sr, bits,
+                                                                      (int)Rpad);
+  }
+  count_launch();
 }
 
 template <int OSTAGES>
@@ -621,32 +687,31 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   __nv_bfloat16 *DA = (__nv_bfloat16 *)w;
   w += rup((size_t)S * Mpad * Kpad * 2, 1024);
   int *ea = (int *)w;
-  w += rup(4 * (size_t)Mpad, 1024);
+  unsigned long long *ma = (unsigned long long *)(w + 4 * (size_t)Mpad);  // Mpad % 128 == 0
+  w += rup(12 * (size_t)Mpad, 1024);
   __nv_bfloat16 *DB = DA;
   int *eb = ea;
+  unsigned long long *mb = ma;
   if (!shared) {
     DB = (__nv_bfloat16 *)w;
     w += rup((size_t)S * Npad * Kpad * 2, 1024);
     eb = (int *)w;
+    mb = (unsigned long long *)(w + 4 * (size_t)Npad);
   }
   // op(A)[i,k] = A[i + k lda] (ta = 0) or A[k + i lda]
   const int64_t asr = ta ? lda : 1, ask = ta ? 1 : lda;
   // op(B) column j, entry k: B[k + j ldb] (tb = 0) or B[j + k ldb]
   const int64_t bsr = tb ? 1 : ldb, bsk = tb ? ldb : 1;
   {
-    dim3 g((unsigned)((Mpad + 7) / 8));
-    row_exponent_kernel<<<g, 256, 0, st>>>(A, M, K, asr, ask, ea, (int)Mpad);
-    count_launch();
+    launch_rowmax(A, M, K, asr, ask, ma, Mpad, st);
     dim3 gs((unsigned)(Kpad / 64), (unsigned)(Mpad / 32));
-    slice_kernel<<<gs, 256, 0, st>>>(A, M, K, asr, ask, ea, S, beta, DA, (int)Mpad, (int)Kpad);
+    slice_kernel<<<gs, 256, 0, st>>>(A, M, K, asr, ask, ma, ea, S, beta, DA, (int)Mpad, (int)Kpad);
     count_launch();
   }
   if (!shared) {
-    dim3 g((unsigned)((Npad + 7) / 8));
-    row_exponent_kernel<<<g, 256, 0, st>>>(B, N, K, bsr, bsk, eb, (int)Npad);
-    count_launch();
+    launch_rowmax(B, N, K, bsr, bsk, mb, Npad, st);
     dim3 gs((unsigned)(Kpad / 64), (unsigned)(Npad / 32));
-    slice_kernel<<<gs, 256, 0, st>>>(B, N, K, bsr, bsk, eb, S, beta, DB, (int)Npad, (int)Kpad);
+    slice_kernel<<<gs, 256, 0, st>>>(B, N, K, bsr, bsk, mb, eb, S, beta, DB, (int)Npad, (int)Kpad);
     count_launch();
   }
   CUtensorMap mA, mB;
