@@ -384,7 +384,11 @@ void potrf_split(Call &c, Split &sp, double *A, int64_t n, int64_t lda, double *
   for (int64_t j = 0; j < n; j += kNBS) {
     const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
     double *Ajj = A + j + j * lda;
-    // float64 blocked factorisation of the diagonal block (64-wide)
+    double *T = sp.tinv_scratch();  // (kNBS/2)^2 doubles: the panel block below, then the doubling
+    if (!T) return;
+    // float64 blocked factorisation of the diagonal block (64-wide); each
+    // solved block below a 64-block goes through T (m2 x 64 <= (kNBS - kNB)
+    // x kNB) so that its product can take small tiles (not in place)
     for (int64_t i = 0; i < jb; i += kNB) {
       const int64_t ib = (jb - i) < kNB ? (jb - i) : kNB;
       double *Lb = Linv64 + ((j + i) / kNB) * kNB * kNB;
@@ -394,14 +398,13 @@ void potrf_split(Call &c, Split &sp, double *A, int64_t n, int64_t lda, double *
         const int64_t m2 = jb - i - ib;
         double *A21 = Ajj + (i + ib) + i * lda;
         double *A22 = Ajj + (i + ib) + (i + ib) * lda;
-        launch_dgemm(0, 1, m2, ib, ib, 1.0, A21, lda, Lb, kNB, 0.0, A21, lda, 0, c.status, c.st);
-        launch_dgemm(0, 1, m2, m2, ib, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1, c.status, c.st);
+        launch_dgemm(0, 1, m2, ib, ib, 1.0, A21, lda, Lb, kNB, 0.0, T, m2, 0, c.status, c.st);
+        launch_dgemm(0, 1, m2, m2, ib, -1.0, T, m2, T, m2, 1.0, A22, lda, 1, c.status, c.st);
+        launch_copy_matrix(T, m2, A21, lda, m2, ib, c.st);
       }
     }
     // explicit inverse of the diagonal block (float64)
     double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
-    double *T = sp.tinv_scratch();
-    if (!T) return;
     trinv_doubling(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, kNBS, T);
     if (j + jb < n) {
       const int64_t m2 = n - j - jb;
