@@ -8,6 +8,7 @@
 // tx + 16 i and columns ty + 16 j (i, j < 4), so a warp's stores cover 16
 // consecutive rows of 2 columns and its shared reads broadcast.
 #include "internal.cuh"
+#include "ptx.cuh"
 
 #include <math.h>
 
@@ -230,12 +231,16 @@ __device__ void invert_lower_blocked(double (*a)[kLDA], double (*x)[kLDA], const
   }
 }
 
-// With factor == 0 the block already holds L and only the inverse is formed
-// (blockIdx.x selects the block: j0 = blockIdx.x * kNB).
-__global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda, int64_t n,
+// mode 1: factor and invert; mode 0: the block already holds L and only the
+// inverse is formed (blockIdx.x selects the block: j0 = blockIdx.x * kNB);
+// mode 2: factor only, and Linv receives the scaled coefficients of the row
+// solve x L^T = b instead of an inverse (kernel trsm_rows_kernel):
+//   Linv[c kNB + j] = L_jc / L_jj (j > c),  1 / L_cc (j = c),  0 otherwise.
+__global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t lda, int64_t n,
                                                          int64_t j0, double *Linv,
                                                          double *logdet_part,
-                                                         DevStatus *status, int factor) {
+                                                         DevStatus *status, int mode) {
+  const int factor = mode != 0;
   extern __shared__ __align__(16) double dsm[];
   double(*a)[kLDA] = (double(*)[kLDA])dsm;
   double(*x)[kLDA] = (double(*)[kLDA])(dsm + kNB * kLDA);
@@ -250,10 +255,21 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
     Linv += (int64_t)blockIdx.x * kNB * kNB;
   }
   const int jb = (int)((n - j0) < kNB ? (n - j0) : kNB);
-  for (int t = tid; t < kNB * kNB; t += blockDim.x) {
-    int i = t % kNB, j = t / kNB;
-    a[i][j] = (i < jb && j < jb && i >= j) ? A[i + j * lda] : 0.0;
-    x[i][j] = 0.0;
+  // the tile's loads in two batches of 8 per thread, each batch in flight together
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = tid + 256 * (8 * h + u), i = t % kNB, j = t / kNB;
+      v[u] = (i < jb && j < jb && i >= j) ? A[i + j * lda] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = tid + 256 * (8 * h + u), i = t % kNB, j = t / kNB;
+      a[i][j] = v[u];
+      if (mode != 2) x[i][j] = 0.0;
+    }
   }
   if (tid == 0) *bad = 0;
   __syncthreads();
@@ -360,6 +376,15 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) *logdet_part = 2.0 * s;
     }
+    if (mode == 2) {
+      for (int t = tid; t < kNB * kNB; t += blockDim.x) {
+        const int j = t % kNB, c = t / kNB;
+        double v = 0.0;
+        if (j < jb && c < jb) v = j > c ? a[j][c] * invd[j] : (j == c ? invd[c] : 0.0);
+        Linv[t] = v;
+      }
+      return;
+    }
   } else {
     if (tid < jb) invd[tid] = 1.0 / a[tid][tid];
     __syncthreads();
@@ -368,6 +393,68 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int64_t lda,
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {
     int i = t % kNB, j = t / kNB;
     Linv[i + j * kNB] = (i < jb && j < jb) ? x[i][j] : 0.0;
+  }
+}
+
+// X = B L^-T for the m x ib rows B (ld ldb) and a lower-triangular ib x ib
+// block L, i.e. each row solves x L^T = b by forward substitution,
+//   x_c = b_c / L_cc - sum_{k<c} (L_ck / L_cc) x_k,
+// from the scaled coefficients S (kNB x kNB, S[k kNB + c] = L_ck / L_cc for
+// c > k, S[c kNB + c] = 1 / L_cc: mode 2 of potrf_diag_kernel).  One warp per
+// CTA, two rows per warp, 16 lanes per row: lane g keeps columns g, g + 16,
+// g + 32, g + 48 in registers, x_c reaches the row's other lanes by shuffle and
+// every later column takes one fma per step.  S comes into shared memory by one
+// bulk copy (bounded wait).  X goes to B (in place) and to T (ld ldt).
+constexpr int kTrsmRows = 2;
+__global__ void __launch_bounds__(32) trsm_rows_kernel(const double *S, int ib, double *B,
+                                                       int64_t ldb, int64_t m, double *T,
+                                                       int64_t ldt, DevStatus *status) {
+  __shared__ __align__(128) double s[kNB * kNB];
+  __shared__ __align__(8) uint64_t bar;
+  if (*((volatile int *)&status->code) != 0) return;
+  const int lane = threadIdx.x, g = lane & 15;
+  const int64_t row = (int64_t)blockIdx.x * kTrsmRows + (lane >> 4);
+  const bool on = row < m;
+  const uint32_t b = smem_u32(&bar);
+  if (lane == 0) {
+    mbar_init(b, 1);
+    fence_mbar_init();
+    mbar_expect_tx(b, (uint32_t)sizeof(s));
+    bulk_load(smem_u32(s), S, (uint32_t)sizeof(s), b);
+  }
+  double v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int col = g + 16 * q;
+    v[q] = (on && col < ib) ? B[row + (int64_t)col * ldb] : 0.0;
+  }
+  __syncwarp();
+  if (!mbar_wait(b, 0, status)) {
+    mbar_drain_wait(b, 0);
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] *= s[(g + 16 * q) * (kNB + 1)];
+#pragma unroll
+  for (int qc = 0; qc < 4; ++qc) {
+#pragma unroll
+    for (int g0 = 0; g0 < 16; ++g0) {
+      const int c = 16 * qc + g0;
+      const double xc = __shfl_sync(0xffffffffu, v[qc], g0, 16);
+#pragma unroll
+      for (int q = qc; q < 4; ++q)
+        if (g + 16 * q > c) v[q] = fma(-s[c * kNB + g + 16 * q], xc, v[q]);
+    }
+  }
+  if (on) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = g + 16 * q;
+      if (col < ib) {
+        B[row + (int64_t)col * ldb] = v[q];
+        T[row + (int64_t)col * ldt] = v[q];
+      }
+    }
   }
 }
 
@@ -639,6 +726,19 @@ void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Li
                        double *logdet_part, DevStatus *status, cudaStream_t st) {
   set_diag_smem();
   { potrf_diag_kernel<<<1, 256, kDiagSmem, st>>>(A, lda, n, j0, Linv, logdet_part, status, 1); count_launch(); }
+}
+
+void launch_potrf_diag_factor(double *A, int64_t lda, int64_t n, int64_t j0, double *S,
+                              double *logdet_part, DevStatus *status, cudaStream_t st) {
+  set_diag_smem();
+  { potrf_diag_kernel<<<1, 256, kDiagSmem, st>>>(A, lda, n, j0, S, logdet_part, status, 2); count_launch(); }
+}
+
+void launch_trsm_rows(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m, double *T,
+                      int64_t ldt, DevStatus *status, cudaStream_t st) {
+  if (m <= 0 || ib <= 0) return;
+  const unsigned grid = (unsigned)((m + kTrsmRows - 1) / kTrsmRows);
+  { trsm_rows_kernel<<<grid, 32, 0, st>>>(S, (int)ib, B, ldb, m, T, ldt, status); count_launch(); }
 }
 
 void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,

@@ -67,6 +67,16 @@ constexpr int kNB = 64;  // Cholesky / TRSM block size
 // 2 sum ln L_ii into *logdet_part.
 void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,
                        double *logdet_part, DevStatus *status, cudaStream_t st);
+// Factor only (mode 2 of the diagonal kernel): S (kNB x kNB) receives the
+// scaled coefficients of the row solve, S[k kNB + c] = L_ck / L_cc (c > k),
+// S[c kNB + c] = 1 / L_cc.
+void launch_potrf_diag_factor(double *A, int64_t lda, int64_t n, int64_t j0, double *S,
+                              double *logdet_part, DevStatus *status, cudaStream_t st);
+// B <- B L^-T (m rows, ib <= kNB columns, ld ldb) by forward substitution
+// from the coefficients S of launch_potrf_diag_factor; the result also goes
+// to T (ld ldt).
+void launch_trsm_rows(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m, double *T,
+                      int64_t ldt, DevStatus *status, cudaStream_t st);
 // Inverses of every kNB diagonal block of an existing lower factor L
 // (block b at Linv + b kNB^2, ld kNB), one CTA per block.
 void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,

@@ -33,6 +33,7 @@
 // Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the CTA records
 // QML_ETIMEOUT, drains what it issued, frees TMEM and returns.
 #include "internal.cuh"
+#include "ptx.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -61,56 +62,6 @@ constexpr int kChunkK = 1024;
 constexpr int kMaxSlices = 10;
 
 // ------------------------------------------------------------ PTX helpers --
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s budget per wait
-
-// bounded wait; false (and the status word set) when the time budget runs out
-// or another role already failed
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevStatus *st) {
-  const uint64_t t0 = global_ns();
-  for (unsigned i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 63) {
-      if (*((volatile int *)&st->code) != 0) return false;
-      if (global_ns() - t0 > kWaitNs) break;
-    }
-  }
-  atomicCAS(&st->code, 0, 5 /* QML_ETIMEOUT */);
-  return false;
-}
-// bounded wait used while draining after a failure (no status update)
-__device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitNs) return;
-}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int x, int y) {
   asm volatile(
