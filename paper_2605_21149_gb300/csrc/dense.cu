@@ -8,6 +8,7 @@
 // tx + 16 i and columns ty + 16 j (i, j < 4), so a warp's stores cover 16
 // consecutive rows of 2 columns and its shared reads broadcast.
 #include "internal.cuh"
+#include "dfloat.cuh"
 #include "ptx.cuh"
 
 #include <math.h>
@@ -233,14 +234,15 @@ __device__ void invert_lower_blocked(double (*a)[kLDA], double (*x)[kLDA], const
 
 // mode 1: factor and invert; mode 0: the block already holds L and only the
 // inverse is formed (blockIdx.x selects the block: j0 = blockIdx.x * kNB);
-// mode 2: factor only, and Linv receives the scaled coefficients of the row
-// solve x L^T = b instead of an inverse (kernel trsm_rows_kernel):
-//   Linv[c kNB + j] = L_jc / L_jj (j > c),  1 / L_cc (j = c),  0 otherwise.
+// mode 3: as mode 0, but the factor comes from the float-float slot that
+// potrf_diag_df_kernel left at Linv (packed L~ and the row exponents k_i,
+// L_ij = L~_ij 2^k_i): it is written into A (lower triangle), 2 sum ln L_ii
+// goes to logdet_part[blockIdx.x], and the inverse replaces the slot.
 __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t lda, int64_t n,
                                                          int64_t j0, double *Linv,
                                                          double *logdet_part,
                                                          DevStatus *status, int mode) {
-  const int factor = mode != 0;
+  const int factor = mode == 1;
   extern __shared__ __align__(16) double dsm[];
   double(*a)[kLDA] = (double(*)[kLDA])dsm;
   double(*x)[kLDA] = (double(*)[kLDA])(dsm + kNB * kLDA);
@@ -255,6 +257,39 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
     Linv += (int64_t)blockIdx.x * kNB * kNB;
   }
   const int jb = (int)((n - j0) < kNB ? (n - j0) : kNB);
+  if (mode == 3) {
+    const float2 *slot = (const float2 *)Linv;
+    const int *kx = (const int *)(slot + packed_off(kNB, kNB));
+    for (int t = tid; t < kNB * kNB; t += blockDim.x) {
+      const int i = t % kNB, j = t / kNB;
+      double v = 0.0;
+      if (i >= j && i < jb && j < jb) {
+        const float2 f = slot[packed_off(j, kNB) + (i - j)];
+        v = df_to_double({f.x, f.y}, kx[i]);
+        A[i + j * lda] = v;
+      }
+      a[i][j] = v;
+      x[i][j] = 0.0;
+    }
+    __syncthreads();
+    // log det part: one log per thread of warps 0 and 1, fixed-order sums
+    if (warp < 2) {
+      double sl = tid < jb ? log(a[tid][tid]) : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);
+      if (lane == 0) tmp[warp] = sl;
+    }
+    __syncthreads();
+    if (tid == 0) logdet_part[blockIdx.x] = 2.0 * (tmp[0] + tmp[1]);
+    if (tid < jb) invd[tid] = 1.0 / a[tid][tid];
+    __syncthreads();
+    invert_lower_blocked(a, x, invd, jb, tmp);
+    for (int t = tid; t < kNB * kNB; t += blockDim.x) {
+      int i = t % kNB, j = t / kNB;
+      Linv[i + j * kNB] = (i < jb && j < jb) ? x[i][j] : 0.0;
+    }
+    return;
+  }
   // the tile's loads in two batches of 8 per thread, each batch in flight together
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -268,7 +303,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
     for (int u = 0; u < 8; ++u) {
       const int t = tid + 256 * (8 * h + u), i = t % kNB, j = t / kNB;
       a[i][j] = v[u];
-      if (mode != 2) x[i][j] = 0.0;
+      x[i][j] = 0.0;
     }
   }
   if (tid == 0) *bad = 0;
@@ -376,15 +411,6 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) *logdet_part = 2.0 * s;
     }
-    if (mode == 2) {
-      for (int t = tid; t < kNB * kNB; t += blockDim.x) {
-        const int j = t % kNB, c = t / kNB;
-        double v = 0.0;
-        if (j < jb && c < jb) v = j > c ? a[j][c] * invd[j] : (j == c ? invd[c] : 0.0);
-        Linv[t] = v;
-      }
-      return;
-    }
   } else {
     if (tid < jb) invd[tid] = 1.0 / a[tid][tid];
     __syncthreads();
@@ -396,20 +422,179 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
   }
 }
 
-// X = B L^-T for the m x ib rows B (ld ldb) and a lower-triangular ib x ib
-// block L, i.e. each row solves x L^T = b by forward substitution,
-//   x_c = b_c / L_cc - sum_{k<c} (L_ck / L_cc) x_k,
-// from the scaled coefficients S (kNB x kNB, S[k kNB + c] = L_ck / L_cc for
-// c > k, S[c kNB + c] = 1 / L_cc: mode 2 of potrf_diag_kernel).  One warp per
-// CTA, two rows per warp, 16 lanes per row: lane g keeps columns g, g + 16,
-// g + 32, g + 48 in registers, x_c reaches the row's other lanes by shuffle and
-// every later column takes one fma per step.  S comes into shared memory by one
-// bulk copy (bounded wait).  X goes to B (in place) and to T (ld ldt).
+// Float-float factor of one diagonal block of the split-precision Cholesky
+// (rows and columns j0 .. j0 + jb - 1 of A, lower triangle; A is only read).
+// The block is scaled symmetrically by powers of two, a~_ij = a_ij
+// 2^-(k_i + k_j) with k_i = floor(e_i / 2) for the binary exponent e_i of a_ii
+// (so a~_ii lies in [1, 4) and every float-float entry stays far from the
+// float range limits), then factored right-looking as in potrf_diag_kernel:
+// eight columns per panel in warp 0 (pivots and column entries by shuffle),
+// rank-8 updates of the trailing triangle by all threads.  Two outputs of
+// kSlot float2 each (packed lower triangle, then the 64 exponents as int):
+//   Lslot: L~, with L_ij = L~_ij 2^k_i (mode 3 of potrf_diag_kernel turns it
+//          into float64 L, the log det part and the inverse);
+//   Sout:  the coefficients of the row solve x L^T = b (trsm_rows_df_kernel),
+//          S(j, c) = L~_jc / L~_jj for j > c and S(c, c) = 1 / L~_cc.
+// A pivot that is not positive and finite sets QML_ENOTSPD with its column.
+constexpr int kSlot = packed_off(kNB, kNB) + kNB / 2;
+__global__ void __launch_bounds__(256, 1) potrf_diag_df_kernel(const double *A, int64_t lda,
+                                                                int64_t n, int64_t j0,
+                                                                float2 *Lslot, float2 *Sout,
+                                                                DevStatus *status) {
+  __shared__ dfl a[kNB][kNB + 1];
+  __shared__ dfl rd[kNB];
+  __shared__ int kx[kNB];
+  __shared__ int bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (*((volatile int *)&status->code) != 0) return;
+  const int jb = (int)((n - j0) < kNB ? (n - j0) : kNB);
+  constexpr int kPer = kNB * kNB / 256;
+  double raw[kPer];  // all loads of the tile in flight together
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int t = tid + 256 * u, i = t % kNB, j = t / kNB;
+    raw[u] = (i < jb && j < jb && i >= j) ? A[i + j * lda] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int t = tid + 256 * u, i = t % kNB, j = t / kNB;
+    if (i == j) {
+      const int E = (int)(((unsigned)__double2hiint(raw[u]) >> 20) & 0x7FFu);
+      kx[i] = (E == 0 || E == 0x7FF) ? 0 : ((E - 1023) >> 1);
+    }
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int t = tid + 256 * u, i = t % kNB, j = t / kNB;
+    a[i][j] = df_from_double(raw[u], kx[i] + kx[j]);
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < jb; c0 += kPW) {
+    const int cend = (c0 + kPW < jb) ? c0 + kPW : jb;
+    if (warp == 0) {
+      // lane l holds rows i0 = c0 + l and i1 = c0 + 32 + l of the panel
+      const int i0 = c0 + lane, i1 = c0 + 32 + lane;
+      dfl v0[kPW], v1[kPW];
+#pragma unroll
+      for (int q = 0; q < kPW; ++q) {
+        v0[q] = (c0 + q < cend && i0 < jb) ? a[i0][c0 + q] : dfl{0.0f, 0.0f};
+        v1[q] = (c0 + q < cend && i1 < jb) ? a[i1][c0 + q] : dfl{0.0f, 0.0f};
+      }
+      int fail_col = -1;
+#pragma unroll
+      for (int q = 0; q < kPW; ++q) {
+        const int c = c0 + q;
+        if (c < cend && fail_col < 0) {
+          const dfl d = {__shfl_sync(0xffffffffu, v0[q].h, q), __shfl_sync(0xffffffffu, v0[q].l, q)};
+          if (!(d.h > 0.0f) || !isfinite(d.h)) {  // a_cc <= 0, infinite or NaN
+            fail_col = c;
+          } else {
+            const dfl r = df_rsqrt(d);
+            if (i0 > c) v0[q] = df_mul(v0[q], r);
+            else if (i0 == c) v0[q] = df_mul(d, r);
+            v1[q] = df_mul(v1[q], r);  // i1 > c always
+            if (lane == 0) rd[c] = r;
+#pragma unroll
+            for (int qj = q + 1; qj < kPW; ++qj) {
+              const dfl ljc = {__shfl_sync(0xffffffffu, v0[q].h, qj),
+                               __shfl_sync(0xffffffffu, v0[q].l, qj)};  // row c0 + qj
+              if (i0 >= c0 + qj) v0[qj] = df_fms(v0[qj], v0[q], ljc);
+              v1[qj] = df_fms(v1[qj], v1[q], ljc);
+            }
+          }
+        }
+      }
+      if (fail_col >= 0) {
+        if (lane == 0) {
+          bad = 1;
+          status->info = (int)(j0 + fail_col + 1);
+          atomicExch(&status->code, 2 /* QML_ENOTSPD */);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kPW; ++q) {
+          if (c0 + q < cend) {
+            if (i0 < jb && i0 >= c0 + q) a[i0][c0 + q] = v0[q];
+            if (i1 < jb) a[i1][c0 + q] = v1[q];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    // rank-(cend - c0) update of the trailing triangle cend <= j <= i < jb,
+    // two elements per pass, each with two partial sums
+    const int m = jb - cend;
+    const int T = m * (m + 1) / 2;
+    for (int t = tid; t < T; t += 2 * blockDim.x) {
+      int ii[2], jj[2];
+      bool on[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int tu = t + u * (int)blockDim.x;
+        on[u] = tu < T;
+        int r = (int)((sqrtf(8.0f * tu + 1.0f) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= tu) ++r;
+        while (r * (r + 1) / 2 > tu) --r;
+        ii[u] = cend + r;
+        jj[u] = cend + (tu - r * (r + 1) / 2);
+        if (!on[u]) ii[u] = jj[u] = cend;  // harmless in-range indices
+      }
+      dfl v[2], w[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        v[u] = a[ii[u]][jj[u]];
+        w[u] = dfl{0.0f, 0.0f};
+      }
+#pragma unroll
+      for (int q = 0; q < kPW; q += 2) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (c0 + q < cend) v[u] = df_fms(v[u], a[ii[u]][c0 + q], a[jj[u]][c0 + q]);
+          if (c0 + q + 1 < cend) w[u] = df_fms(w[u], a[ii[u]][c0 + q + 1], a[jj[u]][c0 + q + 1]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (on[u]) a[ii[u]][jj[u]] = df_add(v[u], w[u]);
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < kNB * kNB; t += blockDim.x) {
+    const int j = t % kNB, c = t / kNB;
+    if (j < c) continue;
+    dfl l = {0.0f, 0.0f}, sc = {0.0f, 0.0f};
+    if (j < jb) {
+      l = a[j][c];
+      sc = j == c ? rd[c] : df_mul(l, rd[j]);
+    }
+    const int p = packed_off(c, kNB) + (j - c);
+    Lslot[p] = make_float2(l.h, l.l);
+    Sout[p] = make_float2(sc.h, sc.l);
+  }
+  if (tid < kNB) {
+    ((int *)(Lslot + packed_off(kNB, kNB)))[tid] = kx[tid];
+    ((int *)(Sout + packed_off(kNB, kNB)))[tid] = kx[tid];
+  }
+}
+
+// X = B L^-T for the m x ib rows B (ld ldb) and the diagonal block factored
+// by potrf_diag_df_kernel: each row solves sum_k L~_ck x_k = b_c 2^-k_c by
+// forward substitution in float-float,
+//   x_c = b_c 2^-k_c / L~_cc - sum_{k<c} (L~_ck / L~_cc) x_k,
+// from its coefficients S (kSlot float2, brought into shared memory by one
+// bulk copy with a bounded wait).  One warp per CTA, two rows per warp, 16
+// lanes per row: lane g keeps columns g, g + 16, g + 32, g + 48, x_c reaches
+// the row's other lanes by shuffle and every later column takes one
+// float-float multiply-subtract per step.  X (float64) goes to B (in place)
+// and to T (ld ldt).
 constexpr int kTrsmRows = 2;
-__global__ void __launch_bounds__(32) trsm_rows_kernel(const double *S, int ib, double *B,
-                                                       int64_t ldb, int64_t m, double *T,
-                                                       int64_t ldt, DevStatus *status) {
-  __shared__ __align__(128) double s[kNB * kNB];
+__global__ void __launch_bounds__(32) trsm_rows_df_kernel(const float2 *S, int ib, double *B,
+                                                          int64_t ldb, int64_t m, double *T,
+                                                          int64_t ldt, DevStatus *status) {
+  __shared__ __align__(128) float2 s[kSlot];
   __shared__ __align__(8) uint64_t bar;
   if (*((volatile int *)&status->code) != 0) return;
   const int lane = threadIdx.x, g = lane & 15;
@@ -422,28 +607,40 @@ __global__ void __launch_bounds__(32) trsm_rows_kernel(const double *S, int ib, 
     mbar_expect_tx(b, (uint32_t)sizeof(s));
     bulk_load(smem_u32(s), S, (uint32_t)sizeof(s), b);
   }
-  double v[4];
+  double raw[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int col = g + 16 * q;
-    v[q] = (on && col < ib) ? B[row + (int64_t)col * ldb] : 0.0;
+    raw[q] = (on && col < ib) ? B[row + (int64_t)col * ldb] : 0.0;
   }
   __syncwarp();
   if (!mbar_wait(b, 0, status)) {
     mbar_drain_wait(b, 0);
     return;
   }
+  const int *kx = (const int *)(s + packed_off(kNB, kNB));
+  dfl v[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) v[q] *= s[(g + 16 * q) * (kNB + 1)];
+  for (int q = 0; q < 4; ++q) {
+    const int col = g + 16 * q;
+    const float2 r = s[packed_off(col, kNB)];
+    v[q] = df_mul(df_from_double(raw[q], kx[col]), dfl{r.x, r.y});
+  }
 #pragma unroll
   for (int qc = 0; qc < 4; ++qc) {
 #pragma unroll
     for (int g0 = 0; g0 < 16; ++g0) {
       const int c = 16 * qc + g0;
-      const double xc = __shfl_sync(0xffffffffu, v[qc], g0, 16);
+      const dfl xc = {__shfl_sync(0xffffffffu, v[qc].h, g0, 16),
+                      __shfl_sync(0xffffffffu, v[qc].l, g0, 16)};
 #pragma unroll
-      for (int q = qc; q < 4; ++q)
-        if (g + 16 * q > c) v[q] = fma(-s[c * kNB + g + 16 * q], xc, v[q]);
+      for (int q = qc; q < 4; ++q) {
+        const int j = g + 16 * q;
+        if (j > c) {
+          const float2 sc = s[packed_off(c, kNB) + (j - c)];
+          v[q] = df_fms(v[q], dfl{sc.x, sc.y}, xc);
+        }
+      }
     }
   }
   if (on) {
@@ -451,8 +648,9 @@ __global__ void __launch_bounds__(32) trsm_rows_kernel(const double *S, int ib, 
     for (int q = 0; q < 4; ++q) {
       const int col = g + 16 * q;
       if (col < ib) {
-        B[row + (int64_t)col * ldb] = v[q];
-        T[row + (int64_t)col * ldt] = v[q];
+        const double xv = df_to_double(v[q], 0);
+        B[row + (int64_t)col * ldb] = xv;
+        T[row + (int64_t)col * ldt] = xv;
       }
     }
   }
@@ -728,17 +926,23 @@ void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Li
   { potrf_diag_kernel<<<1, 256, kDiagSmem, st>>>(A, lda, n, j0, Linv, logdet_part, status, 1); count_launch(); }
 }
 
-void launch_potrf_diag_factor(double *A, int64_t lda, int64_t n, int64_t j0, double *S,
-                              double *logdet_part, DevStatus *status, cudaStream_t st) {
-  set_diag_smem();
-  { potrf_diag_kernel<<<1, 256, kDiagSmem, st>>>(A, lda, n, j0, S, logdet_part, status, 2); count_launch(); }
+void launch_potrf_diag_df(const double *A, int64_t lda, int64_t n, int64_t j0, double *Lslot,
+                          double *S, DevStatus *status, cudaStream_t st) {
+  { potrf_diag_df_kernel<<<1, 256, 0, st>>>(A, lda, n, j0, (float2 *)Lslot, (float2 *)S, status); count_launch(); }
 }
 
-void launch_trsm_rows(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m, double *T,
-                      int64_t ldt, DevStatus *status, cudaStream_t st) {
+void launch_trsm_rows_df(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m,
+                         double *T, int64_t ldt, DevStatus *status, cudaStream_t st) {
   if (m <= 0 || ib <= 0) return;
   const unsigned grid = (unsigned)((m + kTrsmRows - 1) / kTrsmRows);
-  { trsm_rows_kernel<<<grid, 32, 0, st>>>(S, (int)ib, B, ldb, m, T, ldt, status); count_launch(); }
+  { trsm_rows_df_kernel<<<grid, 32, 0, st>>>((const float2 *)S, (int)ib, B, ldb, m, T, ldt, status); count_launch(); }
+}
+
+void launch_trtri_blocks_df(double *L, int64_t lda, int64_t n, double *Linv,
+                            double *logdet_parts, DevStatus *status, cudaStream_t st) {
+  const int nb = (int)((n + kNB - 1) / kNB);
+  set_diag_smem();
+  { potrf_diag_kernel<<<nb, 256, kDiagSmem, st>>>(L, lda, n, 0, Linv, logdet_parts, status, 3); count_launch(); }
 }
 
 void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,

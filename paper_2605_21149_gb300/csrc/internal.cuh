@@ -67,16 +67,25 @@ constexpr int kNB = 64;  // Cholesky / TRSM block size
 // 2 sum ln L_ii into *logdet_part.
 void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,
                        double *logdet_part, DevStatus *status, cudaStream_t st);
-// Factor only (mode 2 of the diagonal kernel): S (kNB x kNB) receives the
-// scaled coefficients of the row solve, S[k kNB + c] = L_ck / L_cc (c > k),
-// S[c kNB + c] = 1 / L_cc.
-void launch_potrf_diag_factor(double *A, int64_t lda, int64_t n, int64_t j0, double *S,
-                              double *logdet_part, DevStatus *status, cudaStream_t st);
-// B <- B L^-T (m rows, ib <= kNB columns, ld ldb) by forward substitution
-// from the coefficients S of launch_potrf_diag_factor; the result also goes
-// to T (ld ldt).
-void launch_trsm_rows(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m, double *T,
-                      int64_t ldt, DevStatus *status, cudaStream_t st);
+// Split-precision diagonal blocks in float-float.  launch_potrf_diag_df
+// factors the diagonal block at row / column j0 (A at the matrix origin plus
+// j0 + j0 lda, n the matrix size; A is only read) and writes two slots of
+// kDfSlotDoubles doubles: Lslot (the scaled float-float factor, packed, with
+// its row exponents) and S (the coefficients of its row solve).
+constexpr int kDfSlotDoubles = kNB * (kNB + 1) / 2 + kNB / 2;
+void launch_potrf_diag_df(const double *A, int64_t lda, int64_t n, int64_t j0, double *Lslot,
+                          double *S, DevStatus *status, cudaStream_t st);
+// B <- B L^-T (m rows, ib <= kNB columns, ld ldb) from the coefficients S of
+// launch_potrf_diag_df; the result also goes to T (ld ldt).  S must be
+// 16-byte aligned.
+void launch_trsm_rows_df(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m,
+                         double *T, int64_t ldt, DevStatus *status, cudaStream_t st);
+// For every kNB block b of an n x n region L (ld lda) whose float-float
+// factor slot is at Linv + b kNB^2: float64 L into the region's lower
+// triangle, 2 sum ln L_ii into logdet_parts[b], and the block's inverse into
+// Linv + b kNB^2 (ld kNB), replacing the slot.
+void launch_trtri_blocks_df(double *L, int64_t lda, int64_t n, double *Linv,
+                            double *logdet_parts, DevStatus *status, cudaStream_t st);
 // Inverses of every kNB diagonal block of an existing lower factor L
 // (block b at Linv + b kNB^2, ld kNB), one CTA per block.
 void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,
