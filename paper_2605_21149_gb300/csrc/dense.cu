@@ -471,63 +471,72 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_df_kernel(const double *A, 
     a[i][j] = df_from_double(raw[u], kx[i] + kx[j]);
   }
   __syncthreads();
+  // Lane-dependent conditions below are selects, not branches, so that the
+  // independent float-float chains of a step stay in one basic block and
+  // interleave (each step is a dependent chain of 4-cycle float32 operations).
   for (int c0 = 0; c0 < jb; c0 += kPW) {
     const int cend = (c0 + kPW < jb) ? c0 + kPW : jb;
-    if (warp == 0) {
-      // lane l holds rows i0 = c0 + l and i1 = c0 + 32 + l of the panel
-      const int i0 = c0 + lane, i1 = c0 + 32 + lane;
-      dfl v0[kPW], v1[kPW];
+    // Warps 0-2 each factor the panel's 8 x 8 pivot block in lanes 0-7 (the
+    // same operations on the same values, so identical results) and carry 24
+    // rows of their own below it in lanes 8-31: no exchange between warps,
+    // one row per lane.  dg is every lane's copy of the pivot block's diagonal,
+    // updated by the same operations as its owner's entry, so a pivot needs
+    // no shuffle.
+    if (warp == 0 || (warp < 3 && c0 + kPW + 24 * warp < jb)) {
+      const int row = lane < kPW ? c0 + lane : c0 + kPW + 24 * warp + (lane - kPW);
+      const bool live = row < jb;
+      dfl v[kPW], dg[kPW];
 #pragma unroll
       for (int q = 0; q < kPW; ++q) {
-        v0[q] = (c0 + q < cend && i0 < jb) ? a[i0][c0 + q] : dfl{0.0f, 0.0f};
-        v1[q] = (c0 + q < cend && i1 < jb) ? a[i1][c0 + q] : dfl{0.0f, 0.0f};
+        v[q] = (c0 + q < cend && live) ? a[row][c0 + q] : dfl{0.0f, 0.0f};
+        dg[q] = c0 + q < cend ? a[c0 + q][c0 + q] : dfl{0.0f, 0.0f};
       }
       int fail_col = -1;
 #pragma unroll
       for (int q = 0; q < kPW; ++q) {
         const int c = c0 + q;
         if (c < cend && fail_col < 0) {
-          const dfl d = {__shfl_sync(0xffffffffu, v0[q].h, q), __shfl_sync(0xffffffffu, v0[q].l, q)};
+          const dfl d = dg[q];
           if (!(d.h > 0.0f) || !isfinite(d.h)) {  // a_cc <= 0, infinite or NaN
             fail_col = c;
           } else {
             const dfl r = df_rsqrt(d);
-            if (i0 > c) v0[q] = df_mul(v0[q], r);
-            else if (i0 == c) v0[q] = df_mul(d, r);
-            v1[q] = df_mul(v1[q], r);  // i1 > c always
-            if (lane == 0) rd[c] = r;
+            const dfl s0 = df_mul(v[q], r), lcc = df_mul(d, r);
+            v[q] = row > c ? s0 : (row == c ? lcc : v[q]);
+            if (warp == 0 && lane == 0) rd[c] = r;
+            dfl lj[kPW];
+#pragma unroll
+            for (int qj = q + 1; qj < kPW; ++qj)  // l(c0 + qj, c): lane qj of every warp
+              lj[qj] = {__shfl_sync(0xffffffffu, v[q].h, qj), __shfl_sync(0xffffffffu, v[q].l, qj)};
 #pragma unroll
             for (int qj = q + 1; qj < kPW; ++qj) {
-              const dfl ljc = {__shfl_sync(0xffffffffu, v0[q].h, qj),
-                               __shfl_sync(0xffffffffu, v0[q].l, qj)};  // row c0 + qj
-              if (i0 >= c0 + qj) v0[qj] = df_fms(v0[qj], v0[q], ljc);
-              v1[qj] = df_fms(v1[qj], v1[q], ljc);
+              const dfl n = df_fms(v[qj], v[q], lj[qj]);
+              v[qj] = row >= c0 + qj ? n : v[qj];
+              dg[qj] = df_fms(dg[qj], lj[qj], lj[qj]);
             }
           }
         }
       }
       if (fail_col >= 0) {
-        if (lane == 0) {
+        if (warp == 0 && lane == 0) {
           bad = 1;
           status->info = (int)(j0 + fail_col + 1);
           atomicExch(&status->code, 2 /* QML_ENOTSPD */);
         }
-      } else {
+      } else if (live && (warp == 0 || lane >= kPW)) {
 #pragma unroll
-        for (int q = 0; q < kPW; ++q) {
-          if (c0 + q < cend) {
-            if (i0 < jb && i0 >= c0 + q) a[i0][c0 + q] = v0[q];
-            if (i1 < jb) a[i1][c0 + q] = v1[q];
-          }
-        }
+        for (int q = 0; q < kPW; ++q)
+          if (c0 + q < cend && row >= c0 + q) a[row][c0 + q] = v[q];
       }
     }
     __syncthreads();
     if (bad) return;
     // rank-(cend - c0) update of the trailing triangle cend <= j <= i < jb,
-    // two elements per pass, each with two partial sums
+    // two elements per pass, each with two partial sums (a full panel takes
+    // the branch-free form)
     const int m = jb - cend;
     const int T = m * (m + 1) / 2;
+    const bool full = cend - c0 == kPW;
     for (int t = tid; t < T; t += 2 * blockDim.x) {
       int ii[2], jj[2];
       bool on[2];
@@ -548,12 +557,19 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_df_kernel(const double *A, 
         v[u] = a[ii[u]][jj[u]];
         w[u] = dfl{0.0f, 0.0f};
       }
+      if (full) {
 #pragma unroll
-      for (int q = 0; q < kPW; q += 2) {
+        for (int q = 0; q < kPW; q += 2) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (c0 + q < cend) v[u] = df_fms(v[u], a[ii[u]][c0 + q], a[jj[u]][c0 + q]);
-          if (c0 + q + 1 < cend) w[u] = df_fms(w[u], a[ii[u]][c0 + q + 1], a[jj[u]][c0 + q + 1]);
+          for (int u = 0; u < 2; ++u) {
+            v[u] = df_fms(v[u], a[ii[u]][c0 + q], a[jj[u]][c0 + q]);
+            w[u] = df_fms(w[u], a[ii[u]][c0 + q + 1], a[jj[u]][c0 + q + 1]);
+          }
+        }
+      } else {
+        for (int q = 0; q < cend - c0; ++q) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) v[u] = df_fms(v[u], a[ii[u]][c0 + q], a[jj[u]][c0 + q]);
         }
       }
 #pragma unroll
@@ -562,17 +578,18 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_df_kernel(const double *A, 
     }
     __syncthreads();
   }
+#pragma unroll 4
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {
     const int j = t % kNB, c = t / kNB;
-    if (j < c) continue;
-    dfl l = {0.0f, 0.0f}, sc = {0.0f, 0.0f};
-    if (j < jb) {
-      l = a[j][c];
-      sc = j == c ? rd[c] : df_mul(l, rd[j]);
+    const bool in = j < jb;
+    const dfl l = in ? a[j][c] : dfl{0.0f, 0.0f};
+    const dfl sm = df_mul(l, rd[j]);
+    const dfl sc = !in ? dfl{0.0f, 0.0f} : (j == c ? rd[c] : sm);
+    if (j >= c) {
+      const int p = packed_off(c, kNB) + (j - c);
+      Lslot[p] = make_float2(l.h, l.l);
+      Sout[p] = make_float2(sc.h, sc.l);
     }
-    const int p = packed_off(c, kNB) + (j - c);
-    Lslot[p] = make_float2(l.h, l.l);
-    Sout[p] = make_float2(sc.h, sc.l);
   }
   if (tid < kNB) {
     ((int *)(Lslot + packed_off(kNB, kNB)))[tid] = kx[tid];
@@ -633,13 +650,17 @@ __global__ void __launch_bounds__(32) trsm_rows_df_kernel(const float2 *S, int i
       const int c = 16 * qc + g0;
       const dfl xc = {__shfl_sync(0xffffffffu, v[qc].h, g0, 16),
                       __shfl_sync(0xffffffffu, v[qc].l, g0, 16)};
+      // column qc of this lane is later than c only where g > g0 (a select);
+      // columns q > qc always are
+      {
+        const float2 sc = s[packed_off(c, kNB) + (g + 16 * qc - c)];  // in range for g <= g0 too
+        const dfl nv = df_fms(v[qc], dfl{sc.x, sc.y}, xc);
+        v[qc] = g > g0 ? nv : v[qc];
+      }
 #pragma unroll
-      for (int q = qc; q < 4; ++q) {
-        const int j = g + 16 * q;
-        if (j > c) {
-          const float2 sc = s[packed_off(c, kNB) + (j - c)];
-          v[q] = df_fms(v[q], dfl{sc.x, sc.y}, xc);
-        }
+      for (int q = qc + 1; q < 4; ++q) {
+        const float2 sc = s[packed_off(c, kNB) + (g + 16 * q - c)];
+        v[q] = df_fms(v[q], dfl{sc.x, sc.y}, xc);
       }
     }
   }
