@@ -391,6 +391,24 @@ def run_ours(args):
                                "ms_per_step": 1e3 * ts / args.steps,
                                "speedup_vs_fp64": (args.steps / ts) / (args.steps / (t / world)),
                                "tolerance": "1e-8 vs float64 oracle"}
+        # the opt-in float-float 64-wide diagonal blocks of the split Cholesky
+        # (tuning key split_diag_df; the default keeps them in float64)
+        api.tune_set("split_diag_df", 1)
+        try:
+            step_s()
+            torch.cuda.synchronize()
+            e6.record()
+            for _ in range(args.steps):
+                step_s()
+            e7.record()
+            e7.synchronize()
+        finally:
+            api.tune_set("split_diag_df", 0)
+        tdf = e6.elapsed_time(e7) * 1e-3
+        forms["split_bf16"]["float_float_diagonal"] = {
+            "value": args.steps / tdf, "unit": UNIT, "ms_per_step": 1e3 * tdf / args.steps,
+            "note": "64-wide Cholesky diagonal blocks and their row solves in float-float "
+                    "(split_diag_df = 1); the default factors them in float64"}
         # the QU Nside 32 split-precision workload (n = 17152, k = 18424)
         wl3 = synth.workload(2)
         p3s = api.Problem.from_workload(wl3, device=True, precision=1)

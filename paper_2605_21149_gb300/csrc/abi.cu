@@ -381,35 +381,49 @@ struct Split {
 // (ceil(n/kNBS) blocks of kNBS x kNBS, ld kNBS).
 void potrf_split(Call &c, Split &sp, double *A, int64_t n, int64_t lda, double *Linv64,
                  double *LinvB, double *ldparts, double *logdet) {
+  const bool dfdiag = tune_get("split_diag_df", 0) != 0;
   for (int64_t j = 0; j < n; j += kNBS) {
     const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
     double *Ajj = A + j + j * lda;
     double *T = sp.tinv_scratch();  // (kNBS/2)^2 doubles: the panel block below, then the doubling
     if (!T) return;
-    // blocked factorisation of the diagonal block, 64-wide.  Each 64-block is
-    // factored in float-float (its factor goes to the block's inverse slot,
-    // the coefficients of its row solve to S); the rows below it are solved by
-    // forward substitution, in place and into T (m2 x 64 <= (kNBS - kNB) x
-    // kNB), whose product with itself updates the rest in float64 (out of
-    // place, so it can take small tiles).
+    // blocked factorisation of the diagonal block, 64-wide, in float64.  The
+    // 64-block factor leaves the coefficients of its row solve in the slot of
+    // its inverse; the rows below are solved by forward substitution, in
+    // place and into T (m2 x 64 <= (kNBS - kNB) x kNB), whose product with
+    // itself updates the rest (out of place, so it can take small tiles).
+    // With split_diag_df the 64-blocks and their row solves run in
+    // float-float instead (about 2^-46 per operation; the factor goes to the
+    // inverse slot, the coefficients to S behind T's panel part).
     double *S = T + (int64_t)(kNBS - kNB) * kNB;
     for (int64_t i = 0; i < jb; i += kNB) {
       const int64_t ib = (jb - i) < kNB ? (jb - i) : kNB;
       double *Lb = Linv64 + ((j + i) / kNB) * kNB * kNB;
-      launch_potrf_diag_df(A + (j + i) + (j + i) * lda, lda, j + jb, j + i, Lb, S, c.status,
-                           c.st);
+      double *Ab = A + (j + i) + (j + i) * lda;
+      if (dfdiag)
+        launch_potrf_diag_df(Ab, lda, j + jb, j + i, Lb, S, c.status, c.st);
+      else
+        launch_potrf_diag_factor(Ab, lda, j + jb, j + i, Lb, ldparts + (j + i) / kNB, c.status,
+                                 c.st);
       if (i + ib < jb) {
         const int64_t m2 = jb - i - ib;
         double *A21 = Ajj + (i + ib) + i * lda;
         double *A22 = Ajj + (i + ib) + (i + ib) * lda;
-        launch_trsm_rows_df(S, ib, A21, lda, m2, T, m2, c.status, c.st);
+        if (dfdiag)
+          launch_trsm_rows_df(S, ib, A21, lda, m2, T, m2, c.status, c.st);
+        else
+          launch_trsm_rows(Lb, ib, A21, lda, m2, T, m2, c.status, c.st);
         launch_dgemm(0, 1, m2, m2, ib, -1.0, T, m2, T, m2, 1.0, A22, lda, 1, c.status, c.st);
       }
     }
-    // float64 factor blocks, their log det parts and inverses (one launch, a
-    // CTA each), then the explicit inverse of the diagonal block (float64)
-    launch_trtri_blocks_df(Ajj, lda, jb, Linv64 + (j / kNB) * kNB * kNB, ldparts + j / kNB,
-                           c.status, c.st);
+    // inverses of the 64-blocks (one launch, a CTA each; from the float-float
+    // slots also the float64 factor and its log det parts), then the explicit
+    // inverse of the diagonal block (float64)
+    if (dfdiag)
+      launch_trtri_blocks_df(Ajj, lda, jb, Linv64 + (j / kNB) * kNB * kNB, ldparts + j / kNB,
+                             c.status, c.st);
+    else
+      launch_trtri_blocks(Ajj, lda, jb, Linv64 + (j / kNB) * kNB * kNB, c.status, c.st);
     double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
     trinv_doubling(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, kNBS, T);
     if (j + jb < n) {

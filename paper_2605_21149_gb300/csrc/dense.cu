@@ -232,8 +232,11 @@ __device__ void invert_lower_blocked(double (*a)[kLDA], double (*x)[kLDA], const
   }
 }
 
-// mode 1: factor and invert; mode 0: the block already holds L and only the
-// inverse is formed (blockIdx.x selects the block: j0 = blockIdx.x * kNB);
+// mode 1: factor and invert; mode 2: factor only, and Linv receives the
+// scaled coefficients of the row solve x L^T = b (trsm_rows_kernel) instead of
+// an inverse, Linv[c kNB + j] = L_jc / L_jj (j > c), 1 / L_cc (j = c), 0
+// otherwise; mode 0: the block already holds L and only the inverse is formed
+// (blockIdx.x selects the block: j0 = blockIdx.x * kNB);
 // mode 3: as mode 0, but the factor comes from the float-float slot that
 // potrf_diag_df_kernel left at Linv (packed L~ and the row exponents k_i,
 // L_ij = L~_ij 2^k_i): it is written into A (lower triangle), 2 sum ln L_ii
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
                                                          int64_t j0, double *Linv,
                                                          double *logdet_part,
                                                          DevStatus *status, int mode) {
-  const int factor = mode == 1;
+  const int factor = mode == 1 || mode == 2;
   extern __shared__ __align__(16) double dsm[];
   double(*a)[kLDA] = (double(*)[kLDA])dsm;
   double(*x)[kLDA] = (double(*)[kLDA])(dsm + kNB * kLDA);
@@ -309,62 +312,65 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
   if (tid == 0) *bad = 0;
   __syncthreads();
   if (factor) {
+    // Warps 0-2 each factor the panel's 8 x 8 pivot block in lanes 0-7 (the
+    // same operations on the same values, so identical results) and carry 24
+    // rows of their own below it in lanes 8-31: one row per lane, and the
+    // panel's float64 instructions spread over three SM sub-partitions (a
+    // float64 warp instruction holds its sub-partition for ~76 clocks).
+    // Lane-dependent conditions are selects, so each step is one basic block.
     for (int c0 = 0; c0 < jb; c0 += kPW) {
       const int cend = (c0 + kPW < jb) ? c0 + kPW : jb;
-      if (warp == 0) {
-        // lane l holds rows i0 = c0 + l and i1 = c0 + 32 + l of the panel
-        const int i0 = c0 + lane, i1 = c0 + 32 + lane;
-        double v0[kPW], v1[kPW];
+      if (warp == 0 || (warp < 3 && c0 + kPW + 24 * warp < jb)) {
+        const int row = lane < kPW ? c0 + lane : c0 + kPW + 24 * warp + (lane - kPW);
+        const bool live = row < jb;
+        double v[kPW];
 #pragma unroll
-        for (int q = 0; q < kPW; ++q) {
-          v0[q] = (c0 + q < cend && i0 < jb) ? a[i0][c0 + q] : 0.0;
-          v1[q] = (c0 + q < cend && i1 < jb) ? a[i1][c0 + q] : 0.0;
-        }
+        for (int q = 0; q < kPW; ++q) v[q] = (c0 + q < cend && live) ? a[row][c0 + q] : 0.0;
         int fail_col = -1;
 #pragma unroll
         for (int q = 0; q < kPW; ++q) {
           const int c = c0 + q;
           if (c < cend && fail_col < 0) {
-            const double d = __shfl_sync(0xffffffffu, v0[q], q);  // a_cc (row c is lane q)
+            const double d = __shfl_sync(0xffffffffu, v[q], q);  // a_cc: lane q holds row c
             const double r = rsqrt(d);
             if (!(r > 0.0) || !isfinite(r)) {  // a_cc <= 0, infinite or NaN
               fail_col = c;
             } else {
-              if (i0 > c) v0[q] *= r;
-              else if (i0 == c) v0[q] = d * r;
-              v1[q] *= r;  // i1 > c always
-              if (lane == 0) invd[c] = r;
+              // row c: L_cc = a_cc r; rows below: l_ic = a_ic r
+              const double sc = (row == c ? d : v[q]) * r;
+              v[q] = row >= c ? sc : v[q];
+              if (warp == 0 && lane == 0) invd[c] = r;
+              double lj[kPW];
+#pragma unroll
+              for (int qj = q + 1; qj < kPW; ++qj) lj[qj] = __shfl_sync(0xffffffffu, v[q], qj);
 #pragma unroll
               for (int qj = q + 1; qj < kPW; ++qj) {
-                const double ljc = __shfl_sync(0xffffffffu, v0[q], qj);  // row c0 + qj
-                if (i0 >= c0 + qj) v0[qj] = fma(-v0[q], ljc, v0[qj]);
-                v1[qj] = fma(-v1[q], ljc, v1[qj]);
+                const double nv = fma(-v[q], lj[qj], v[qj]);
+                v[qj] = row >= c0 + qj ? nv : v[qj];
               }
             }
           }
         }
         if (fail_col >= 0) {
-          if (lane == 0) {
+          if (warp == 0 && lane == 0) {
             *bad = 1;
             status->info = (int)(j0 + fail_col + 1);
             atomicExch(&status->code, 2 /* QML_ENOTSPD */);
           }
-        } else {
+        } else if (live && (warp == 0 || lane >= kPW)) {
 #pragma unroll
-          for (int q = 0; q < kPW; ++q) {
-            if (c0 + q < cend) {
-              if (i0 < jb && i0 >= c0 + q) a[i0][c0 + q] = v0[q];
-              if (i1 < jb) a[i1][c0 + q] = v1[q];
-            }
-          }
+          for (int q = 0; q < kPW; ++q)
+            if (c0 + q < cend && row >= c0 + q) a[row][c0 + q] = v[q];
         }
       }
       __syncthreads();
       if (*bad) return;
       // rank-(cend - c0) update of the trailing triangle cend <= j <= i < jb,
-      // two elements per pass, each with two partial sums
+      // two elements per pass, each with two partial sums (a full panel takes
+      // the branch-free form)
       const int m = jb - cend;
       const int T = m * (m + 1) / 2;
+      const bool full = cend - c0 == kPW;
       for (int t = tid; t < T; t += 2 * blockDim.x) {
         int ii[2], jj[2];
         bool on[2];
@@ -385,12 +391,19 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
           v[u] = a[ii[u]][jj[u]];
           w[u] = 0.0;
         }
+        if (full) {
 #pragma unroll
-        for (int q = 0; q < kPW; q += 2) {
+          for (int q = 0; q < kPW; q += 2) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            if (c0 + q < cend) v[u] = fma(-a[ii[u]][c0 + q], a[jj[u]][c0 + q], v[u]);
-            if (c0 + q + 1 < cend) w[u] = fma(-a[ii[u]][c0 + q + 1], a[jj[u]][c0 + q + 1], w[u]);
+            for (int u = 0; u < 2; ++u) {
+              v[u] = fma(-a[ii[u]][c0 + q], a[jj[u]][c0 + q], v[u]);
+              w[u] = fma(-a[ii[u]][c0 + q + 1], a[jj[u]][c0 + q + 1], w[u]);
+            }
+          }
+        } else {
+          for (int q = 0; q < cend - c0; ++q) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) v[u] = fma(-a[ii[u]][c0 + q], a[jj[u]][c0 + q], v[u]);
           }
         }
 #pragma unroll
@@ -411,6 +424,15 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) *logdet_part = 2.0 * s;
     }
+    if (mode == 2) {
+      for (int t = tid; t < kNB * kNB; t += blockDim.x) {
+        const int j = t % kNB, c = t / kNB;
+        double v = 0.0;
+        if (j < jb && c < jb) v = j > c ? a[j][c] * invd[j] : (j == c ? invd[c] : 0.0);
+        Linv[t] = v;
+      }
+      return;
+    }
   } else {
     if (tid < jb) invd[tid] = 1.0 / a[tid][tid];
     __syncthreads();
@@ -419,6 +441,70 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
   for (int t = tid; t < kNB * kNB; t += blockDim.x) {
     int i = t % kNB, j = t / kNB;
     Linv[i + j * kNB] = (i < jb && j < jb) ? x[i][j] : 0.0;
+  }
+}
+
+// X = B L^-T for the m x ib rows B (ld ldb) and a lower-triangular ib x ib
+// block L, i.e. each row solves x L^T = b by forward substitution,
+//   x_c = b_c / L_cc - sum_{k<c} (L_ck / L_cc) x_k,
+// from the scaled coefficients S (kNB x kNB, S[k kNB + c] = L_ck / L_cc for
+// c > k, S[c kNB + c] = 1 / L_cc: mode 2 of potrf_diag_kernel).  One warp per
+// CTA, two rows per warp, 16 lanes per row: lane g keeps columns g, g + 16,
+// g + 32, g + 48 in registers, x_c reaches the row's other lanes by shuffle and
+// every later column takes one fma per step (the current column by a select).
+// S comes into shared memory by one bulk copy (bounded wait).  X goes to B (in
+// place) and to T (ld ldt).
+constexpr int kTrsmRows = 2;
+__global__ void __launch_bounds__(32) trsm_rows_kernel(const double *S, int ib, double *B,
+                                                       int64_t ldb, int64_t m, double *T,
+                                                       int64_t ldt, DevStatus *status) {
+  __shared__ __align__(128) double s[kNB * kNB];
+  __shared__ __align__(8) uint64_t bar;
+  if (*((volatile int *)&status->code) != 0) return;
+  const int lane = threadIdx.x, g = lane & 15;
+  const int64_t row = (int64_t)blockIdx.x * kTrsmRows + (lane >> 4);
+  const bool on = row < m;
+  const uint32_t b = smem_u32(&bar);
+  if (lane == 0) {
+    mbar_init(b, 1);
+    fence_mbar_init();
+    mbar_expect_tx(b, (uint32_t)sizeof(s));
+    bulk_load(smem_u32(s), S, (uint32_t)sizeof(s), b);
+  }
+  double v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int col = g + 16 * q;
+    v[q] = (on && col < ib) ? B[row + (int64_t)col * ldb] : 0.0;
+  }
+  __syncwarp();
+  if (!mbar_wait(b, 0, status)) {
+    mbar_drain_wait(b, 0);
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] *= s[(g + 16 * q) * (kNB + 1)];
+#pragma unroll
+  for (int qc = 0; qc < 4; ++qc) {
+#pragma unroll
+    for (int g0 = 0; g0 < 16; ++g0) {
+      const int c = 16 * qc + g0;
+      const double xc = __shfl_sync(0xffffffffu, v[qc], g0, 16);
+      const double nv = fma(-s[c * kNB + g + 16 * qc], xc, v[qc]);
+      v[qc] = g > g0 ? nv : v[qc];
+#pragma unroll
+      for (int q = qc + 1; q < 4; ++q) v[q] = fma(-s[c * kNB + g + 16 * q], xc, v[q]);
+    }
+  }
+  if (on) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = g + 16 * q;
+      if (col < ib) {
+        B[row + (int64_t)col * ldb] = v[q];
+        T[row + (int64_t)col * ldt] = v[q];
+      }
+    }
   }
 }
 
@@ -607,7 +693,6 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_df_kernel(const double *A, 
 // the row's other lanes by shuffle and every later column takes one
 // float-float multiply-subtract per step.  X (float64) goes to B (in place)
 // and to T (ld ldt).
-constexpr int kTrsmRows = 2;
 __global__ void __launch_bounds__(32) trsm_rows_df_kernel(const float2 *S, int ib, double *B,
                                                           int64_t ldb, int64_t m, double *T,
                                                           int64_t ldt, DevStatus *status) {
@@ -945,6 +1030,19 @@ void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Li
                        double *logdet_part, DevStatus *status, cudaStream_t st) {
   set_diag_smem();
   { potrf_diag_kernel<<<1, 256, kDiagSmem, st>>>(A, lda, n, j0, Linv, logdet_part, status, 1); count_launch(); }
+}
+
+void launch_potrf_diag_factor(double *A, int64_t lda, int64_t n, int64_t j0, double *S,
+                              double *logdet_part, DevStatus *status, cudaStream_t st) {
+  set_diag_smem();
+  { potrf_diag_kernel<<<1, 256, kDiagSmem, st>>>(A, lda, n, j0, S, logdet_part, status, 2); count_launch(); }
+}
+
+void launch_trsm_rows(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m, double *T,
+                      int64_t ldt, DevStatus *status, cudaStream_t st) {
+  if (m <= 0 || ib <= 0) return;
+  const unsigned grid = (unsigned)((m + kTrsmRows - 1) / kTrsmRows);
+  { trsm_rows_kernel<<<grid, 32, 0, st>>>(S, (int)ib, B, ldb, m, T, ldt, status); count_launch(); }
 }
 
 void launch_potrf_diag_df(const double *A, int64_t lda, int64_t n, int64_t j0, double *Lslot,

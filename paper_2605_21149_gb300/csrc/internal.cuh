@@ -67,7 +67,19 @@ constexpr int kNB = 64;  // Cholesky / TRSM block size
 // 2 sum ln L_ii into *logdet_part.
 void launch_potrf_diag(double *A, int64_t lda, int64_t n, int64_t j0, double *Linv,
                        double *logdet_part, DevStatus *status, cudaStream_t st);
-// Split-precision diagonal blocks in float-float.  launch_potrf_diag_df
+// Factor only (mode 2 of the diagonal kernel): S (kNB x kNB) receives the
+// scaled coefficients of the row solve, S[k kNB + c] = L_ck / L_cc (c > k),
+// S[c kNB + c] = 1 / L_cc, and *logdet_part 2 sum ln L_ii.  S must be
+// 16-byte aligned.
+void launch_potrf_diag_factor(double *A, int64_t lda, int64_t n, int64_t j0, double *S,
+                              double *logdet_part, DevStatus *status, cudaStream_t st);
+// B <- B L^-T (m rows, ib <= kNB columns, ld ldb) by float64 forward
+// substitution from the coefficients S of launch_potrf_diag_factor; the
+// result also goes to T (ld ldt).
+void launch_trsm_rows(const double *S, int64_t ib, double *B, int64_t ldb, int64_t m, double *T,
+                      int64_t ldt, DevStatus *status, cudaStream_t st);
+// Split-precision diagonal blocks in float-float (opt-in, tuning key
+// split_diag_df).  launch_potrf_diag_df
 // factors the diagonal block at row / column j0 (A at the matrix origin plus
 // j0 + j0 lda, n the matrix size; A is only read) and writes two slots of
 // kDfSlotDoubles doubles: Lslot (the scaled float-float factor, packed, with

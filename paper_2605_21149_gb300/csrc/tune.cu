@@ -9,6 +9,10 @@
 //                    heuristic only
 //   dgemm:<ta>,<tb>,<lower>,<M>,<N>,<K>,<alias>   measured tile, 10 RM + RN
 //   batch_streams    worker streams of pix_loglike_batch (default 4, 1..16)
+//   split_diag_df    0 (default): the split-precision Cholesky factors its
+//                    64-wide diagonal blocks and their row solves in float64;
+//                    1: in float-float (pairs of float32, about 2^-46 per
+//                    operation; faster on this part's narrow float64 pipe)
 //   batch_graphs     1 (default): pix_loglike_batch captures each worker's
 //                    per-item sequence once per mask as a CUDA graph and
 //                    replays it; 0: plain launches

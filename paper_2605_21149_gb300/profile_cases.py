@@ -26,8 +26,13 @@ def main():
     ap.add_argument("case", choices=("syrk", "syrk_split", "trail_split", "ybuild", "fisher", "step"))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--tune", action="append", default=[],
+                    help="key=value entry of the library's tuning table (repeatable)")
     args = ap.parse_args()
     build.build()
+    for kv in args.tune:
+        key, value = kv.split("=", 1)
+        api.tune_set(key, int(value))
     wl = synth.workload(1)
     prob = api.Problem.from_workload(wl, precision=args.precision)
     if args.case in ("syrk", "syrk_split"):

@@ -37,6 +37,21 @@ def test_potrf_trsm_across_panels(api, precision, n):
     """Split Cholesky panels are 512 wide, float64 blocks 64: sizes just
     below, at and above the panel edge, and several panels with a ragged one.
     Reference: LAPACK Cholesky and triangular solve (scipy), float64."""
+    _potrf_trsm_check(api, precision, n)
+
+
+@pytest.mark.parametrize("n", [1, 100, 513, 1537])
+def test_potrf_float_float_diagonal(api, n):
+    """The opt-in float-float 64-blocks of the split Cholesky (tuning key
+    split_diag_df) against the same LAPACK reference and tolerances."""
+    api.tune_set("split_diag_df", 1)
+    try:
+        _potrf_trsm_check(api, 1, n)
+    finally:
+        api.tune_set("split_diag_df", 0)
+
+
+def _potrf_trsm_check(api, precision, n):
     A = spd(n, n)
     Lref = np.linalg.cholesky(A)
     At = colmajor(A)

@@ -65,3 +65,13 @@ def test_split_qu_nside32_full(api):
     """The split-precision workload: QU, Nside 32, f_sky 0.7, l = 2..95
     (n = 17152, k = 18424), against the full float64 oracle."""
     _check(api, synth.workload(2), nsims=2)
+
+
+def test_split_tqu_nside16_float_float_diagonal(api):
+    """The opt-in float-float 64-blocks of the split Cholesky (tuning key
+    split_diag_df) keep the whole path within the split tolerance."""
+    api.tune_set("split_diag_df", 1)
+    try:
+        _check(api, synth.workload(1), nsims=4)
+    finally:
+        api.tune_set("split_diag_df", 0)
