@@ -228,7 +228,10 @@ void emu_free(qml_emu *emu);
  * *logdet (host or device, may be NULL) receives ln|A| = 2 sum ln L_ii.
  * precision QML_FP64: float64 throughout; QML_SPLIT_BF16: 512-wide panels
  * whose diagonal blocks (and ln|A|) are factored in float64, panel solves and
- * trailing updates as split-precision products (the scheme of qml_fisher).
+ * trailing updates as split-precision products (the scheme of qml_fisher);
+ * with the tuning entry split_diag_df = 1 (qml_tune_set) the 64-wide blocks
+ * inside each diagonal block and their row solves run in float-float
+ * (about 2^-46 per operation) instead.
  * Errors: QML_ENOTSPD with the failing column in the message. */
 qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t precision,
                      void *stream);
@@ -263,6 +266,10 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *   batch_streams   worker streams of pix_loglike_batch (default 4, 1..16)
  *   batch_graphs    1 (default) / 0: pix_loglike_batch replays each worker's
  *                   per-item kernel sequence as a captured CUDA graph
+ *   ozaki_stages    6 (default) / 4: depth of the split kernel's TMA ring
+ *   split_diag_df   0 (default) / 1: the split-precision Cholesky factors
+ *                   its 64-wide diagonal blocks and their row solves in
+ *                   float64 / in float-float (about 2^-46 per operation)
  * qml_tune_set / qml_tune_get: one entry (key without white space; get
  * returns QML_EINVAL when absent).  qml_tune_table writes the table as text,
  * one "key value" line per entry, into buf (capacity cap bytes, NUL
