@@ -514,8 +514,9 @@ __global__ void __launch_bounds__(32) trsm_rows_kernel(const double *S, int ib, 
 // 2^-(k_i + k_j) with k_i = floor(e_i / 2) for the binary exponent e_i of a_ii
 // (so a~_ii lies in [1, 4) and every float-float entry stays far from the
 // float range limits), then factored right-looking as in potrf_diag_kernel:
-// eight columns per panel in warp 0 (pivots and column entries by shuffle),
-// rank-8 updates of the trailing triangle by all threads.  Two outputs of
+// eight-column panels in warps 0-2 (each with the pivot block in lanes 0-7,
+// column entries by shuffle), rank-8 updates of the trailing triangle by all
+// threads.  Two outputs of
 // kSlot float2 each (packed lower triangle, then the 64 exponents as int):
 //   Lslot: L~, with L_ij = L~_ij 2^k_i (mode 3 of potrf_diag_kernel turns it
 //          into float64 L, the log det part and the inverse);
