@@ -546,13 +546,19 @@ def run_ours(args):
     e2e = None
     if rank == 0 and not args.no_e2e:
         def pinned(a):
-            t_ = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
-            t_.numpy()[...] = a
-            return t_.numpy()
+            # pinned host memory, column-major like every matrix of the C ABI
+            # (a row-major array would be copied into pageable memory by the
+            # binding first)
+            t_ = torch.empty(a.shape[::-1], dtype=torch.float64, pin_memory=True)
+            f = t_.numpy().T
+            f[...] = a
+            return f
+        hN = pinned(wl.N())
         hp = api.Problem(wl.lmin, wl.lmax, theta_T=pinned(wl.theta_T), phi_T=pinned(wl.phi_T),
                          theta_P=pinned(wl.theta_P), phi_P=pinned(wl.phi_P),
                          transfer_T=pinned(wl.transfer_T), transfer_P=pinned(wl.transfer_P),
-                         spec=wl.spec, cl_fid=pinned(wl.cl_fid.reshape(-1)), N=pinned(wl.N()))
+                         spec=wl.spec, cl_fid=pinned(wl.cl_fid.reshape(-1)), N=hN)
+        assert hp._p.N == hN.ctypes.data, "N must reach the library without a copy"
         hmaps = np.asfortranarray(maps.cpu().numpy())
         hm = torch.empty((args.nsims, wl.n), dtype=torch.float64, pin_memory=True).numpy().T
         hm[...] = hmaps
