@@ -10,8 +10,10 @@
 // trained on the normalised residuals (lnL - q) / sigma_r.  The residual is
 // small next to lnL itself, so bf16 weights with FP32 accumulation are enough.
 //
-// Every product runs on tensor cores (WMMA bf16 x bf16 -> fp32): forward
-// Z = X W^T, data gradient dX = dZ W, weight gradient dW = dZ^T X.  Master
+// Every product runs on tensor cores: in training WMMA bf16 x bf16 -> fp32
+// (forward Z = X W^T, data gradient dX = dZ W, weight gradient dW = dZ^T X);
+// at inference the layers after the first on tcgen05 with the bias and GELU
+// fused into the epilogue (mlp_tc_kernel).  Master
 // weights, gradients and the Adam state are float32; each layer's input
 // activations and its weights are rounded to bf16 for the products.
 // Prediction averages the two heads; a point is flagged for exact evaluation
@@ -19,7 +21,9 @@
 // tolerance.
 #include "qmlgb.h"
 #include "internal.cuh"
+#include "ptx.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <mma.h>
 
@@ -398,6 +402,144 @@ __global__ void predict_finish_kernel(const double *theta, int ntot, int off, in
   }
 }
 
+// ------------------------------------------------- tcgen05 inference layer --
+// One 128-row tile of a layer at inference, Y = X W^T + b, on tcgen05 tensor
+// cores (kind::f16: bf16 x bf16 -> fp32 in TMEM).  X is the layer's bf16
+// input (rows x K, row-major, rows a multiple of 128), W its bf16 weights
+// (N x K, row-major), K a multiple of 64 up to 256.  Warp 0 (one lane) loads
+// all of K at once by TMA into 128-byte-swizzled stages of 64 columns, then
+// issues the K / 16 MMAs (M = 128, N) and commits; warp 1 owns the TMEM
+// allocation; warps 2-9 are the epilogue (TMEM lanes 32 (w % 4) .., column half
+// (w - 2) / 4), which adds the bias and writes bf16(gelu(Y)) to Xn for a hidden
+// layer or fp32 Y to Z for the output layer.  Every wait is bounded: on expiry
+// the status takes QML_ETIMEOUT, copies and MMAs in flight are drained, TMEM is
+// freed and nothing is written.
+constexpr int kTcMaxStages = 4;  // K <= 256
+constexpr int kTcThreads = 320;
+template <int N>
+constexpr size_t tc_smem() {
+  return 1024 + (size_t)kTcMaxStages * (128 * 128 + N * 128) + 64;
+}
+template <int N>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    mlp_tc_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mW,
+                  int rows, int K, const float *bias, __nv_bfloat16 *Xn, float *Z, DevStatus *st) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int kA = 128 * 128, kB = N * 128;  // bytes of one 64-column stage
+  constexpr int kCols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  constexpr uint32_t kIdescN = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+  unsigned char *tA = smem, *tB = smem + kTcMaxStages * kA;
+  uint64_t *bars = (uint64_t *)(tB + kTcMaxStages * kB);  // full, acc, drain
+  uint32_t *holder = (uint32_t *)(bars + 3);
+  int *s_flags = (int *)(holder + 1);  // [0] go, [1] failed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 128;
+  const int nst = K / 64;
+  const uint32_t full = smem_u32(&bars[0]), acc = smem_u32(&bars[1]), drain = smem_u32(&bars[2]);
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(acc, 1);
+    mbar_init(drain, 1);
+    fence_mbar_init();
+    s_flags[0] = *((volatile int *)&st->code) == 0;
+    s_flags[1] = 0;
+  }
+  if (warp == 1) tmem_alloc(smem_u32(holder), kCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *holder;
+  if (s_flags[0]) {
+    if (warp == 0 && lane == 0) {
+      bool issued = false;
+      mbar_expect_tx(full, (uint32_t)(nst * (kA + kB)));
+      for (int s = 0; s < nst; ++s) {
+        tma_load_2d(smem_u32(tA + s * kA), &mX, full, 64 * s, m0);
+        tma_load_2d(smem_u32(tB + s * kB), &mW, full, 64 * s, 0);
+      }
+      if (mbar_wait(full, 0, st)) {
+        tc_fence_after();
+        uint32_t on = 0;
+        for (int s = 0; s < nst; ++s) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            mma_bf16(tbase, smem_desc(smem_u32(tA + s * kA) + 32 * kk),
+                     smem_desc(smem_u32(tB + s * kB) + 32 * kk), kIdescN, on);
+            on = 1u;
+          }
+        }
+        mma_commit(acc);
+        issued = true;
+      } else {
+        mbar_drain_wait(full, 0);  // the copies must land before the CTA exits
+      }
+      if (!issued) {
+        s_flags[1] = 1;
+        mbar_arrive(acc);  // release the epilogue without a result
+      }
+      mma_commit(drain);  // every MMA issued above has finished when this arrives
+      mbar_drain_wait(drain, 0);
+    } else if (warp >= 2 && (N > 16 || warp < 6)) {
+      const int quad = warp & 3;
+      const int half = N > 16 ? (warp - 2) >> 2 : 0;
+      constexpr int kW = N > 16 ? N / 2 : N;  // columns per epilogue warp
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(acc, 0, st) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      __syncwarp();
+      if (okw && !*((volatile int *)&s_flags[1])) {
+        tc_fence_after();
+        const int row = m0 + quad * 32 + lane;
+        const uint32_t lb = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * kW);
+#pragma unroll 1
+        for (int cb = 0; cb < kW / 16; ++cb) {
+          uint32_t a[16];
+          tmem_ld16(lb + 16 * cb, a);
+          const int c0 = half * kW + 16 * cb;
+          float y[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) y[j] = __uint_as_float(a[j]) + bias[c0 + j];
+          if (row < rows) {
+            if (Xn) {
+              __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16_rn(gelu_f(y[j]));
+              uint4 *dst = (uint4 *)(Xn + (int64_t)row * N + c0);
+              dst[0] = ((const uint4 *)o)[0];
+              dst[1] = ((const uint4 *)o)[1];
+            } else {
+              float4 *dst = (float4 *)(Z + (int64_t)row * N + c0);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tbase, kCols);
+}
+
+template <int N>
+bool launch_mlp_tc(const CUtensorMap &mX, const CUtensorMap &mW, int rows, int K, const float *bias,
+                   __nv_bfloat16 *Xn, float *Z, DevStatus *st, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(mlp_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_smem<N>()) != cudaSuccess)
+      return false;
+    attr = true;
+  }
+  mlp_tc_kernel<N><<<rows / 128, kTcThreads, tc_smem<N>(), s>>>(mX, mW, rows, K, bias, Xn, Z, st);
+  count_launch();
+  return true;
+}
+
 int grid_of(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -494,6 +636,60 @@ void forward(qml_emu *e, int h, Acts &A, cudaStream_t st) {
   }
 }
 
+// Inference on tcgen05: layers after the first (K = width, a multiple of 64
+// up to 256) run as mlp_tc_kernel with bias and activation fused; the first
+// layer (16 inputs) keeps the WMMA product.  Tuning key emu_tc = 0 selects the
+// WMMA path for every layer.
+bool use_tc(const qml_emu *e) {
+  return tune_get("emu_tc", 1) != 0 && e->width % 64 == 0 && e->width <= 256;
+}
+
+// tensor maps of every layer l >= 1: its input activations (rows x in) and
+// head h's weights (out x in)
+bool make_tc_maps(const qml_emu *e, int h, const Acts &A, int rows,
+                  std::vector<CUtensorMap> &mx, std::vector<CUtensorMap> &mw) {
+  const int nl = (int)e->layers.size();
+  mx.assign(nl, CUtensorMap{});
+  mw.assign(nl, CUtensorMap{});
+  for (int l = 1; l < nl; ++l) {
+    const int out = e->layers[l].first, in = e->layers[l].second;
+    if (!make_map_bf16(&mx[l], A.X[l], in, rows, (int64_t)in * 2, 64, 128)) return false;
+    if (!make_map_bf16(&mw[l], e->ph[h] + e->woff[l], in, out, (int64_t)in * 2, 64, out))
+      return false;
+  }
+  return true;
+}
+
+bool forward_tc(qml_emu *e, int h, Acts &A, int rows, const std::vector<CUtensorMap> &mx,
+                const std::vector<CUtensorMap> &mw, DevStatus *st, cudaStream_t s) {
+  const int nl = (int)e->layers.size();
+  {
+    const int out = e->layers[0].first, in = e->layers[0].second;
+    wmma_gemm<wmma::row_major, wmma::col_major>(A.B, out, in, A.X[0], in, e->ph[h] + e->woff[0],
+                                                in, A.Z[0], out, 0, s);
+    bias_act_kernel<<<grid_of((int64_t)A.B * out), 256, 0, s>>>(A.Z[0], A.B, out,
+                                                                e->p[h] + e->boff[0], A.X[1], 1);
+    count_launch();
+  }
+  for (int l = 1; l < nl; ++l) {
+    const int out = e->layers[l].first, in = e->layers[l].second;
+    const float *b = e->p[h] + e->boff[l];
+    __nv_bfloat16 *xn = (l + 1 < nl) ? A.X[l + 1] : nullptr;
+    float *z = (l + 1 < nl) ? nullptr : A.Z[l];
+    bool ok = false;
+    switch (out) {
+      case 16: ok = launch_mlp_tc<16>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
+      case 64: ok = launch_mlp_tc<64>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
+      case 128: ok = launch_mlp_tc<128>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
+      case 192: ok = launch_mlp_tc<192>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
+      case 256: ok = launch_mlp_tc<256>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
+      default: break;
+    }
+    if (!ok) return false;
+  }
+  return true;
+}
+
 // gradient of the mean squared error of head h over the first nreal rows
 void backward(qml_emu *e, int h, Acts &A, int nreal, cudaStream_t st) {
   const int nl = (int)e->layers.size();
@@ -542,10 +738,19 @@ const double *dev_in(const double *p, size_t count, std::vector<void *> &keep) {
 qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *od, int *fd,
                        double *dis, cudaStream_t st) {
   const int chunk = 65536;
+  // activation rows allocated in whole 128-row tiles (the tcgen05 layers read
+  // and write complete tiles; rows past the points are never used)
+  const int rows_alloc = (std::min(chunk, (n + 15) / 16 * 16) + 127) / 128 * 128;
   Acts A0, A1;
-  if (!A0.make(e, std::min(chunk, (n + 15) / 16 * 16)) ||
-      !A1.make(e, std::min(chunk, (n + 15) / 16 * 16)))
-    return QML_ENOMEM;
+  if (!A0.make(e, rows_alloc) || !A1.make(e, rows_alloc)) return QML_ENOMEM;
+  bool tc = use_tc(e);
+  std::vector<CUtensorMap> mx0, mw0, mx1, mw1;
+  DevStatus *dst = nullptr;
+  if (tc)
+    tc = make_tc_maps(e, 0, A0, rows_alloc, mx0, mw0) &&
+         make_tc_maps(e, 1, A1, rows_alloc, mx1, mw1) &&
+         cudaMalloc(&dst, sizeof(DevStatus)) == cudaSuccess &&
+         cudaMemsetAsync(dst, 0, sizeof(DevStatus), st) == cudaSuccess;
   for (int off = 0; off < n; off += chunk) {
     const int cnt = std::min(chunk, n - off);
     const int Bc = (cnt + 15) / 16 * 16;
@@ -555,13 +760,31 @@ qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *
     count_launch();
     cudaMemcpyAsync(A1.X[0], A0.X[0], (size_t)Bc * kIn0 * sizeof(__nv_bfloat16),
                     cudaMemcpyDeviceToDevice, st);
-    forward(e, 0, A0, st);
-    forward(e, 1, A1, st);
+    const int rows_tc = (Bc + 127) / 128 * 128;
+    if (!tc || !forward_tc(e, 0, A0, rows_tc, mx0, mw0, dst, st) ||
+        !forward_tc(e, 1, A1, rows_tc, mx1, mw1, dst, st)) {
+      if (tc) {  // a launch was refused: finish on the WMMA path
+        tc = false;
+        cudaGetLastError();
+      }
+      forward(e, 0, A0, st);
+      forward(e, 1, A1, st);
+    }
     const int nl = (int)e->layers.size();
     predict_finish_kernel<<<grid_of(cnt), 256, 0, st>>>(th, n, off, cnt, e->d, e->centre, e->half,
                                                         e->coef, e->sigma, A0.Z[nl - 1],
                                                         A1.Z[nl - 1], thr, od, fd, dis);
     count_launch();
+  }
+  if (dst) {
+    DevStatus hs{};
+    cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    const cudaError_t err = cudaStreamSynchronize(st);
+    cudaFree(dst);
+    if (err != cudaSuccess)
+      return efail(QML_ECUDA, std::string("emulator inference: ") + cudaGetErrorString(err));
+    if (hs.code != 0)
+      return efail(QML_ETIMEOUT, "emulator inference: a tensor-core wait ran out of time");
   }
   return QML_OK;
 }
@@ -818,11 +1041,14 @@ qml_status emu_train(qml_emu *e, int32_t n, const double *theta, const double *l
     keep.push_back(vd);
     keep.push_back(vo);
     keep.push_back(vf);
-    if (!vd || !vo || !vf ||
-        run_predict(e, n_val, th + (int64_t)n * e->d, INFINITY, vo, vf, vd, st) != QML_OK) {
+    const qml_status ps = (!vd || !vo || !vf)
+                              ? QML_ENOMEM
+                              : run_predict(e, n_val, th + (int64_t)n * e->d, INFINITY, vo, vf,
+                                            vd, st);
+    if (ps != QML_OK) {
       cleanup();
       e->fitted = false;
-      return efail(QML_ENOMEM, "emu_train: held-out evaluation failed");
+      return ps == QML_ENOMEM ? efail(QML_ENOMEM, "emu_train: held-out evaluation failed") : ps;
     }
     std::vector<double> dh(n_val), oh(n_val);
     std::vector<int> fh(n_val);
@@ -865,10 +1091,12 @@ qml_status emu_predict(qml_emu *e, int32_t n, const double *theta, double tol, d
     cudaMalloc(&fd, n * sizeof(int));
     keep.push_back(fd);
   }
-  if (!th || !od || (flags && !fd) ||
-      run_predict(e, n, th, flag_threshold(e, tol), od, fd, nullptr, st) != QML_OK) {
+  const qml_status ps = (!th || !od || (flags && !fd))
+                            ? QML_ENOMEM
+                            : run_predict(e, n, th, flag_threshold(e, tol), od, fd, nullptr, st);
+  if (ps != QML_OK) {
     for (void *p : keep) cudaFree(p);
-    return efail(QML_ENOMEM, "emu_predict: allocation failed");
+    return ps == QML_ENOMEM ? efail(QML_ENOMEM, "emu_predict: allocation failed") : ps;
   }
   if (out_host) cudaMemcpyAsync(out, od, n * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (flags_host) cudaMemcpyAsync(flags, fd, n * sizeof(int), cudaMemcpyDeviceToHost, st);

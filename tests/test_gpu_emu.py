@@ -132,3 +132,30 @@ def test_emu_end_to_end_exact_labels(api):
     print("exact", t_exact, "s; emulator with fallback", t_emu, "s")
     assert t_emu < t_exact
     emu.free()
+
+
+@pytest.mark.parametrize("width,depth", [(256, 4), (64, 2), (192, 1)])
+def test_emu_tcgen05_inference_matches_wmma(api, width, depth):
+    """Inference layers after the first run on tcgen05 (bias and GELU fused);
+    tuning key emu_tc = 0 runs every layer through the WMMA product instead.
+    Same trained network, same points: the two differ only in float32
+    accumulation order (and the bf16 rounding it can flip), far inside the
+    0.05 audit tolerance; 70000 points cover a second 65536-point chunk and a
+    ragged last tile."""
+    rng = np.random.default_rng(9)
+    th = rng.uniform(-1, 1, size=(2048, 3))
+    y = -0.5 * (th ** 2 * np.array([20.0, 6.0, 2.0])).sum(axis=1) + np.sin(3 * th[:, 0])
+    emu = api.Emulator(-np.ones(3), np.ones(3), width=width, depth=depth, seed=4)
+    emu.train(th, y, epochs=10, batch=64)
+    test = rng.uniform(-1.05, 1.05, size=(70000, 3))
+    pred_tc, flags_tc = emu.predict(test, tol=0.05)
+    api.tune_set("emu_tc", 0)
+    try:
+        pred_w, flags_w = emu.predict(test, tol=0.05)
+    finally:
+        api.tune_set("emu_tc", 1)
+    d = np.abs(pred_tc - pred_w)
+    assert np.all(np.isfinite(pred_tc))
+    assert d.max() <= 5e-3, d.max()
+    assert np.mean(flags_tc == flags_w) >= 0.99
+    emu.free()
