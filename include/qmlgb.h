@@ -203,7 +203,11 @@ qml_status emu_train(qml_emu *emu, int32_t n, const double *theta, const double 
  * tol (|delta lnL|): tol / 2, lowered below the smallest held-out disagreement
  * at which a held-out point (or one of lower disagreement) missed by more
  * than 0.8 tol.  The caller evaluates flagged points exactly
- * (pix_loglike_batch). */
+ * (pix_loglike_batch).  The emulator keeps its inference buffers between
+ * calls (both heads' activations for up to 65536 points, about a gigabyte at
+ * width 256; released by emu_free), so calls on one emulator must not overlap;
+ * each call returns after its work has finished.  QML_ETIMEOUT when a
+ * tensor-core wait ran out of time. */
 qml_status emu_predict(qml_emu *emu, int32_t n, const double *theta, double tol, double *out,
                        int32_t *flags, void *stream);
 /* The head-disagreement threshold emu_predict applies for accuracy target

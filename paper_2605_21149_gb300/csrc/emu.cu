@@ -566,6 +566,9 @@ struct qml_emu {
   // running maximum of the prediction error up to it
   std::vector<double> val_dis, val_maxerr;
   std::vector<void *> mem;
+  // buffers of emu_predict, kept between calls (freed by emu_free)
+  void *pcache = nullptr;
+  void (*pcache_free)(void *) = nullptr;
 };
 
 namespace {
@@ -735,22 +738,58 @@ const double *dev_in(const double *p, size_t count, std::vector<void *> &keep) {
 }
 
 // Predictions (and flags / disagreements when given) at n device points.
+// Activations of both heads for emu_predict, their tensor maps and a status
+// word, sized for `rows` points per chunk; kept in the emulator between calls
+// (the buffers are about a gigabyte at width 256, and allocating and freeing
+// them each call would cost more than the inference).
+struct PredCache {
+  int rows = 0;
+  Acts A0, A1;
+  bool tc = false;
+  std::vector<CUtensorMap> mx0, mw0, mx1, mw1;
+  DevStatus *dst = nullptr;
+  ~PredCache() {
+    if (dst) cudaFree(dst);
+  }
+};
+
+void free_pred_cache(void *p) { delete (PredCache *)p; }
+
+PredCache *pred_cache(qml_emu *e, int rows) {
+  PredCache *c = (PredCache *)e->pcache;
+  if (c && c->rows >= rows) return c;
+  if (c) {
+    cudaDeviceSynchronize();
+    delete c;
+    e->pcache = nullptr;
+  }
+  c = new PredCache();
+  c->rows = rows;
+  if (!c->A0.make(e, rows) || !c->A1.make(e, rows) ||
+      cudaMalloc(&c->dst, sizeof(DevStatus)) != cudaSuccess) {
+    delete c;
+    return nullptr;
+  }
+  c->tc = use_tc(e) && make_tc_maps(e, 0, c->A0, rows, c->mx0, c->mw0) &&
+          make_tc_maps(e, 1, c->A1, rows, c->mx1, c->mw1);
+  e->pcache = c;
+  e->pcache_free = free_pred_cache;
+  return c;
+}
+
 qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *od, int *fd,
                        double *dis, cudaStream_t st) {
   const int chunk = 65536;
   // activation rows allocated in whole 128-row tiles (the tcgen05 layers read
   // and write complete tiles; rows past the points are never used)
   const int rows_alloc = (std::min(chunk, (n + 15) / 16 * 16) + 127) / 128 * 128;
-  Acts A0, A1;
-  if (!A0.make(e, rows_alloc) || !A1.make(e, rows_alloc)) return QML_ENOMEM;
-  bool tc = use_tc(e);
-  std::vector<CUtensorMap> mx0, mw0, mx1, mw1;
-  DevStatus *dst = nullptr;
-  if (tc)
-    tc = make_tc_maps(e, 0, A0, rows_alloc, mx0, mw0) &&
-         make_tc_maps(e, 1, A1, rows_alloc, mx1, mw1) &&
-         cudaMalloc(&dst, sizeof(DevStatus)) == cudaSuccess &&
-         cudaMemsetAsync(dst, 0, sizeof(DevStatus), st) == cudaSuccess;
+  PredCache *pc = pred_cache(e, rows_alloc);
+  if (!pc) return QML_ENOMEM;
+  Acts &A0 = pc->A0, &A1 = pc->A1;
+  bool tc = pc->tc && use_tc(e);
+  const std::vector<CUtensorMap> &mx0 = pc->mx0, &mw0 = pc->mw0, &mx1 = pc->mx1, &mw1 = pc->mw1;
+  DevStatus *dst = pc->dst;
+  if (cudaMemsetAsync(dst, 0, sizeof(DevStatus), st) != cudaSuccess) return QML_ENOMEM;
   for (int off = 0; off < n; off += chunk) {
     const int cnt = std::min(chunk, n - off);
     const int Bc = (cnt + 15) / 16 * 16;
@@ -776,11 +815,10 @@ qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *
                                                         A1.Z[nl - 1], thr, od, fd, dis);
     count_launch();
   }
-  if (dst) {
+  {
     DevStatus hs{};
     cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, st);
     const cudaError_t err = cudaStreamSynchronize(st);
-    cudaFree(dst);
     if (err != cudaSuccess)
       return efail(QML_ECUDA, std::string("emulator inference: ") + cudaGetErrorString(err));
     if (hs.code != 0)
@@ -902,6 +940,7 @@ qml_status emu_create(int32_t ndim, const double *lo, const double *hi, int32_t 
 void emu_free(qml_emu *emu) {
   if (!emu) return;
   cudaDeviceSynchronize();
+  if (emu->pcache && emu->pcache_free) emu->pcache_free(emu->pcache);
   for (void *p : emu->mem) cudaFree(p);
   delete emu;
 }
