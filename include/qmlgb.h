@@ -271,9 +271,11 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *   batch_graphs    1 (default) / 0: pix_loglike_batch replays each worker's
  *                   per-item kernel sequence as a captured CUDA graph
  *   ozaki_stages    6 (default) / 4: depth of the split kernel's TMA ring
- *   emu_tc          1 (default) / 0: emulator inference runs the layers
- *                   after the first on tcgen05 (width a multiple of 64, at
- *                   most 256) / every layer through the WMMA product
+ *   emu_tc          1 (default) / 0: emulator inference runs its layers on
+ *                   tcgen05 (width a multiple of 64, at most 256) / every
+ *                   layer through the WMMA product
+ *   emu_tc0         1 (default) / 0: with emu_tc, the first layer (16
+ *                   inputs, widened with zeros to 64) on tcgen05 too / WMMA
  *   split_diag_df   0 (default) / 1: the split-precision Cholesky factors
  *                   its 64-wide diagonal blocks and their row solves in
  *                   float64 / in float-float (about 2^-46 per operation)

@@ -12,8 +12,9 @@
 //
 // Every product runs on tensor cores: in training WMMA bf16 x bf16 -> fp32
 // (forward Z = X W^T, data gradient dX = dZ W, weight gradient dW = dZ^T X);
-// at inference the layers after the first on tcgen05 with the bias and GELU
-// fused into the epilogue (mlp_tc_kernel).  Master
+// at inference every layer on tcgen05 with the bias and GELU fused into the
+// epilogue (mlp_tc_kernel; the first layer's 16 inputs widened with zeros to
+// one 64-column stage).  Master
 // weights, gradients and the Adam state are float32; each layer's input
 // activations and its weights are rounded to bf16 for the products.
 // Prediction averages the two heads; a point is flagged for exact evaluation
@@ -260,6 +261,20 @@ __global__ void gather_kernel(const double *theta, int n, int d, const double *c
       if (tb && b < nreal) tb[b] = targ[(off + (int64_t)b * stride) % n];
       else if (tb) tb[b] = 0.0f;
     }
+  }
+}
+
+// dst (rows x dcols, bf16 row-major) <- src (rows x cols) with zero columns
+// cols .. dcols - 1 (the 16 inputs of the first layer widened to one
+// 64-column tensor-core stage)
+__global__ void pad_cols_kernel(const __nv_bfloat16 *src, int rows, int cols, __nv_bfloat16 *dst,
+                                int dcols) {
+  const int64_t total = (int64_t)rows * dcols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / dcols;
+    const int c = (int)(t - r * dcols);
+    dst[t] = c < cols ? src[r * cols + c] : __float2bfloat16_rn(0.0f);
   }
 }
 
@@ -639,10 +654,10 @@ void forward(qml_emu *e, int h, Acts &A, cudaStream_t st) {
   }
 }
 
-// Inference on tcgen05: layers after the first (K = width, a multiple of 64
-// up to 256) run as mlp_tc_kernel with bias and activation fused; the first
-// layer (16 inputs) keeps the WMMA product.  Tuning key emu_tc = 0 selects the
-// WMMA path for every layer.
+// Inference on tcgen05: every layer (K = width, a multiple of 64 up to 256;
+// the first layer's 16 inputs and weights widened with zeros to 64) runs as
+// mlp_tc_kernel with bias and activation fused.  Tuning key emu_tc = 0
+// selects the WMMA path for every layer, emu_tc0 = 0 for the first one.
 bool use_tc(const qml_emu *e) {
   return tune_get("emu_tc", 1) != 0 && e->width % 64 == 0 && e->width <= 256;
 }
@@ -663,32 +678,44 @@ bool make_tc_maps(const qml_emu *e, int h, const Acts &A, int rows,
   return true;
 }
 
+bool launch_tc_layer(int out, const CUtensorMap &mx, const CUtensorMap &mw, int rows, int in,
+                     const float *b, __nv_bfloat16 *xn, float *z, DevStatus *st, cudaStream_t s) {
+  switch (out) {
+    case 16: return launch_mlp_tc<16>(mx, mw, rows, in, b, xn, z, st, s);
+    case 64: return launch_mlp_tc<64>(mx, mw, rows, in, b, xn, z, st, s);
+    case 128: return launch_mlp_tc<128>(mx, mw, rows, in, b, xn, z, st, s);
+    case 192: return launch_mlp_tc<192>(mx, mw, rows, in, b, xn, z, st, s);
+    case 256: return launch_mlp_tc<256>(mx, mw, rows, in, b, xn, z, st, s);
+    default: return false;
+  }
+}
+
+// m0x / m0w: maps of the first layer's inputs and weights widened to 64
+// columns (then the first layer runs on tcgen05 too), or null (WMMA)
 bool forward_tc(qml_emu *e, int h, Acts &A, int rows, const std::vector<CUtensorMap> &mx,
-                const std::vector<CUtensorMap> &mw, DevStatus *st, cudaStream_t s) {
+                const std::vector<CUtensorMap> &mw, const CUtensorMap *m0x,
+                const CUtensorMap *m0w, DevStatus *st, cudaStream_t s) {
   const int nl = (int)e->layers.size();
   {
     const int out = e->layers[0].first, in = e->layers[0].second;
-    wmma_gemm<wmma::row_major, wmma::col_major>(A.B, out, in, A.X[0], in, e->ph[h] + e->woff[0],
-                                                in, A.Z[0], out, 0, s);
-    bias_act_kernel<<<grid_of((int64_t)A.B * out), 256, 0, s>>>(A.Z[0], A.B, out,
-                                                                e->p[h] + e->boff[0], A.X[1], 1);
-    count_launch();
+    if (m0x && m0w) {
+      if (!launch_tc_layer(out, *m0x, *m0w, rows, 64, e->p[h] + e->boff[0], A.X[1], nullptr, st,
+                           s))
+        return false;
+    } else {
+      wmma_gemm<wmma::row_major, wmma::col_major>(A.B, out, in, A.X[0], in,
+                                                  e->ph[h] + e->woff[0], in, A.Z[0], out, 0, s);
+      bias_act_kernel<<<grid_of((int64_t)A.B * out), 256, 0, s>>>(A.Z[0], A.B, out,
+                                                                  e->p[h] + e->boff[0], A.X[1], 1);
+      count_launch();
+    }
   }
   for (int l = 1; l < nl; ++l) {
     const int out = e->layers[l].first, in = e->layers[l].second;
-    const float *b = e->p[h] + e->boff[l];
     __nv_bfloat16 *xn = (l + 1 < nl) ? A.X[l + 1] : nullptr;
     float *z = (l + 1 < nl) ? nullptr : A.Z[l];
-    bool ok = false;
-    switch (out) {
-      case 16: ok = launch_mlp_tc<16>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
-      case 64: ok = launch_mlp_tc<64>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
-      case 128: ok = launch_mlp_tc<128>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
-      case 192: ok = launch_mlp_tc<192>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
-      case 256: ok = launch_mlp_tc<256>(mx[l], mw[l], rows, in, b, xn, z, st, s); break;
-      default: break;
-    }
-    if (!ok) return false;
+    if (!launch_tc_layer(out, mx[l], mw[l], rows, in, e->p[h] + e->boff[l], xn, z, st, s))
+      return false;
   }
   return true;
 }
@@ -747,9 +774,17 @@ struct PredCache {
   Acts A0, A1;
   bool tc = false;
   std::vector<CUtensorMap> mx0, mw0, mx1, mw1;
+  // the first layer widened to 64 input columns: inputs (rows x 64, both
+  // heads) and each head's weights (width x 64), refreshed every call
+  __nv_bfloat16 *x0p = nullptr, *w0p[2] = {nullptr, nullptr};
+  bool tc0 = false;
+  CUtensorMap mx0p, mw0p[2];
   DevStatus *dst = nullptr;
   ~PredCache() {
     if (dst) cudaFree(dst);
+    if (x0p) cudaFree(x0p);
+    for (auto *w : w0p)
+      if (w) cudaFree(w);
   }
 };
 
@@ -772,6 +807,15 @@ PredCache *pred_cache(qml_emu *e, int rows) {
   }
   c->tc = use_tc(e) && make_tc_maps(e, 0, c->A0, rows, c->mx0, c->mw0) &&
           make_tc_maps(e, 1, c->A1, rows, c->mx1, c->mw1);
+  if (c->tc) {
+    const int w0 = e->layers[0].first;
+    c->tc0 = cudaMalloc(&c->x0p, (size_t)rows * 64 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+             cudaMalloc(&c->w0p[0], (size_t)w0 * 64 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+             cudaMalloc(&c->w0p[1], (size_t)w0 * 64 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+             make_map_bf16(&c->mx0p, c->x0p, 64, rows, 128, 64, 128) &&
+             make_map_bf16(&c->mw0p[0], c->w0p[0], 64, w0, 128, 64, w0) &&
+             make_map_bf16(&c->mw0p[1], c->w0p[1], 64, w0, 128, 64, w0);
+  }
   e->pcache = c;
   e->pcache_free = free_pred_cache;
   return c;
@@ -790,6 +834,15 @@ qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *
   const std::vector<CUtensorMap> &mx0 = pc->mx0, &mw0 = pc->mw0, &mx1 = pc->mx1, &mw1 = pc->mw1;
   DevStatus *dst = pc->dst;
   if (cudaMemsetAsync(dst, 0, sizeof(DevStatus), st) != cudaSuccess) return QML_ENOMEM;
+  const bool tc0 = tc && pc->tc0 && tune_get("emu_tc0", 1) != 0;
+  if (tc0) {
+    const int w0 = e->layers[0].first;
+    for (int h = 0; h < 2; ++h) {
+      pad_cols_kernel<<<grid_of((int64_t)w0 * 64), 256, 0, st>>>(e->ph[h] + e->woff[0], w0, kIn0,
+                                                                 pc->w0p[h], 64);
+      count_launch();
+    }
+  }
   for (int off = 0; off < n; off += chunk) {
     const int cnt = std::min(chunk, n - off);
     const int Bc = (cnt + 15) / 16 * 16;
@@ -800,8 +853,15 @@ qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *
     cudaMemcpyAsync(A1.X[0], A0.X[0], (size_t)Bc * kIn0 * sizeof(__nv_bfloat16),
                     cudaMemcpyDeviceToDevice, st);
     const int rows_tc = (Bc + 127) / 128 * 128;
-    if (!tc || !forward_tc(e, 0, A0, rows_tc, mx0, mw0, dst, st) ||
-        !forward_tc(e, 1, A1, rows_tc, mx1, mw1, dst, st)) {
+    if (tc0) {
+      pad_cols_kernel<<<grid_of((int64_t)Bc * 64), 256, 0, st>>>(A0.X[0], Bc, kIn0, pc->x0p, 64);
+      count_launch();
+    }
+    if (!tc ||
+        !forward_tc(e, 0, A0, rows_tc, mx0, mw0, tc0 ? &pc->mx0p : nullptr,
+                    tc0 ? &pc->mw0p[0] : nullptr, dst, st) ||
+        !forward_tc(e, 1, A1, rows_tc, mx1, mw1, tc0 ? &pc->mx0p : nullptr,
+                    tc0 ? &pc->mw0p[1] : nullptr, dst, st)) {
       if (tc) {  // a launch was refused: finish on the WMMA path
         tc = false;
         cudaGetLastError();

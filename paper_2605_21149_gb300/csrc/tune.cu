@@ -10,8 +10,10 @@
 //   dgemm:<ta>,<tb>,<lower>,<M>,<N>,<K>,<alias>   measured tile, 10 RM + RN
 //   batch_streams    worker streams of pix_loglike_batch (default 4, 1..16)
 //   ozaki_stages     6 (default) / 4: depth of the split kernel's TMA ring
-//   emu_tc           1 (default) / 0: emulator inference layers after the
-//                    first on tcgen05 / all through the WMMA product
+//   emu_tc           1 (default) / 0: emulator inference layers on tcgen05
+//                    / all through the WMMA product
+//   emu_tc0          1 (default) / 0: with emu_tc, the first layer too (its
+//                    16 inputs widened with zeros to 64) / on WMMA
 //   split_diag_df    0 (default): the split-precision Cholesky factors its
 //                    64-wide diagonal blocks and their row solves in float64;
 //                    1: in float-float (pairs of float32, about 2^-46 per
