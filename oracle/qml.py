@@ -73,17 +73,32 @@ def total_cov(Y, cl, comps, lmin, lmax, N) -> np.ndarray:
     return signal_cov(Y, cl, comps, lmin, lmax) + N
 
 
-def _blocksum(H: np.ndarray, lmin: int, lmax: int) -> np.ndarray:
-    """Sum an (k0 x k0) array over (l, l') blocks of modes -> (nl x nl)."""
-    starts = np.array([l * l - lmin * lmin for l in range(lmin, lmax + 1)])
+def mode_starts(lmin: int, lmax: int, edges=None) -> np.ndarray:
+    """First harmonic mode of each multipole (edges None) or of each bin.
+
+    The modes of multipoles l in [e, e') are the contiguous range
+    [e^2 - lmin^2, e'^2 - lmin^2) of one field's k0 modes, so the selector of a
+    bin, E_b = sum_{l in b} E_l (Sect. 2.4: P_b = sum_{l in b} P_l), sums over
+    that range.  edges: lmin = e_0 < e_1 < ... < e_nb = lmax + 1.
+    """
+    if edges is None:
+        edges = np.arange(lmin, lmax + 2)
+    return np.array([e * e - lmin * lmin for e in edges[:-1]])
+
+
+def _blocksum(H: np.ndarray, lmin: int, lmax: int, edges=None) -> np.ndarray:
+    """Sum an (k0 x k0) array over (l, l') (or (bin, bin')) blocks of modes."""
+    starts = mode_starts(lmin, lmax, edges)
     return np.add.reduceat(np.add.reduceat(H, starts, axis=0), starts, axis=1)
 
 
-def fisher_from_W(W: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarray:
-    """F_ab = 1/2 tr[W E_a W E_b] (Eqs. fisher_harmonic, sparse_trace)."""
+def fisher_from_W(W: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None) -> np.ndarray:
+    """F_ab = 1/2 tr[W E_a W E_b] (Eqs. fisher_harmonic, sparse_trace); with
+    bin edges, a and b run over (spectrum, bin) and E_b is the bin selector
+    (Sect. 2.4)."""
     k0 = (lmax + 1) ** 2 - lmin ** 2
     nc = len(comps)
-    nl = lmax - lmin + 1
+    nl = lmax - lmin + 1 if edges is None else len(edges) - 1
     W4 = W.reshape(nc, k0, nc, k0)
     ci = {c: comps.index(c) for c in comps}
     ns = len(spec)
@@ -98,17 +113,18 @@ def fisher_from_W(W: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarra
                     if key not in cache:
                         # H[i, j] = W[v i, u' j] * W[v' j, u i]
                         H = W4[ci[v], :, ci[up], :] * W4[ci[vp], :, ci[u], :].T
-                        cache[key] = _blocksum(H, lmin, lmax)
+                        cache[key] = _blocksum(H, lmin, lmax, edges)
                     acc += cache[key]
             F[A * nl:(A + 1) * nl, B * nl:(B + 1) * nl] = 0.5 * acc
     return F
 
 
-def trace_selector(M: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarray:
-    """t_a = sum_{(u,v) in pairs(a)} sum_{i in l} M[v i, u i]  (= tr[E_a M])."""
+def trace_selector(M: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None) -> np.ndarray:
+    """t_a = sum_{(u,v) in pairs(a)} sum_{i in l} M[v i, u i]  (= tr[E_a M]);
+    per bin with edges (Sect. 2.4)."""
     k0 = (lmax + 1) ** 2 - lmin ** 2
-    nl = lmax - lmin + 1
-    starts = np.array([l * l - lmin * lmin for l in range(lmin, lmax + 1)])
+    nl = lmax - lmin + 1 if edges is None else len(edges) - 1
+    starts = mode_starts(lmin, lmax, edges)
     out = np.zeros(len(spec) * nl)
     for A, sa in enumerate(spec):
         acc = np.zeros(nl)
@@ -120,12 +136,13 @@ def trace_selector(M: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarr
     return out
 
 
-def quad_selector(w: np.ndarray, spec, comps, lmin: int, lmax: int) -> np.ndarray:
-    """y_a = 1/2 w^T E_a w for each column of w (Eq. q_harmonic); shape (na, nsims)."""
+def quad_selector(w: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None) -> np.ndarray:
+    """y_a = 1/2 w^T E_a w for each column of w (Eq. q_harmonic); shape (na, nsims);
+    per bin with edges (Sect. 2.4)."""
     w = np.atleast_2d(w.T).T if w.ndim == 1 else w
     k0 = (lmax + 1) ** 2 - lmin ** 2
-    nl = lmax - lmin + 1
-    starts = np.array([l * l - lmin * lmin for l in range(lmin, lmax + 1)])
+    nl = lmax - lmin + 1 if edges is None else len(edges) - 1
+    starts = mode_starts(lmin, lmax, edges)
     out = np.zeros((len(spec) * nl, w.shape[1]))
     for A, sa in enumerate(spec):
         acc = np.zeros((nl, w.shape[1]))
@@ -168,26 +185,29 @@ def loglike(C: np.ndarray, d: np.ndarray):
     return -0.5 * (chi2 + logdet), chi2, logdet
 
 
-def qml(Y, cl_fid, comps, lmin, lmax, N, spec, maps=None, want_bias=True):
+def qml(Y, cl_fid, comps, lmin, lmax, N, spec, maps=None, want_bias=True, edges=None):
     """Fisher matrix, noise bias, quadratic estimates and Cl in three modes.
 
     Follows Sect. 2.2 (Eqs. fisher, q_ell, noise_bias, qml_estimate) in the
-    harmonic factorisation of Sect. 2.3.3.  Returns a dict.
+    harmonic factorisation of Sect. 2.3.3.  With bin edges (Sect. 2.4) the
+    bin derivative P_b = sum_{l in b} P_l takes the place of P_l in F, q and
+    the noise bias, and the normalisations act on the binned F.  Returns a
+    dict.
     """
     C = total_cov(Y, cl_fid, comps, lmin, lmax, N)
     cf = sla.cho_factor(C, lower=True)
     Z = sla.cho_solve(cf, Y)          # C^-1 Y
     W = Y.T @ Z                       # Y^T C^-1 Y   (Eq. projected_inv)
     W = 0.5 * (W + W.T)
-    F = fisher_from_W(W, spec, comps, lmin, lmax)
+    F = fisher_from_W(W, spec, comps, lmin, lmax, edges)
     out = {"F": F, "W": W, "C": C}
     if want_bias:
         ZNZ = Z.T @ (N @ Z)
-        out["b"] = 0.5 * trace_selector(ZNZ, spec, comps, lmin, lmax)
+        out["b"] = 0.5 * trace_selector(ZNZ, spec, comps, lmin, lmax, edges)
     if maps is not None:
         maps = maps.reshape(maps.shape[0], -1)
         w = Y.T @ sla.cho_solve(cf, maps)   # Y^T C^-1 d  (Eq. weighted_data)
-        y = quad_selector(w, spec, comps, lmin, lmax)
+        y = quad_selector(w, spec, comps, lmin, lmax, edges)
         out["w"] = w
         out["y"] = y
         if want_bias:
@@ -198,9 +218,21 @@ def qml(Y, cl_fid, comps, lmin, lmax, N, spec, maps=None, want_bias=True):
     return out
 
 
-def qml_for(wl, Y, maps=None, want_bias=True):
+def qml_for(wl, Y, maps=None, want_bias=True, edges=None):
     """qml() for a synthetic workload description."""
-    return qml(Y, wl.cl_fid, wl.comps, wl.lmin, wl.lmax, wl.N(), wl.spec, maps, want_bias)
+    return qml(Y, wl.cl_fid, wl.comps, wl.lmin, wl.lmax, wl.N(), wl.spec, maps, want_bias, edges)
+
+
+def bin_matrix(nspec: int, lmin: int, lmax: int, edges) -> np.ndarray:
+    """P_Sigma: the 0/1 matrix summing each spectrum's multipoles into its bins
+    (nspec nb x nspec nl, spectrum-major), for the identity of Sect. 3 (check
+    of the binned path): F_bin = P_Sigma F P_Sigma^T, q_b = sum_{l in b} q_l."""
+    nl, nb = lmax - lmin + 1, len(edges) - 1
+    P = np.zeros((nspec * nb, nspec * nl))
+    for s in range(nspec):
+        for b in range(nb):
+            P[s * nb + b, s * nl + edges[b] - lmin:s * nl + edges[b + 1] - lmin] = 1.0
+    return P
 
 
 def simulate(Y: np.ndarray, alm: np.ndarray, noise: np.ndarray) -> np.ndarray:

@@ -182,3 +182,71 @@ def test_mutation_dropped_cross_pair_is_caught(monkeypatch):
     r = qml.qml(Y, cl, comps, lmin, lmax, N, spec)
     Fc, _, _ = _closed_form(cl, tl, 0.5, spec, comps, lmin, lmax)
     assert np.abs(r["F"] - Fc).max() > 1e-3 * np.abs(Fc).max()
+
+
+# ---- P10: native multipole binning (Sect. 2.4) ---------------------------
+BIN_EDGES = {2: [2, 4, 6], 3: [2, 5, 6], 5: [2, 6], "ragged": [2, 3, 6]}  # lmax = 5
+
+
+@pytest.mark.parametrize("dl", [2, 3, 5, "ragged"])
+def test_P10_binning_identity(dl):
+    """The check of the binned path (Sect. 3): F_bin = P_Sigma F P_Sigma^T and
+    q_b = sum_{l in b} q_l (likewise the noise bias) to machine precision, the
+    binned side computed with the bin selectors E_b = sum_{l in b} E_l."""
+    t = _tiny()
+    edges = np.array(BIN_EDGES[dl])
+    r = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"])
+    rb = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"],
+                 edges=edges)
+    P = qml.bin_matrix(len(t["spec"]), 2, t["lmax"], edges)
+    assert np.abs(rb["F"] - P @ r["F"] @ P.T).max() <= 1e-13 * np.abs(rb["F"]).max()
+    for key in ("y", "b", "q"):
+        ref = P @ r[key]
+        assert np.abs(rb[key] - ref).max() <= 1e-13 * np.abs(ref).max(), key
+    # the normalisations act on the binned F: F_b C_b^deconv = q_b
+    assert np.abs(rb["F"] @ rb["cl_deconv"] - rb["q"]).max() <= 1e-10 * np.abs(rb["q"]).max()
+
+
+def test_P10_binning_vs_brute():
+    """Binned F, noise bias and y against dense pixel traces with the bin
+    derivative P_b = sum_{l in b} P_l built from the brute-force responses
+    (independent of the harmonic selectors)."""
+    t = _tiny()
+    edges = np.array(BIN_EDGES[2])
+    rb = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"],
+                 edges=edges)
+    Ps = brute.pixel_derivatives(t["th"], t["ph"], t["th"], t["ph"], t["tl"], t["tl"],
+                                 True, True, 2, t["lmax"], t["spec"])
+    nl = t["lmax"] - 1
+    Pb = [sum(Ps[s * nl + l - 2] for l in range(edges[b], edges[b + 1]))
+          for s in range(len(t["spec"])) for b in range(len(edges) - 1)]
+    ref = brute.qml_dense(Pb, rb["C"], t["N"], maps=t["d"])
+    for key in ("F", "b", "y"):
+        assert np.abs(rb[key] - ref[key]).max() <= 1e-12 * np.abs(ref[key]).max(), key
+
+
+def test_P10_unit_bins_are_per_l():
+    """Bins of one multipole reproduce the per-l estimator (the single code
+    path of Sect. 2.4 with Delta l = 1)."""
+    t = _tiny(has_P=False)
+    r = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"])
+    rb = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"],
+                 edges=np.arange(2, t["lmax"] + 2))
+    for key in ("F", "b", "y", "cl_deconv", "cl_decorr"):
+        assert np.array_equal(rb[key], r[key]), key
+
+
+def test_mutation_bin_range_off_by_one_is_caught(monkeypatch):
+    """Starting every bin's mode range one multipole late (a plausible index
+    slip in E_b) breaks the brute-force binning pin."""
+    orig = qml.mode_starts
+
+    def late(lmin, lmax, edges=None):
+        if edges is None:
+            return orig(lmin, lmax)
+        shifted = np.array([e + 1 if 0 < i < len(edges) - 1 else e for i, e in enumerate(edges)])
+        return orig(lmin, lmax, shifted)
+
+    monkeypatch.setattr(qml, "mode_starts", late)
+    with pytest.raises(AssertionError):
+        test_P10_binning_vs_brute()
