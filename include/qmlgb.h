@@ -88,6 +88,15 @@ typedef struct {
   int32_t precision;             /* qml_precision */
   int32_t nslices;               /* bf16 slices per operand for QML_SPLIT_BF16
                                     (0 = library default) */
+  /* Native multipole binning (Sect. 2.4), read by qml_fisher only: 0 = one
+   * bin per multipole; else nbins bins per spectrum with HOST edges
+   * bin_edges[0] = lmin < bin_edges[1] < ... < bin_edges[nbins] = lmax + 1,
+   * bin b = [bin_edges[b], bin_edges[b+1]).  The bin derivative
+   * P_b = sum_{l in b} P_l replaces P_l: F, the noise bias and y become
+   * nspec x nbins entries (spectrum-major) and the three normalisations act
+   * on the binned F. */
+  int32_t nbins;
+  const int32_t *bin_edges;
 } qml_problem;
 
 typedef struct qml_plan qml_plan;   /* opaque; owned by the library */

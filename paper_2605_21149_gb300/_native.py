@@ -30,6 +30,7 @@ class QmlProblem(ctypes.Structure):
         ("nspec", c_int32), ("spec", c_int32 * 6),
         ("cl_fid", c_void_p), ("N", c_void_p),
         ("precision", c_int32), ("nslices", c_int32),
+        ("nbins", c_int32), ("bin_edges", c_void_p),
     ]
 
 

@@ -101,7 +101,7 @@ class Problem:
 
     def __init__(self, lmin, lmax, *, theta_T=None, phi_T=None, theta_P=None, phi_P=None,
                  transfer_T=None, transfer_P=None, spec=("TT",), cl_fid=None, N=None,
-                 precision=nat.QML_FP64, nslices=0):
+                 precision=nat.QML_FP64, nslices=0, bin_edges=None):
         self._keep = []
         has_T = theta_T is not None
         has_P = theta_P is not None
@@ -116,7 +116,10 @@ class Problem:
         self.k = len(self.comps) * self.k0
         self.nl = self.lmax - self.lmin + 1
         self.spec = tuple(SPEC_INDEX[s] if isinstance(s, str) else int(s) for s in spec)
-        self.na = len(self.spec) * self.nl
+        # native binning (Sect. 2.4): host edges lmin = e_0 < ... < e_nb = lmax + 1
+        edges = None if bin_edges is None else np.ascontiguousarray(bin_edges, dtype=np.int32)
+        self.nb = self.nl if edges is None else len(edges) - 1
+        self.na = len(self.spec) * self.nb
         p = nat.QmlProblem()
         p.has_T, p.has_P = int(has_T), int(has_P)
         p.npix_T, p.npix_P = self.npix_T, self.npix_P
@@ -132,10 +135,14 @@ class Problem:
         p.N = _mat(N, self.n, self.n, self._keep) if N is not None else None
         p.precision = int(precision)
         p.nslices = int(nslices)
+        if edges is not None:
+            self._keep.append(edges)
+            p.nbins = len(edges) - 1
+            p.bin_edges = edges.ctypes.data
         self._p = p
 
     @classmethod
-    def from_workload(cls, wl, device=True, precision=nat.QML_FP64, nslices=0):
+    def from_workload(cls, wl, device=True, precision=nat.QML_FP64, nslices=0, bin_edges=None):
         """Problem from a synth.Workload; device=True puts every array on cuda:0."""
         def conv(a):
             if a is None or len(a) == 0:
@@ -153,7 +160,7 @@ class Problem:
                    transfer_P=conv(wl.transfer_P) if wl.has_P else None,
                    spec=wl.spec, cl_fid=conv(wl.cl_fid.reshape(-1)),
                    N=(torch.as_tensor(N, device="cuda") if device else N),
-                   precision=precision, nslices=nslices)
+                   precision=precision, nslices=nslices, bin_edges=bin_edges)
 
     @property
     def ref(self):

@@ -465,6 +465,21 @@ void build_C_split(Call &c, Split &sp, const Staged &s, const Dims &d, double *Y
 }  // namespace
 
 // ======================================================================
+// Bin edges of a problem (Sect. 2.4): empty for one bin per multipole.
+qml_status check_bins(const qml_problem *p, const Dims &d, std::vector<int> &edges) {
+  edges.clear();
+  if (p->nbins < 0) return fail(QML_EINVAL, "nbins must be >= 0");
+  if (p->nbins == 0) return QML_OK;
+  if (!p->bin_edges) return fail(QML_EINVAL, "nbins > 0 needs bin_edges");
+  if (p->nbins > d.nl) return fail(QML_EINVAL, "more bins than multipoles");
+  edges.assign(p->bin_edges, p->bin_edges + p->nbins + 1);
+  if (edges.front() != d.lmin || edges.back() != d.lmax + 1)
+    return fail(QML_EINVAL, "bin_edges must run from lmin to lmax + 1");
+  for (int b = 0; b < p->nbins; ++b)
+    if (edges[b + 1] <= edges[b]) return fail(QML_EINVAL, "bin_edges must increase strictly");
+  return QML_OK;
+}
+
 struct qml_plan {
   Dims d;
   int nspec = 0;
@@ -478,6 +493,12 @@ struct qml_plan {
   int nslices = 0;
   double *F = nullptr, *b = nullptr, *Finv = nullptr, *Fm12 = nullptr;
   int *uv = nullptr;
+  // native binning (Sect. 2.4): na = nspec x bins is the size of F and of
+  // every estimate; na_l = nspec x multipoles that of the per-l sums, which
+  // the device arrays bstart / bcount (na entries) gather into bins
+  int na_l = 0;
+  bool binned = false;
+  int *bstart = nullptr, *bcount = nullptr;
 };
 
 extern "C" {
@@ -536,9 +557,15 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
   if (s != QML_OK) return s;
   if (!F) return fail(QML_EINVAL, "F is NULL");
   if (plan_out) *plan_out = nullptr;
-  const int na = prob->nspec * d.nl;
+  std::vector<int> edges;
+  s = check_bins(prob, d, edges);
+  if (s != QML_OK) return s;
+  const bool binned = !edges.empty();
+  const int na_l = prob->nspec * d.nl;  // per-multipole entries
+  const int nb = binned ? prob->nbins : d.nl;
+  const int na = prob->nspec * nb;      // entries of F and of the estimates
   const int naf = d.nspec_full * d.nl;
-  if (na + (na & 1) > 2048)
+  if (na_l + (na_l & 1) > 2048)
     return fail(QML_EINVAL, "Fisher matrix larger than 2048 (nspec x (lmax - lmin + 1))");
   Call c(stream);
   Staged sp;
@@ -552,6 +579,8 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
   plan->nspec = prob->nspec;
   for (int i = 0; i < 6; ++i) plan->spec[i] = prob->spec[i];
   plan->na = na;
+  plan->na_l = na_l;
+  plan->binned = binned;
   plan->st = c.st;
   auto palloc = [&](size_t count) -> double * {
     void *p = nullptr;
@@ -577,6 +606,28 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
       plan->mem.push_back(p);
     plan->uv = (int *)p;
   }
+  std::vector<int> h_bins;  // bstart then bcount, kept alive until the copy completes
+  if (binned) {
+    h_bins.resize(2 * (size_t)na);
+    for (int sp = 0; sp < prob->nspec; ++sp)
+      for (int bb = 0; bb < nb; ++bb) {
+        h_bins[sp * nb + bb] = sp * d.nl + (edges[bb] - d.lmin);
+        h_bins[na + sp * nb + bb] = edges[bb + 1] - edges[bb];
+      }
+    void *p = nullptr;
+    if (c.err == QML_OK &&
+        c.cuda_ok(cudaMallocAsync(&p, h_bins.size() * sizeof(int), c.st), "plan bins")) {
+      plan->mem.push_back(p);
+      plan->bstart = (int *)p;
+      plan->bcount = plan->bstart + na;
+      c.cuda_ok(cudaMemcpyAsync(p, h_bins.data(), h_bins.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, c.st),
+                "plan bins");
+    }
+  }
+  // per-multipole F and noise bias (the plan's own when not binned)
+  double *Fl = binned ? c.alloc<double>((size_t)na_l * na_l, "per-l F") : plan->F;
+  double *bl = binned ? c.alloc<double>(na_l, "per-l b") : plan->b;
   double *ldparts = c.alloc<double>(nblocks);
   double *W = c.alloc<double>((size_t)d.k * d.k, "W");
   const int NP = d.nc * d.nc, NU = NP * (NP + 1) / 2;
@@ -628,7 +679,11 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
   launch_fisher_blocksum(W, d.k, d.nc, d.k0, d.lmin, d.lmax, parts, diag, c.st);
   launch_fisher_assemble(parts, diag, d.nc, d.nl, d.nspec_full, uv_full, Ffull, tfull, c.st);
   launch_fisher_select(Ffull, tfull, sp.cl, d.lmin, d.lmax, d.nspec_full, ids_full, prob->nspec,
-                       sel, plan->F, plan->b, c.st);
+                       sel, Fl, bl, c.st);
+  if (binned) {  // P_b = sum_{l in b} P_l: F and the noise bias summed over bins
+    launch_bin_fisher(Fl, na_l, plan->bstart, plan->bcount, na, plan->F, c.st);
+    launch_bin_rows(bl, na_l, 1, plan->bstart, plan->bcount, na, plan->b, c.st);
+  }
   c.cuda_ok(run_fisher_eig(plan->F, na, eigw, plan->Finv, plan->Fm12, minmax, c.status, c.st),
             "eigendecomposition");
   launch_copy_matrix(plan->F, na, Fout, na, na, na, c.st);
@@ -674,7 +729,14 @@ qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims, doubl
     trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, U, nsims, d.n);
     launch_dgemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, w, d.k, 0, c.status, c.st);
   }
-  launch_quad_y(w, d.k, nsims, d.nc, d.k0, d.lmin, d.lmax, plan->nspec, plan->uv, yd, c.st);
+  if (plan->binned) {  // per-l y, then summed over bins
+    double *yl = c.alloc<double>((size_t)plan->na_l * nsims, "per-l y");
+    if (c.err != QML_OK) return c.finish();
+    launch_quad_y(w, d.k, nsims, d.nc, d.k0, d.lmin, d.lmax, plan->nspec, plan->uv, yl, c.st);
+    launch_bin_rows(yl, plan->na_l, nsims, plan->bstart, plan->bcount, na, yd, c.st);
+  } else {
+    launch_quad_y(w, d.k, nsims, d.nc, d.k0, d.lmin, d.lmax, plan->nspec, plan->uv, yd, c.st);
+  }
   launch_sub_bias(yd, plan->b, na, nsims, q, c.st);
   if (bd) launch_copy_matrix(plan->b, na, bd, na, na, 1, c.st);
   if (dec) launch_dgemm(0, 0, na, nsims, na, 1.0, plan->Finv, na, q, na, 0.0, dec, na, 0, c.status, c.st);

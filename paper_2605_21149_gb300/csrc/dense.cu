@@ -1106,6 +1106,52 @@ void launch_loglike_finish(const double *chi2, const double *logdet, int nmaps, 
   { loglike_finish_kernel<<<(nmaps + 127) / 128, 128, 0, st>>>(chi2, logdet, nmaps, lnL); count_launch(); }
 }
 
+// Native binning (Sect. 2.4): bin B of the binned index covers the per-l
+// rows bstart[B] .. bstart[B] + bcount[B] - 1.
+// dst (nab x ncols, ld nab) <- per-bin sums of the rows of src (na x ncols, ld na)
+__global__ void bin_rows_kernel(const double *src, int na, int ncols, const int *bstart,
+                                const int *bcount, int nab, double *dst) {
+  const int64_t total = (int64_t)nab * ncols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int B = (int)(t % nab);
+    const int64_t j = t / nab;
+    double s = 0.0;
+    for (int u = 0; u < bcount[B]; ++u) s += src[bstart[B] + u + j * na];
+    dst[B + j * nab] = s;
+  }
+}
+
+// Fb (nab x nab) <- per-(bin, bin') block sums of the symmetric F (na x na);
+// (B, B') and (B', B) add the same entries in the same order, so Fb is exactly
+// symmetric
+__global__ void bin_fisher_kernel(const double *F, int na, const int *bstart, const int *bcount,
+                                  int nab, double *Fb) {
+  const int64_t total = (int64_t)nab * nab;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int B = (int)(t % nab), B2 = (int)(t / nab);
+    const int lo = B < B2 ? B : B2, hi = B < B2 ? B2 : B;
+    double s = 0.0;
+    for (int u = 0; u < bcount[hi]; ++u)
+      for (int v = 0; v < bcount[lo]; ++v)
+        s += F[(bstart[lo] + v) + (int64_t)(bstart[hi] + u) * na];
+    Fb[t] = s;
+  }
+}
+
+void launch_bin_rows(const double *src, int na, int ncols, const int *bstart, const int *bcount,
+                     int nab, double *dst, cudaStream_t st) {
+  if (nab <= 0 || ncols <= 0) return;
+  { bin_rows_kernel<<<grid_for((int64_t)nab * ncols), 256, 0, st>>>(src, na, ncols, bstart, bcount, nab, dst); count_launch(); }
+}
+
+void launch_bin_fisher(const double *F, int na, const int *bstart, const int *bcount, int nab,
+                       double *Fb, cudaStream_t st) {
+  if (nab <= 0) return;
+  { bin_fisher_kernel<<<grid_for((int64_t)nab * nab), 256, 0, st>>>(F, na, bstart, bcount, nab, Fb); count_launch(); }
+}
+
 // X (ld x ld, first n rows / columns used) <- block diagonal of the kNB x kNB
 // inverses Dinv (consecutive blocks of kNB * kNB), zeros elsewhere
 __global__ void place_diag_kernel(const double *Dinv, int64_t n, double *X, int64_t ld) {

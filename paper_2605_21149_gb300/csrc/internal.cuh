@@ -108,6 +108,13 @@ void launch_place_diag_inverses(const double *Dinv, int64_t n, double *X, int64_
                                 cudaStream_t st);
 
 void launch_sum_logdet(const double *parts, int nparts, double *out, cudaStream_t st);
+// Native binning: dst (nab x ncols, ld nab) <- per-bin row sums of src (na x
+// ncols, ld na), bin B = rows bstart[B] .. + bcount[B] - 1 (device arrays);
+// Fb (nab x nab) <- per-(bin, bin') block sums of the symmetric F (na x na).
+void launch_bin_rows(const double *src, int na, int ncols, const int *bstart, const int *bcount,
+                     int nab, double *dst, cudaStream_t st);
+void launch_bin_fisher(const double *F, int na, const int *bstart, const int *bcount, int nab,
+                       double *Fb, cudaStream_t st);
 void launch_copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t n,
                        cudaStream_t st);
 void launch_symmetrize_lower(double *A, int64_t lda, int64_t n, cudaStream_t st);

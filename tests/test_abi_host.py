@@ -111,3 +111,55 @@ def test_tuning_table_round_trip(lib):
     need = lib.qml_tune_table(None, 0)
     buf = ctypes.create_string_buffer(b"x" * 4)
     assert lib.qml_tune_table(buf, 4) == need and buf.raw[:4] == b"xxxx"
+
+
+def _bins(edges):
+    arr = (ctypes.c_int32 * len(edges))(*edges)
+    return len(edges) - 1, ctypes.cast(arr, ctypes.c_void_p), arr
+
+
+@pytest.mark.parametrize("edges,needle", [
+    ([3, 4, 6], "lmin"),          # must start at lmin = 2
+    ([2, 4, 5], "lmax + 1"),      # must end at lmax + 1 = 6
+    ([2, 4, 4, 6], "increase"),
+    ([2, 3, 4, 5, 6, 7], "more bins"),
+])
+def test_bin_edge_validation(lib, edges, needle):
+    """Native binning (Sect. 2.4): qml_fisher rejects bad edges before any
+    device work."""
+    nb, ptr, keep_edges = _bins(edges)
+    p, keep = _problem(nbins=nb, bin_edges=ptr)
+    F = (ctypes.c_double * 64)()
+    assert lib.qml_fisher(ctypes.byref(p), ctypes.cast(F, ctypes.c_void_p), None, None) == nat.QML_EINVAL
+    assert needle in lib.qml_last_error().decode()
+
+
+def test_bin_edges_null_and_negative(lib):
+    F = (ctypes.c_double * 64)()
+    p, keep = _problem(nbins=2, bin_edges=None)
+    assert lib.qml_fisher(ctypes.byref(p), ctypes.cast(F, ctypes.c_void_p), None, None) == nat.QML_EINVAL
+    p, keep = _problem(nbins=-1)
+    assert lib.qml_fisher(ctypes.byref(p), ctypes.cast(F, ctypes.c_void_p), None, None) == nat.QML_EINVAL
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of qml_problem and lnl_mask have the C layout
+    (sizes and field offsets from the header, compiled with gcc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    fields = [f[0] for f in nat.QmlProblem._fields_]
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "qmlgb.h"\nint main(void) {\n'
+                   '  printf("%zu %zu\\n", sizeof(qml_problem), sizeof(lnl_mask));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(qml_problem, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(nat.QmlProblem)
+    assert int(out[1]) == ctypes.sizeof(nat.LnlMask)
+    for f, off in zip(fields, out[2:]):
+        assert int(off) == getattr(nat.QmlProblem, f).offset, f

@@ -247,3 +247,55 @@ def test_synthesize_matches_oracle(api):
     td = lambda x: torch.as_tensor(x, device="cuda").t().contiguous().t()
     out = api.synthesize(prob, td(alm), td(noise))
     assert np.abs(P.to_np(out) - maps).max() <= 1e-12 * np.abs(maps).max()
+
+
+# --------------------------------------------------- native binning -------
+BINNED_CASES = [
+    (0, "full", [2, 5, 8, 11, 14, 17], 0),            # T, l 2..16, Delta l = 3
+    (0, "full", [2, 7, 12, 17], 0),                    # Delta l = 5
+    (1, "small", list(range(2, 17, 2)), 0),            # TQU, l 2..15, Delta l = 2
+    (1, "small", [2, 3, 7, 16], 0),                    # ragged bins
+    (1, "small", list(range(2, 17, 2)), 1),            # split precision
+]
+
+
+@pytest.mark.parametrize("cfg,scale,edges,precision", BINNED_CASES)
+def test_qml_binned_matches_oracle(api, cfg, scale, edges, precision):
+    """Sect. 2.4: with bin edges, F, the noise bias, y and the three
+    normalisations are the binned ones (the oracle forms them from the bin
+    selectors E_b = sum_{l in b} E_l); tolerance 1e-10, split 1e-8."""
+    wl = synth.workload(cfg, scale=scale)
+    tol = P.TOL if precision == 0 else 1e-8
+    Y, alm, noise, maps = P.oracle_maps(wl, 3)
+    ref = qml.qml_for(wl, Y, maps=maps, edges=np.asarray(edges))
+    prob = api.Problem.from_workload(wl, precision=precision, bin_edges=edges)
+    F, plan = api.fisher(prob)
+    nab = len(wl.spec) * (len(edges) - 1)
+    assert tuple(F.shape) == (nab, nab)
+    ge, ee = P.fisher_errors(F, ref["F"])
+    assert ge <= tol and ee <= tol, (ge, ee)
+    md = torch.as_tensor(maps, device="cuda").t().contiguous().t()
+    est = plan.estimate(md)
+    assert P.rel_max(est["b"], ref["b"]) <= tol
+    assert P.rel_max(est["y"], ref["y"]) <= tol
+    assert P.rel_max(est["q_conv"], ref["q"]) <= tol
+    assert P.cl_deconv_error(est["cl_deconv"], ref["cl_deconv"], ref["F"]) <= tol
+    assert P.cl_decorr_error(est["cl_decorr"], ref["cl_decorr"]) <= max(tol, P.decorr_tol(ref["F"]))
+    plan.free()
+
+
+def test_qml_unit_bins_equal_per_l(api):
+    """One multipole per bin is the per-l estimator (the single code path of
+    Sect. 2.4): identical outputs."""
+    wl = synth.workload(0)
+    Y, alm, noise, maps = P.oracle_maps(wl, 2)
+    md = torch.as_tensor(maps, device="cuda").t().contiguous().t()
+    out = []
+    for edges in (None, list(range(wl.lmin, wl.lmax + 2))):
+        F, plan = api.fisher(api.Problem.from_workload(wl, bin_edges=edges))
+        est = plan.estimate(md)
+        out.append((P.to_np(F), {k: P.to_np(v) for k, v in est.items()}))
+        plan.free()
+    assert np.array_equal(out[0][0], out[1][0])
+    for k in out[0][1]:
+        assert np.array_equal(out[0][1][k], out[1][1][k]), k
