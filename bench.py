@@ -409,6 +409,36 @@ def run_ours(args):
             "value": args.steps / tdf, "unit": UNIT, "ms_per_step": 1e3 * tdf / args.steps,
             "note": "64-wide Cholesky diagonal blocks and their row solves in float-float "
                     "(split_diag_df = 1); the default factors them in float64"}
+        # native multipole binning (Sect. 2.4), Delta l = 2: qml_fisher +
+        # qml_estimate (100 maps) with and without bins on the split path
+        try:
+            edges = list(range(wl.lmin, wl.lmax + 2, 2))
+            if edges[-1] != wl.lmax + 1:
+                edges.append(wl.lmax + 1)
+            prob_b = api.Problem.from_workload(wl, device=True, precision=1, bin_edges=edges)
+
+            def fisher_estimate(pr):
+                F, plan = api.fisher(pr)
+                plan.estimate(maps)
+                plan.free()
+            tb = {}
+            for name, pr in (("binned", prob_b), ("per_l", prob_s)):
+                fisher_estimate(pr)
+                torch.cuda.synchronize()
+                e6.record()
+                for _ in range(args.steps):
+                    fisher_estimate(pr)
+                e7.record()
+                e7.synchronize()
+                tb[name] = e6.elapsed_time(e7) / args.steps
+            forms["binned_dl2"] = {
+                "workload": cfg["workload"], "bins_per_spectrum": len(edges) - 1,
+                "ms_fisher_estimate_binned": tb["binned"], "ms_fisher_estimate_per_l": tb["per_l"],
+                "binning_overhead_ms": tb["binned"] - tb["per_l"],
+                "note": "split precision; bins sum the per-l F, noise bias and y "
+                        "(two small kernels) before the three normalisations"}
+        except Exception as ex:  # report, do not lose the rest of the line
+            forms["binned_dl2"] = {"error": f"{type(ex).__name__}: {ex}"}
         # the QU Nside 32 split-precision workload (n = 17152, k = 18424)
         wl3 = synth.workload(2)
         p3s = api.Problem.from_workload(wl3, device=True, precision=1)
