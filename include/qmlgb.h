@@ -130,8 +130,10 @@ qml_status qml_synthesize(const qml_problem *prob, const double *alm, const doub
  * If plan is not NULL, *plan receives a plan holding L, X, F, the noise bias
  * and the normalisation matrices for qml_estimate (the analogue of handing a
  * Fisher object to the spectra stage).  na = nspec (lmax - lmin + 1) must
- * not exceed 2048 (QML_EINVAL).  Errors: QML_ENOTSPD if C is not positive
- * definite. */
+ * not exceed 2048 (QML_EINVAL).  With prob->nbins > 0 (Sect. 2.4) F is the
+ * binned Fisher matrix, na_b x na_b with na_b = nspec nbins, and the plan's
+ * noise bias and normalisations are binned too.  Errors: QML_ENOTSPD if C is
+ * not positive definite; QML_EINVAL for bad bin edges. */
 qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan, void *stream);
 
 /* Quadratic estimates for nsims maps (n x nsims) against a plan from
@@ -140,7 +142,8 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan, void 
  * cl_decorr = F^-1/2 (y - b) with eigenvalues below 1e-12 x max dropped
  * (Eq. decorrelated), q_conv = y - b whose window matrix is F itself
  * (Eq. convolved).  Any output pointer may be NULL to skip it.  nsims = 0
- * (maps may then be NULL) only writes b. */
+ * (maps may then be NULL) only writes b.  For a binned plan every na above
+ * is na_b = nspec nbins: y and b summed over each bin's multipoles. */
 qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims,
                         double *y, double *b, double *cl_deconv, double *cl_decorr,
                         double *q_conv, void *stream);
