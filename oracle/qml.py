@@ -223,6 +223,41 @@ def qml_for(wl, Y, maps=None, want_bias=True, edges=None):
     return qml(Y, wl.cl_fid, wl.comps, wl.lmin, wl.lmax, wl.N(), wl.spec, maps, want_bias, edges)
 
 
+def window_columns(lsig0: int, lsig1: int, lmin: int, lmax: int, nc: int):
+    """Columns of a Y built over [lsig0, lsig1] (nc blocks of modes, l-major)
+    whose multipole lies in the window [lmin, lmax], below it and above it."""
+    k0s = (lsig1 + 1) ** 2 - lsig0 ** 2
+
+    def modes(l0, l1):  # multipoles l0 .. l1 - 1 of every block
+        return np.concatenate([np.arange(c * k0s + l0 * l0 - lsig0 * lsig0,
+                                         c * k0s + l1 * l1 - lsig0 * lsig0) for c in range(nc)])
+    return modes(lmin, lmax + 1), modes(lsig0, lmin), modes(lmax + 1, lsig1 + 1)
+
+
+def switched(Y_sig, cl_fid, comps, lsig, lmin, lmax, N, spec, maps=None, want_bias=True,
+             edges=None):
+    """Multipole switching (Sect. 2.3.4, Eqs. C_switched, N_eff).
+
+    Y_sig spans the signal range lsig = (lmin_sig, lmax_sig); the spectrum is
+    estimated on the inference window [lmin, lmax] only, the fiducial signal
+    of the multipoles on either side is absorbed into
+        N_eff = N + sum_{l in [lmin_sig, lmin) u (lmax, lmax_sig]} C_l^fid P_l
+    (one transfer factor, already in P_l), and N_eff takes the place of N
+    throughout: C = Y_inf Lambda_inf Y_inf^T + N_eff and the noise bias is
+    1/2 tr[C^-1 P_l C^-1 N_eff].
+    """
+    lsig0, lsig1 = lsig
+    win, low, high = window_columns(lsig0, lsig1, lmin, lmax, len(comps))
+    Neff = N.copy()
+    if lmin > lsig0:
+        Neff = Neff + signal_cov(Y_sig[:, low], cl_fid, comps, lsig0, lmin - 1)
+    if lsig1 > lmax:
+        Neff = Neff + signal_cov(Y_sig[:, high], cl_fid, comps, lmax + 1, lsig1)
+    out = qml(Y_sig[:, win], cl_fid, comps, lmin, lmax, Neff, spec, maps, want_bias, edges)
+    out["N_eff"] = Neff
+    return out
+
+
 def bin_matrix(nspec: int, lmin: int, lmax: int, edges) -> np.ndarray:
     """P_Sigma: the 0/1 matrix summing each spectrum's multipoles into its bins
     (nspec nb x nspec nl, spectrum-major), for the identity of Sect. 3 (check

@@ -250,3 +250,82 @@ def test_mutation_bin_range_off_by_one_is_caught(monkeypatch):
     monkeypatch.setattr(qml, "mode_starts", late)
     with pytest.raises(AssertionError):
         test_P10_binning_vs_brute()
+
+
+# ---- P11: multipole switching (Sect. 2.3.4, Eqs. C_switched, N_eff) -------
+def _switch_setup():
+    """Signal over l = 2..7, inference window l = 3..5 (one multipole fixed
+    below it, two above), TQU with all six spectra."""
+    t = _tiny(nside=2, lmax=7)
+    lsig, lmin, lmax = (2, 7), 3, 5
+    rs = qml.switched(t["Y"], t["cl"], t["comps"], lsig, lmin, lmax, t["N"], t["spec"],
+                      maps=t["d"])
+    rf = qml.qml(t["Y"], t["cl"], t["comps"], 2, 7, t["N"], t["spec"], maps=t["d"])
+    nlf = 6
+    win = np.array([s * nlf + l - 2 for s in range(len(t["spec"])) for l in range(lmin, lmax + 1)])
+    out = np.array([s * nlf + l - 2 for s in range(len(t["spec"]))
+                    for l in list(range(2, lmin)) + list(range(lmax + 1, 8))])
+    return t, rs, rf, win, out
+
+
+def test_P11_switching_is_the_window_of_the_full_estimator():
+    """C is the same matrix with or without switching, so F and y on the
+    window equal the window blocks of the full-range estimator, and the noise
+    bias (with N_eff) gains exactly the fixed signal's share:
+    b_sw = b_full[win] + F_full[win, out] C_fid[out]."""
+    t, rs, rf, win, out = _switch_setup()
+    assert np.abs(rs["C"] - rf["C"]).max() <= 1e-13 * np.abs(rf["C"]).max()
+    Ff = rf["F"][np.ix_(win, win)]
+    assert np.abs(rs["F"] - Ff).max() <= 1e-11 * np.abs(Ff).max()
+    assert np.abs(rs["y"] - rf["y"][win]).max() <= 1e-11 * np.abs(rf["y"][win]).max()
+    cfid = np.concatenate([t["cl"][s, 2:8] for s in t["spec"]])
+    bref = rf["b"][win] + rf["F"][np.ix_(win, out)] @ cfid[out]
+    assert np.abs(rs["b"] - bref).max() <= 1e-11 * np.abs(bref).max()
+
+
+def test_P11_switching_expectation_identity():
+    """1/2 tr[C^-1 P_a] = (F C_fid)_a + b_a on the window (P7 with N_eff):
+    exact, because C = sum_{a in window} C_a P_a + N_eff."""
+    t, rs, rf, win, out = _switch_setup()
+    cwin = np.concatenate([t["cl"][s, 3:6] for s in t["spec"]])
+    lhs = 0.5 * qml.trace_selector(rs["W"], t["spec"], t["comps"], 3, 5)
+    assert np.abs(lhs - (rs["F"] @ cwin + rs["b"])).max() <= 1e-10 * np.abs(lhs).max()
+
+
+def test_P11_neff_vs_brute():
+    """N_eff built from the dense pixel derivatives P_l of the brute-force
+    responses (Eq. N_eff term by term), independent of Y."""
+    t, rs, rf, win, out = _switch_setup()
+    Ps = brute.pixel_derivatives(t["th"], t["ph"], t["th"], t["ph"], t["tl"], t["tl"],
+                                 True, True, 2, 7, tuple(range(6)))
+    Neff = t["N"].copy()
+    for s in range(6):
+        for l in (2, 6, 7):
+            Neff = Neff + t["cl"][s, l] * Ps[s * 6 + l - 2]
+    assert np.abs(rs["N_eff"] - Neff).max() <= 1e-12 * np.abs(Neff).max()
+
+
+def test_P11_no_switching_is_plain_qml():
+    """A signal range equal to the window leaves N_eff = N: plain QML (up to
+    the rounding of products over a copied Y)."""
+    t = _tiny(has_P=False)
+    r = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"])
+    rs = qml.switched(t["Y"], t["cl"], t["comps"], (2, t["lmax"]), 2, t["lmax"], t["N"],
+                      t["spec"], maps=t["d"])
+    assert np.array_equal(rs["N_eff"], t["N"])
+    for key in ("F", "b", "y", "cl_deconv"):
+        assert np.abs(rs[key] - r[key]).max() <= 1e-13 * np.abs(r[key]).max(), key
+
+
+def test_mutation_switching_drops_high_side_is_caught(monkeypatch):
+    """Absorbing only the multipoles below the window (a dropped term of
+    Eq. N_eff) breaks the brute-force pin."""
+    orig = qml.signal_cov
+
+    def no_high(Y, cl, comps, lmin, lmax):
+        S = orig(Y, cl, comps, lmin, lmax)
+        return 0.0 * S if lmin == 6 else S  # the term above the window l = 3..5
+
+    monkeypatch.setattr(qml, "signal_cov", no_high)
+    with pytest.raises(AssertionError):
+        test_P11_neff_vs_brute()
