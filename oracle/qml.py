@@ -92,14 +92,16 @@ def _blocksum(H: np.ndarray, lmin: int, lmax: int, edges=None) -> np.ndarray:
     return np.add.reduceat(np.add.reduceat(H, starts, axis=0), starts, axis=1)
 
 
-def fisher_from_W(W: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None) -> np.ndarray:
+def fisher_from_W(W: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None,
+                  W2=None) -> np.ndarray:
     """F_ab = 1/2 tr[W E_a W E_b] (Eqs. fisher_harmonic, sparse_trace); with
     bin edges, a and b run over (spectrum, bin) and E_b is the bin selector
-    (Sect. 2.4)."""
+    (Sect. 2.4); with W2 the cross-QML mixing matrix 1/2 tr[W E_a W2 E_b]."""
     k0 = (lmax + 1) ** 2 - lmin ** 2
     nc = len(comps)
     nl = lmax - lmin + 1 if edges is None else len(edges) - 1
     W4 = W.reshape(nc, k0, nc, k0)
+    V4 = W4 if W2 is None else W2.reshape(nc, k0, nc, k0)
     ci = {c: comps.index(c) for c in comps}
     ns = len(spec)
     F = np.zeros((ns * nl, ns * nl))
@@ -112,7 +114,7 @@ def fisher_from_W(W: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None) 
                     key = (v, up, vp, u)
                     if key not in cache:
                         # H[i, j] = W[v i, u' j] * W[v' j, u i]
-                        H = W4[ci[v], :, ci[up], :] * W4[ci[vp], :, ci[u], :].T
+                        H = W4[ci[v], :, ci[up], :] * V4[ci[vp], :, ci[u], :].T
                         cache[key] = _blocksum(H, lmin, lmax, edges)
                     acc += cache[key]
             F[A * nl:(A + 1) * nl, B * nl:(B + 1) * nl] = 0.5 * acc
@@ -136,10 +138,12 @@ def trace_selector(M: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None)
     return out
 
 
-def quad_selector(w: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None) -> np.ndarray:
+def quad_selector(w: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None,
+                  w2=None) -> np.ndarray:
     """y_a = 1/2 w^T E_a w for each column of w (Eq. q_harmonic); shape (na, nsims);
-    per bin with edges (Sect. 2.4)."""
+    per bin with edges (Sect. 2.4); with w2 the cross form 1/2 w^T E_a w2."""
     w = np.atleast_2d(w.T).T if w.ndim == 1 else w
+    w2 = w if w2 is None else (np.atleast_2d(w2.T).T if w2.ndim == 1 else w2)
     k0 = (lmax + 1) ** 2 - lmin ** 2
     nl = lmax - lmin + 1 if edges is None else len(edges) - 1
     starts = mode_starts(lmin, lmax, edges)
@@ -148,7 +152,7 @@ def quad_selector(w: np.ndarray, spec, comps, lmin: int, lmax: int, edges=None) 
         acc = np.zeros((nl, w.shape[1]))
         for (u, v) in pairs(sa):
             iu, iv = comps.index(u), comps.index(v)
-            prod = w[iu * k0:(iu + 1) * k0] * w[iv * k0:(iv + 1) * k0]
+            prod = w[iu * k0:(iu + 1) * k0] * w2[iv * k0:(iv + 1) * k0]
             acc += np.add.reduceat(prod, starts, axis=0)
         out[A * nl:(A + 1) * nl] = 0.5 * acc
     return out
@@ -221,6 +225,31 @@ def qml(Y, cl_fid, comps, lmin, lmax, N, spec, maps=None, want_bias=True, edges=
 def qml_for(wl, Y, maps=None, want_bias=True, edges=None):
     """qml() for a synthetic workload description."""
     return qml(Y, wl.cl_fid, wl.comps, wl.lmin, wl.lmax, wl.N(), wl.spec, maps, want_bias, edges)
+
+
+def cross_qml(Y, cl_fid, comps, lmin, lmax, N1, N2, spec, d1=None, d2=None):
+    """Cross-QML of two data sets on one pixel set, filtered independently
+    (Eq. q_cross): q_x = 1/2 d1^T C1^-1 P_a C2^-1 d2 with C_i = S + N_i and
+    the mode-mixing matrix W_x = 1/2 tr[C1^-1 P_a C2^-1 P_b]; in the harmonic
+    factorisation (Sect. 2.3.3) with W_i = Y^T C_i^-1 Y, w_i = Y^T C_i^-1 d_i:
+    W_x = 1/2 tr[W1 E_a W2 E_b], q_x = 1/2 w1^T E_a w2.  With independent noise
+    there is no noise bias, and C_x = W_x^-1 q_x."""
+    C1 = total_cov(Y, cl_fid, comps, lmin, lmax, N1)
+    C2 = total_cov(Y, cl_fid, comps, lmin, lmax, N2)
+    f1 = sla.cho_factor(C1, lower=True)
+    f2 = sla.cho_factor(C2, lower=True)
+    W1 = Y.T @ sla.cho_solve(f1, Y)
+    W2 = Y.T @ sla.cho_solve(f2, Y)
+    W1, W2 = 0.5 * (W1 + W1.T), 0.5 * (W2 + W2.T)
+    out = {"Wx": fisher_from_W(W1, spec, comps, lmin, lmax, W2=W2), "C1": C1, "C2": C2}
+    if d1 is not None:
+        d1 = d1.reshape(d1.shape[0], -1)
+        d2 = d2.reshape(d2.shape[0], -1)
+        w1 = Y.T @ sla.cho_solve(f1, d1)
+        w2 = Y.T @ sla.cho_solve(f2, d2)
+        out["q"] = quad_selector(w1, spec, comps, lmin, lmax, w2=w2)
+        out["cl_deconv"] = np.linalg.solve(out["Wx"], out["q"])
+    return out
 
 
 def window_columns(lsig0: int, lsig1: int, lmin: int, lmax: int, nc: int):

@@ -329,3 +329,73 @@ def test_mutation_switching_drops_high_side_is_caught(monkeypatch):
     monkeypatch.setattr(qml, "signal_cov", no_high)
     with pytest.raises(AssertionError):
         test_P11_neff_vs_brute()
+
+
+# ---- P16: cross-QML (Eq. q_cross) -----------------------------------------
+def _cross_setup():
+    t = _tiny()
+    g = np.random.default_rng(21)
+    n = t["Y"].shape[0]
+    G2 = g.normal(size=(n, 4)) * 0.4
+    N2 = G2 @ G2.T + 1.5 * np.eye(n)
+    d2 = g.normal(size=(n, 3))
+    return t, N2, d2
+
+
+def test_P16_cross_reduces_to_auto():
+    """Equal noise and equal maps: W_x is the Fisher matrix and q_x the
+    bias-free auto estimate y."""
+    t = _tiny()
+    r = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"])
+    x = qml.cross_qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["N"], t["spec"],
+                      t["d"], t["d"])
+    assert np.abs(x["Wx"] - r["F"]).max() <= 1e-13 * np.abs(r["F"]).max()
+    assert np.abs(x["q"] - r["y"]).max() <= 1e-13 * np.abs(r["y"]).max()
+
+
+def test_P16_cross_vs_brute():
+    """W_x and q_x against dense pixel traces with the brute-force P_a."""
+    t, N2, d2 = _cross_setup()
+    x = qml.cross_qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], N2, t["spec"],
+                      t["d"], d2)
+    Ps = brute.pixel_derivatives(t["th"], t["ph"], t["th"], t["ph"], t["tl"], t["tl"],
+                                 True, True, 2, t["lmax"], t["spec"])
+    S = brute.signal_from_derivatives(Ps, t["cl"], t["spec"], 2, t["lmax"])
+    C1i, C2i = np.linalg.inv(S + t["N"]), np.linalg.inv(S + N2)  # built here, not by the oracle
+    na = len(Ps)
+    Wx = np.array([[0.5 * np.trace(C1i @ Ps[a] @ C2i @ Ps[b]) for b in range(na)]
+                   for a in range(na)])
+    q = np.array([0.5 * np.sum((C1i @ t["d"]) * (Ps[a] @ (C2i @ d2)), axis=0) for a in range(na)])
+    assert np.abs(x["Wx"] - Wx).max() <= 1e-12 * np.abs(Wx).max()
+    assert np.abs(x["q"] - q).max() <= 1e-12 * np.abs(q).max()
+
+
+def test_P16_cross_is_unbiased_exactly():
+    """With independent noise the cross-covariance of the two maps is S, so
+    <q_x> = 1/2 tr[C1^-1 P_a C2^-1 S] = W_x C_fid exactly (no noise bias)."""
+    t, N2, d2 = _cross_setup()
+    x = qml.cross_qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], N2, t["spec"])
+    Ps = brute.pixel_derivatives(t["th"], t["ph"], t["th"], t["ph"], t["tl"], t["tl"],
+                                 True, True, 2, t["lmax"], tuple(range(6)))
+    S = brute.signal_from_derivatives(Ps, t["cl"], tuple(range(6)), 2, t["lmax"])
+    C1i, C2i = np.linalg.inv(x["C1"]), np.linalg.inv(x["C2"])
+    nl = t["lmax"] - 1
+    mean = np.array([0.5 * np.trace(C1i @ Ps[s * nl + l] @ C2i @ S)
+                     for s in t["spec"] for l in range(nl)])
+    cfid = np.concatenate([t["cl"][s, 2:t["lmax"] + 1] for s in t["spec"]])
+    assert np.abs(mean - x["Wx"] @ cfid).max() <= 1e-11 * np.abs(mean).max()
+
+
+def test_mutation_cross_filters_both_with_C1_is_caught(monkeypatch):
+    """Filtering the second map with C1 (the two-filter structure lost) breaks
+    the brute-force cross pin."""
+    orig = qml.total_cov
+    first = {}
+
+    def same(Y, cl, comps, lmin, lmax, N):
+        first.setdefault("N", N)
+        return orig(Y, cl, comps, lmin, lmax, first["N"])
+
+    monkeypatch.setattr(qml, "total_cov", same)
+    with pytest.raises(AssertionError):
+        test_P16_cross_vs_brute()
