@@ -658,9 +658,8 @@ void forward(qml_emu *e, int h, Acts &A, cudaStream_t st) {
 // the first layer's 16 inputs and weights widened with zeros to 64) runs as
 // mlp_tc_kernel with bias and activation fused.  Tuning key emu_tc = 0
 // selects the WMMA path for every layer, emu_tc0 = 0 for the first one.
-bool use_tc(const qml_emu *e) {
-  return tune_get("emu_tc", 1) != 0 && e->width % 64 == 0 && e->width <= 256;
-}
+bool tc_capable(const qml_emu *e) { return e->width % 64 == 0 && e->width <= 256; }
+bool use_tc(const qml_emu *e) { return tune_get("emu_tc", 1) != 0 && tc_capable(e); }
 
 // tensor maps of every layer l >= 1: its input activations (rows x in) and
 // head h's weights (out x in)
@@ -805,7 +804,8 @@ PredCache *pred_cache(qml_emu *e, int rows) {
     delete c;
     return nullptr;
   }
-  c->tc = use_tc(e) && make_tc_maps(e, 0, c->A0, rows, c->mx0, c->mw0) &&
+  // the tensor maps are made whenever the width allows; emu_tc is read per call
+  c->tc = tc_capable(e) && make_tc_maps(e, 0, c->A0, rows, c->mx0, c->mw0) &&
           make_tc_maps(e, 1, c->A1, rows, c->mx1, c->mw1);
   if (c->tc) {
     const int w0 = e->layers[0].first;
