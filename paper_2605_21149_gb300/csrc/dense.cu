@@ -953,9 +953,11 @@ bool dgemm_autotune(int ta, int tb, int64_t M, int64_t N, int64_t K, const doubl
 // them safe: C == A (C's rows read only by their own CTA) needs the whole of
 // N in one tile, C == B the whole of M; callers only alias with N (resp. M)
 // <= 64, and those shapes are never timed.
-void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
-                  const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
-                  double *C, int64_t ldc, int lower, const DevStatus *status, cudaStream_t st) {
+namespace {
+void launch_dgemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                       const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                       double *C, int64_t ldc, int lower, const DevStatus *status,
+                       cudaStream_t st, bool may_tune) {
   if (M <= 0 || N <= 0) return;
   const bool aliasA = (C == A), aliasB = (C == B);
   const std::string key = "dgemm:" + std::to_string(ta) + "," + std::to_string(tb) + "," +
@@ -972,7 +974,8 @@ void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                    C, ldc, lower, status, st);
     return;
   }
-  if (!aliasA && !aliasB && M * N <= (1 << 24) && K <= 4096 && tune_get("dgemm_autotune", 1)) {
+  if (may_tune && !aliasA && !aliasB && M * N <= (1 << 24) && K <= 4096 &&
+      tune_get("dgemm_autotune", 1)) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       int rm = 4, rn = 4;
@@ -1006,6 +1009,20 @@ void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
     }
   }
   dgemm_dispatch(ta, tb, rm, rn, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st);
+}
+}  // namespace
+
+void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                  const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                  double *C, int64_t ldc, int lower, const DevStatus *status, cudaStream_t st) {
+  launch_dgemm_impl(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, true);
+}
+
+void launch_dgemm_fixed(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                        double *C, int64_t ldc, int lower, const DevStatus *status,
+                        cudaStream_t st) {
+  launch_dgemm_impl(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, status, st, false);
 }
 
 // count products C_z <- alpha op(A_z) op(B_z) + beta C_z, X_z = X + z sX; the

@@ -53,6 +53,13 @@ void launch_mix_lambda(double *Y, int64_t ldy, int n, int nc, int k0, int lmin, 
 void launch_dgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                   double *C, int64_t ldc, int lower, const DevStatus *status, cudaStream_t st);
+// launch_dgemm without the autotuner: a measured tuning-table entry for the
+// shape when one exists, else the heuristic tile.  Never allocates, creates
+// events or synchronises (for callers that may not).
+void launch_dgemm_fixed(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                        double *C, int64_t ldc, int lower, const DevStatus *status,
+                        cudaStream_t st);
 // strided batch: product z uses A + z sA, B + z sB, C + z sC (no aliasing)
 void launch_dgemm_batched(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                           const double *A, int64_t lda, int64_t sA, const double *B,

@@ -6,7 +6,10 @@
 // pre-allocated buffers and forbids it from allocating), and hot loops where
 // the implicit device synchronisation of cudaMalloc / cudaFree, or a call into
 // another allocator, is not acceptable.  This entry point calls no
-// cudaMalloc, cudaMallocAsync, cudaFree or allocating library routine.
+// cudaMalloc, cudaMallocAsync, cudaFree or allocating library routine, and it
+// never runs the float64 GEMM tile autotuner (which allocates a timing buffer
+// and synchronises): each product takes the tuning table's measured tile for
+// its shape when one is there, else the heuristic tile.
 //
 // Its scratch (the inverses of the 64 x 64 diagonal blocks, the per-block
 // log-determinants and the status word) lives in the file-scope array below,
@@ -21,7 +24,8 @@
 // it names a host-side shadow); the device address comes from
 // cudaGetSymbolAddress, taken once per device with that device current, on
 // the first call on that device.  That first call should therefore come
-// before any stream capture the caller performs.
+// before any stream capture the caller performs.  Every call reads the status
+// word back and synchronises `stream` before it returns.
 #include "qmlgb.h"
 #include "internal.cuh"
 
@@ -120,8 +124,9 @@ extern "C" qml_status qml_potrf_noalloc(int64_t n, double *A, int64_t lda, doubl
       const int64_t m2 = n - j - jb;
       double *A21 = A + (j + jb) + j * lda;
       double *A22 = A + (j + jb) + (j + jb) * lda;
-      launch_dgemm(0, 1, m2, jb, jb, 1.0, A21, lda, Lb, kNB, 0.0, A21, lda, 0, status, st);
-      launch_dgemm(0, 1, m2, m2, jb, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1, status, st);
+      // never the tile autotuner: it allocates a timing buffer and synchronises
+      launch_dgemm_fixed(0, 1, m2, jb, jb, 1.0, A21, lda, Lb, kNB, 0.0, A21, lda, 0, status, st);
+      launch_dgemm_fixed(0, 1, m2, m2, jb, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1, status, st);
     }
   }
   if (logdet) launch_sum_logdet(ldparts, (int)((n + kNB - 1) / kNB), logdet, st);

@@ -3,10 +3,14 @@
 qml_potrf_noalloc serves callers that cannot allocate device memory (a host
 runtime that owns all GPU memory and only hands out pre-allocated buffers, or
 hot loops that cannot pay for cudaMalloc's device synchronisation); it keeps
-its scratch in a static device array shared by every call.  Two calls in a
-row (different sizes, so the second runs on the first one's leftover scratch)
-must reproduce qml_potrf on the same matrices.  This file is collected last
-so that a run stopping at the first failure has already run every other test.
+its scratch in a static device array shared by every call.  The first test
+calls it on shapes no other test uses, before anything else has run them, and
+checks that it left no trace of the float64 tile autotuner (which allocates):
+no new "dgemm:" entry in the tuning table and no less free device memory.
+Two calls in a row (different sizes, so the second runs on the first one's
+leftover scratch) must reproduce qml_potrf on the same matrices.  This file is
+collected last so that a run stopping at the first failure has already run
+every other test.
 """
 import ctypes
 
@@ -40,21 +44,45 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _dgemm_entries(lib):
+    need = lib.qml_tune_table(None, 0)
+    buf = ctypes.create_string_buffer(int(need) + 1)
+    lib.qml_tune_table(buf, len(buf))
+    return {ln.split()[0] for ln in buf.value.decode().splitlines() if ln.startswith("dgemm:")}
+
+
+def _check_pair(lib, n, seed, before_ref=None):
+    A = _spd(n, seed)
+    out = _colmajor_dev(A)
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    tuned0 = _dgemm_entries(lib)
+    free0 = torch.cuda.mem_get_info()[0]
+    st = lib.qml_potrf_noalloc(n, out.data_ptr(), n, ld.data_ptr(), _stream())
+    assert st == 0, lib.qml_last_error()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert _dgemm_entries(lib) == tuned0, "qml_potrf_noalloc ran the allocating tile autotuner"
+    assert free1 >= free0, (free0, free1)
+    ref = _colmajor_dev(A)
+    ld_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = lib.qml_potrf(n, ref.data_ptr(), n, ld_ref.data_ptr(), 0, _stream())
+    assert st == 0, lib.qml_last_error()
+    L, Lr = torch.tril(out).cpu().numpy(), torch.tril(ref).cpu().numpy()
+    assert np.abs(L - Lr).max() <= 1e-12 * np.abs(Lr).max(), n
+    assert abs(ld.item() - ld_ref.item()) <= 1e-12 * abs(ld_ref.item())
+
+
+def test_noalloc_first_on_unseen_shapes(lib):
+    """Shapes no other test factors (ragged tails of 59 and 55 columns), run
+    through qml_potrf_noalloc before qml_potrf has tuned them."""
+    for n in (1531, 2999):
+        _check_pair(lib, n, 7000 + n)
+
+
 @pytest.mark.parametrize("sizes", [(1000, 257), (4096, 65)])
 def test_noalloc_matches_potrf_two_calls(lib, sizes):
-    for i, n in enumerate(sizes):
-        A = _spd(n, 100 + n)
-        ref = _colmajor_dev(A)
-        ld_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
-        st = lib.qml_potrf(n, ref.data_ptr(), n, ld_ref.data_ptr(), 0, _stream())
-        assert st == 0, lib.qml_last_error()
-        out = _colmajor_dev(A)
-        ld = torch.zeros(1, dtype=torch.float64, device="cuda")
-        st = lib.qml_potrf_noalloc(n, out.data_ptr(), n, ld.data_ptr(), _stream())
-        assert st == 0, lib.qml_last_error()
-        L, Lr = torch.tril(out).cpu().numpy(), torch.tril(ref).cpu().numpy()
-        assert np.abs(L - Lr).max() <= 1e-12 * np.abs(Lr).max(), (i, n)
-        assert abs(ld.item() - ld_ref.item()) <= 1e-12 * abs(ld_ref.item())
+    for n in sizes:
+        _check_pair(lib, n, 100 + n)
 
 
 def test_noalloc_rejects_oversize_and_host(lib):
