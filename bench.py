@@ -30,8 +30,8 @@ METRIC = "Fisher+Cl solves/s (TQU Nside16 l2-47, 100 sims)"
 # at this workload, from one ncu capture of that kernel (set to None when the
 # kernel changes until it is captured again)
 DGEMM_SYRK_TRAFFIC = 8.550515e9 + 0.187149e9
-DGEMM_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                             "profiles/dgemm_syrk_tqu_nside16_fp64.md")
+DGEMM_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                             "--set full capture of this launch")
 UNIT = "solves/s"
 
 

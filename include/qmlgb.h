@@ -178,7 +178,8 @@ typedef struct {
  * spectra item_cl + i*6*(lmax+1).  Outputs (row-major per item, leading
  * dimension ld_out >= the largest nmaps): lnL[i*ld_out + j], chi2[...] and
  * logdet[i]; any may be NULL.  The per-mask part (Cholesky of N, M, Y^T N^-1 d)
- * runs once; items run on four internal streams.  Errors: QML_EINVAL,
+ * runs once; items are spread round-robin over internal worker streams
+ * (tuning key batch_streams, default 4).  Errors: QML_EINVAL,
  * QML_ENOTSPD (N not positive definite), QML_ETIMEOUT. */
 qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitems,
                              const int32_t *item_mask, const double *item_cl, int32_t ld_out,

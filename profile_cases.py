@@ -1,12 +1,12 @@
 """Single-call cases for profiler captures (ncu), on the TQU Nside 16 workload.
 
-    python -m paper_2605_21149_gb300.profile_cases syrk     # W = X^T X, k=6900, n=5952
-    python -m paper_2605_21149_gb300.profile_cases syrk_split  # the same, split precision
-    python -m paper_2605_21149_gb300.profile_cases trail_split
+    python profile_cases.py syrk     # W = X^T X, k=6900, n=5952
+    python profile_cases.py syrk_split  # the same, split precision
+    python profile_cases.py trail_split
         # split Cholesky trailing update: C (6400 x 6400, lower) -= P P^T, K = 512
-    python -m paper_2605_21149_gb300.profile_cases ybuild   # Y, 5952 x 6900
-    python -m paper_2605_21149_gb300.profile_cases fisher   # one full qml_fisher
-    python -m paper_2605_21149_gb300.profile_cases step --precision 1
+    python profile_cases.py ybuild   # Y, 5952 x 6900
+    python profile_cases.py fisher   # one full qml_fisher
+    python profile_cases.py step --precision 1
         # one bench step: qml_fisher + qml_estimate (100 maps) + pix_loglike
 
 Each case runs its call `--reps` times (default 2) after one untimed call and
@@ -15,12 +15,16 @@ prints the CUDA-event time per call.
 from __future__ import annotations
 
 import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():
     import torch
 
-    from . import api, build, synth
+    from paper_2605_21149_gb300 import api, build, synth
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=("syrk", "syrk_split", "trail_split", "ybuild", "fisher", "step"))
