@@ -174,7 +174,10 @@ typedef struct {
  * Kt = I + L^T M L with M = Y^T N^-1 Y and Lambda(theta) = L L^T per (l, m),
  * App. C.3): ln|C| = ln|N| + ln|Kt|, d^T C^-1 d = d^T N^-1 d - |Lk^-1 L^T Y^T
  * N^-1 d|^2.  masks: HOST array of nmask descriptors (same fields and
- * multipole band).  Item i uses mask item_mask[i] (host or device, nitems) and
+ * multipole band).  With QML_SPLIT_BF16 masks the per-mask products are split
+ * precision and each item's Kt is factored in float64 (tuning key
+ * batch_split_kt = 1: split trailing updates for Kt as well).
+ * Item i uses mask item_mask[i] (host or device, nitems) and
  * spectra item_cl + i*6*(lmax+1).  Outputs (row-major per item, leading
  * dimension ld_out >= the largest nmaps): lnL[i*ld_out + j], chi2[...] and
  * logdet[i]; any may be NULL.  The per-mask part (Cholesky of N, M, Y^T N^-1 d)
@@ -231,6 +234,13 @@ qml_status emu_threshold(const qml_emu *emu, double tol, double *thr, int32_t *n
  * layout: per layer W (out x in, row-major) then b, inputs padded to 16). */
 int64_t emu_param_count(const qml_emu *emu);
 qml_status emu_params(qml_emu *emu, int32_t head, float *out);
+/* The float64 baseline polynomial and residual scale of a trained emulator
+ * (host outputs): lnL = q(x) + sigma (f_0(x) + f_1(x)) / 2 with q(x) =
+ * sum_k coef[k] phi_k(x), the features phi in the order 1, x_i, x_i x_j
+ * (i <= j), x_i x_j x_l (i <= j <= l, cubic part only for d <= 5); coef holds
+ * at least 56 doubles, *nfeat receives the count used.  Exposes the model so
+ * that its inference can be checked term by term. */
+qml_status emu_baseline(const qml_emu *emu, double *coef, int32_t *nfeat, double *sigma);
 /* Mean squared error of head `head` on n given normalised inputs (host, n x 16
  * row-major) and targets (host, n), and its gradient (float32, host or
  * device) -- exposes the training kernels for testing. */
@@ -292,6 +302,14 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *   split_diag_df   0 (default) / 1: the split-precision Cholesky factors
  *                   its 64-wide diagonal blocks and their row solves in
  *                   float64 / in float-float (about 2^-46 per operation)
+ *   batch_split_kt  0 (default) / 1: with QML_SPLIT_BF16 masks,
+ *                   pix_loglike_batch factors each item's inner matrix Kt in
+ *                   native float64 / with split-precision trailing updates
+ *                   and panel products (float64 diagonal blocks and ln|Kt|)
+ *   test_wait_timeout  0 (default) / 1: for testing the failure path only:
+ *                   the split-precision product issues no copies and its
+ *                   waits give up after 1 ms, so the call returns
+ *                   QML_ETIMEOUT (no fault; the context stays usable)
  * qml_tune_set / qml_tune_get: one entry (key without white space; get
  * returns QML_EINVAL when absent).  qml_tune_table writes the table as text,
  * one "key value" line per entry, into buf (capacity cap bytes, NUL

@@ -11,8 +11,12 @@ Parameter layout (shared interface with the library): for each layer l in
 order, W_l (out_l x in_l, row-major) then b_l (out_l).  The library stores
 weights in bf16 for its tensor-core products and rounds each layer's input
 activations to bf16; `forward(..., bf16_inputs=True)` reproduces those two
-roundings so that its outputs and gradients are comparable.  Everything else
-is float64.
+roundings so that its outputs and gradients are comparable.  In training the
+library also rounds the back-propagated errors dL/dz to bf16 where they enter
+a tensor-core product (the weight gradient dz^T a and the error of the layer
+below, dz W), while the bias gradient sums the unrounded dz;
+`loss_and_grad(..., bf16_grads=True)` reproduces that rounding too.
+Everything else is float64.
 """
 from __future__ import annotations
 
@@ -70,7 +74,7 @@ def forward(params, X, in0, width, depth, out0, bf16_inputs=False):
     return a[:, 0], cache
 
 
-def loss_and_grad(params, X, t, in0, width, depth, out0, bf16_inputs=False):
+def loss_and_grad(params, X, t, in0, width, depth, out0, bf16_inputs=False, bf16_grads=False):
     """MSE of the first output and its gradient w.r.t. params (float64)."""
     layers = unpack(params, in0, width, depth, out0)
     pred, cache = forward(params, X, in0, width, depth, out0, bf16_inputs)
@@ -85,11 +89,12 @@ def loss_and_grad(params, X, t, in0, width, depth, out0, bf16_inputs=False):
         au, z = cache[li]
         if li < len(layers) - 1:
             dz = dz * dgelu(z)
-        gW = dz.T @ au
+        dzu = bf16_round(dz) if bf16_grads else dz
+        gW = dzu.T @ au
         gb = dz.sum(axis=0)
         grads.append((gW, gb))
         Wu = bf16_round(W) if bf16_inputs else W
-        dz = dz @ Wu
+        dz = dzu @ Wu
     grads.reverse()
     flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     return loss, flat

@@ -67,6 +67,7 @@ SIGNATURES = {
     "qml_tune_load": (c_int32, [c_char_p]),
     "emu_threshold": (c_int32, [c_void_p, c_double, c_void_p, c_void_p]),
     "emu_params": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "emu_baseline": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "emu_loss_grad": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "emu_free": (None, [c_void_p]),
     "qml_potrf": (c_int32, [c_int64, c_void_p, c_int64, c_void_p, c_int32, c_void_p]),

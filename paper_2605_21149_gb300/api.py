@@ -376,6 +376,15 @@ class Emulator:
         _check(_lib().emu_params(self._h, head, out.ctypes.data))
         return out
 
+    def baseline(self):
+        """(coef, sigma): the float64 baseline polynomial's coefficients (feature
+        order of emu_baseline) and the residual scale of the network term."""
+        coef = np.zeros(64, dtype=np.float64)
+        nf = ctypes.c_int32(0)
+        sig = ctypes.c_double(0.0)
+        _check(_lib().emu_baseline(self._h, coef.ctypes.data, ctypes.byref(nf), ctypes.byref(sig)))
+        return coef[:nf.value].copy(), sig.value
+
     def loss_grad(self, x, t, head=0):
         """(loss, grad) of one head on normalised inputs x (n x 16) and targets t."""
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -881,8 +881,14 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
   // sequence once -- reading the spectrum from a fixed per-worker slot and
   // writing its results to fixed slots -- and replays it for every later item
   bool graphs = tune_get("batch_graphs", 1) != 0 && nitems > NS;
+  // Split precision covers the per-mask products (L_N, U = L_N^-1 Y, M, v);
+  // the per-item inner factor Kt (the SMW inner inverse and ln|Kt|) stays in
+  // native float64 unless the tuning key batch_split_kt asks for its trailing
+  // updates and panel products in split precision too.
+  const bool split_kt = tune_get("batch_split_kt", 0) != 0;
   bool any_split = false;
-  for (int m = 0; m < nmask; ++m) any_split |= (masks[m].prob.precision == QML_SPLIT_BF16);
+  for (int m = 0; m < nmask; ++m)
+    any_split |= (split_kt && masks[m].prob.precision == QML_SPLIT_BF16);
   struct Worker {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
@@ -944,7 +950,7 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
     launch_lambda_factor(cl, d0.lmin, d0.lmax, d0.nc, d0.comps, W.lamL, W.st);
     launch_form_ktilde(ms[m].M, k, d0.nc, d0.k0, d0.lmin, W.lamL, W.K, k, W.st);
     launch_lambda_t_apply(ms[m].v, k, d0.nc, d0.k0, d0.lmin, W.lamL, nm, W.z, k, W.st);
-    if (masks[m].prob.precision == QML_SPLIT_BF16) {
+    if (split_kt && masks[m].prob.precision == QML_SPLIT_BF16) {
       Split spl{&cw, masks[m].prob.nslices};
       spl.preset(W.ws, W.ws_bytes);
       spl.tinv = W.tinv;

@@ -1221,6 +1221,17 @@ qml_status emu_params(qml_emu *e, int32_t head, float *out) {
   return QML_OK;
 }
 
+qml_status emu_baseline(const qml_emu *e, double *coef, int32_t *nfeat_out, double *sigma) {
+  if (!e || !coef || !nfeat_out || !sigma) return efail(QML_EINVAL, "emu_baseline: bad arguments");
+  const int nf = nfeat(e->d);
+  cudaDeviceSynchronize();
+  if (cudaMemcpy(coef, e->coef, nf * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(sigma, e->sigma, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return efail(QML_ECUDA, "emu_baseline: copy failed");
+  *nfeat_out = nf;
+  return QML_OK;
+}
+
 qml_status emu_loss_grad(qml_emu *e, int32_t head, int32_t n, const double *x, const double *t,
                          double *loss, float *grad) {
   if (!e || head < 0 || head > 1 || n < 1 || !x || !t || !loss || !grad)

@@ -80,6 +80,11 @@ struct OzParams {
   int64_t ldc;
   const int *ea, *eb;
   DevStatus *status;
+  // failure-path test (tuning key test_wait_timeout): the producer issues no
+  // copies and every wait gives up after wait_ns, so each CTA takes its
+  // timeout exit; normal calls have wait_ns = kWaitNs and no_loads = 0
+  uint64_t wait_ns;
+  int no_loads;
 };
 
 // acc 2^E as a float64, sign flipped when neg: one int64 -> float64
@@ -165,14 +170,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int last_phase[OSTAGES];
       for (int q = 0; q < OSTAGES; ++q) last_phase[q] = -1;
-      bool ok = (*((volatile int *)&st->code) == 0);
+      bool ok = (*((volatile int *)&st->code) == 0) && !p.no_loads;
       for (int L = 2; L <= S + 1 && ok; ++L) {
         for (int c = 0; c < nchunks && ok; ++c) {
           const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
           for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
             const int t = L - s;
             for (int ks = k0; ks < k1 && ok; ++ks) {
-              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st)) { ok = false; break; }
+              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st, p.wait_ns)) { ok = false; break; }
               mbar_expect_tx(full0 + 8 * stage, 2 * kTileBytes);
               tma_load_2d(smem_u32(tilesA + stage * kTileBytes), &tmA, full0 + 8 * stage, ks * OBK,
                           (s - 1) * p.Mpad + m0);
@@ -204,7 +209,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < nchunks && ok; ++c) {
           const uint32_t b = q & 1;
           // the epilogue must have read this buffer's previous chunk
-          if (q >= 2 && !mbar_wait(acce0 + 8 * b, ((q >> 1) - 1) & 1, st)) { ok = false; break; }
+          if (q >= 2 && !mbar_wait(acce0 + 8 * b, ((q >> 1) - 1) & 1, st, p.wait_ns)) {
+            ok = false;
+            break;
+          }
           tc_fence_after();
           const uint32_t dacc = tbase + 128 * b;
           const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
@@ -212,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // every digit pair of this level adds into the same accumulator
           for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
             for (int ks = k0; ks < k1; ++ks) {
-              if (!mbar_wait(full0 + 8 * stage, phase, st)) { ok = false; break; }
+              if (!mbar_wait(full0 + 8 * stage, phase, st, p.wait_ns)) { ok = false; break; }
               tc_fence_after();
               const uint32_t a_addr = smem_u32(tilesA + stage * kTileBytes);
               const uint32_t b_addr = smem_u32(tilesB + stage * kTileBytes);
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < nchunks; ++c) {
           const uint32_t b = q & 1;
           int okw = 1;
-          if (lane == 0) okw = mbar_wait(accf0 + 8 * b, (q >> 1) & 1, st) ? 1 : 0;
+          if (lane == 0) okw = mbar_wait(accf0 + 8 * b, (q >> 1) & 1, st, p.wait_ns) ? 1 : 0;
           okw = __shfl_sync(0xffffffffu, okw, 0);
           __syncwarp();
           if (!okw) { ok = false; break; }
@@ -652,6 +660,8 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.ea = ea;
   p.eb = eb;
   p.status = status;
+  p.no_loads = tune_get("test_wait_timeout", 0) != 0 ? 1 : 0;
+  p.wait_ns = p.no_loads ? 1000000ull : kWaitNs;  // 1 ms in the failure-path test
   const int tiles_m = (int)(Mpad / OBM);
   int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
   // ring depth: 6 stages by default (the tuning table may pick 4)

@@ -39,15 +39,16 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s budget per wait
 
-// bounded wait; false (and the status word set) when the time budget runs out
-// or another role already failed
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevStatus *st) {
+// bounded wait; false (and the status word set) when the time budget (ns)
+// runs out or another role already failed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevStatus *st,
+                                          uint64_t budget_ns = kWaitNs) {
   const uint64_t t0 = global_ns();
   for (unsigned i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63) == 63) {
       if (*((volatile int *)&st->code) != 0) return false;
-      if (global_ns() - t0 > kWaitNs) break;
+      if (global_ns() - t0 > budget_ns) break;
     }
   }
   atomicCAS(&st->code, 0, 5 /* QML_ETIMEOUT */);

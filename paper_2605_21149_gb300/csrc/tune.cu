@@ -18,6 +18,11 @@
 //                    64-wide diagonal blocks and their row solves in float64;
 //                    1: in float-float (pairs of float32, about 2^-46 per
 //                    operation; faster on this part's narrow float64 pipe)
+//   batch_split_kt   0 (default): with split-precision masks the per-item
+//                    inner factor Kt of pix_loglike_batch is native float64;
+//                    1: its trailing updates and panel products are split
+//   test_wait_timeout  1: failure-path test; the split-precision kernel
+//                    issues no copies and gives up each wait after 1 ms
 //   batch_graphs     1 (default): pix_loglike_batch captures each worker's
 //                    per-item sequence once per mask as a CUDA graph and
 //                    replays it; 0: plain launches

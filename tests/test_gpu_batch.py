@@ -67,6 +67,49 @@ def test_batch_small(api, precision, tol):
     _run(api, 8, 15, 9, precision, tol)
 
 
+def _with_split_kt(api, fn):
+    api.tune_set("batch_split_kt", 1)
+    try:
+        fn()
+    finally:
+        api.tune_set("batch_split_kt", 0)
+
+
+def test_batch_split_kt_64_items_nside8(api):
+    """The opt-in split-precision inner factor (batch_split_kt = 1: Kt's
+    trailing updates and panel products as split products, k = 756 > 512 so
+    two panels) on 64 items over the three masks, against the oracle's pixel
+    lnL at the split tolerance."""
+    _with_split_kt(api, lambda: _run(api, 8, 15, 64, 1, 1e-8))
+
+
+def test_batch_split_kt_grid_corners_nside16(api):
+    """Split Kt at TQU Nside 16 (k = 6900) on the f_sky 0.5 mask, 64 items of
+    the 64 x 64 (tau, r) grid including its four corners (tau = 0.03, 0.09 and
+    r = 0, 0.1), every item against the oracle's pixel lnL within 1e-8."""
+    masks, taus, rs = synth.batch_workload(nside=16, lmax=47, rank=30, ngrid=64)
+    wl = masks[0]
+    corners = [0, 63, 64 * 63, 64 * 64 - 1]
+    rest = np.linspace(1, 64 * 64 - 2, 60).astype(int)
+    sel = np.array(corners + list(rest))
+    item_cl = synth.batch_item_spectra(47, taus[sel], rs[sel])
+    Y, alm, noise, maps = P.oracle_maps(wl, 1, seed_purpose=20)
+    refs = [qml.loglike(qml.total_cov(Y, item_cl[i], wl.comps, wl.lmin, wl.lmax, wl.N()), maps)
+            for i in range(len(sel))]
+    del Y
+
+    def run():
+        prob = api.Problem.from_workload(wl, precision=1)
+        lnl, chi2, ld = api.loglike_batch([(prob, td(maps))], np.zeros(len(sel), dtype=np.int32),
+                                          torch.as_tensor(item_cl, device="cuda"))
+        lnl, chi2, ld = P.to_np(lnl), P.to_np(chi2), P.to_np(ld)
+        for i, (rl, rc, rd) in enumerate(refs):
+            assert abs(lnl[i, 0] - rl[0]) <= 1e-8 * abs(rl[0]), (i, taus[sel[i]], rs[sel[i]])
+            assert abs(chi2[i, 0] - rc[0]) <= 1e-8 * abs(rc[0]), i
+            assert abs(ld[i] - rd) <= 1e-8 * abs(rd), i
+    _with_split_kt(api, run)
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-8)])
 def test_batch_tqu_nside16(api, precision, tol):
     """Nside 16 TQU, l <= 47 (k = 6900), masks f_sky 0.5 / 0.7 / 0.9
