@@ -6,9 +6,10 @@ hot loops that cannot pay for cudaMalloc's device synchronisation); it keeps
 its scratch in a static device array shared by every call.  The first test
 calls it on shapes no other test uses, before anything else has run them, and
 checks that it left no trace of the float64 tile autotuner (which allocates):
-no new "dgemm:" entry in the tuning table and no less free device memory.
-Two calls in a row (different sizes, so the second runs on the first one's
-leftover scratch) must reproduce qml_potrf on the same matrices.  This file is
+no new "dgemm:" entry in the tuning table, and no less free device memory
+across a repeated call once CUDA has loaded the kernels' modules.  Calls in a
+row (different sizes, so later ones run on leftover scratch) must reproduce
+qml_potrf on the same matrices.  This file is
 collected last so that a run stopping at the first failure has already run
 every other test.
 """
@@ -51,25 +52,44 @@ def _dgemm_entries(lib):
     return {ln.split()[0] for ln in buf.value.decode().splitlines() if ln.startswith("dgemm:")}
 
 
-def _check_pair(lib, n, seed, before_ref=None):
-    A = _spd(n, seed)
+def _noalloc(lib, A):
     out = _colmajor_dev(A)
     ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = lib.qml_potrf_noalloc(A.shape[0], out.data_ptr(), A.shape[0], ld.data_ptr(), _stream())
+    assert st == 0, lib.qml_last_error()
+    return out, ld
+
+
+def _potrf(lib, A):
+    ref = _colmajor_dev(A)
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = lib.qml_potrf(A.shape[0], ref.data_ptr(), A.shape[0], ld.data_ptr(), 0, _stream())
+    assert st == 0, lib.qml_last_error()
+    return ref, ld
+
+
+def _check_pair(lib, n, seed):
+    """Two calls of qml_potrf_noalloc on n x n matrices.  The first may meet a
+    shape nothing has tuned: the tuning table must gain no "dgemm:" entry.
+    The second (same shape, another matrix) runs with every kernel module
+    already loaded -- CUDA loads modules lazily on first use, which takes
+    device memory for code and for the static scratch array itself -- and
+    must leave free device memory unchanged.  Both match qml_potrf."""
+    mats = [_spd(n, seed), _spd(n, seed + 1)]
     torch.cuda.synchronize()
     tuned0 = _dgemm_entries(lib)
-    free0 = torch.cuda.mem_get_info()[0]
-    st = lib.qml_potrf_noalloc(n, out.data_ptr(), n, ld.data_ptr(), _stream())
-    assert st == 0, lib.qml_last_error()
-    free1 = torch.cuda.mem_get_info()[0]
+    out0, ld0 = _noalloc(lib, mats[0])
     assert _dgemm_entries(lib) == tuned0, "qml_potrf_noalloc ran the allocating tile autotuner"
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    out1, ld1 = _noalloc(lib, mats[1])
+    free1 = torch.cuda.mem_get_info()[0]
     assert free1 >= free0, (free0, free1)
-    ref = _colmajor_dev(A)
-    ld_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
-    st = lib.qml_potrf(n, ref.data_ptr(), n, ld_ref.data_ptr(), 0, _stream())
-    assert st == 0, lib.qml_last_error()
-    L, Lr = torch.tril(out).cpu().numpy(), torch.tril(ref).cpu().numpy()
-    assert np.abs(L - Lr).max() <= 1e-12 * np.abs(Lr).max(), n
-    assert abs(ld.item() - ld_ref.item()) <= 1e-12 * abs(ld_ref.item())
+    for A, out, ld in ((mats[0], out0, ld0), (mats[1], out1, ld1)):
+        ref, ld_ref = _potrf(lib, A)
+        L, Lr = torch.tril(out).cpu().numpy(), torch.tril(ref).cpu().numpy()
+        assert np.abs(L - Lr).max() <= 1e-12 * np.abs(Lr).max(), n
+        assert abs(ld.item() - ld_ref.item()) <= 1e-12 * abs(ld_ref.item())
 
 
 def test_noalloc_first_on_unseen_shapes(lib):
