@@ -293,7 +293,8 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *   batch_streams   worker streams of pix_loglike_batch (default 4, 1..16)
  *   batch_graphs    1 (default) / 0: pix_loglike_batch replays each worker's
  *                   per-item kernel sequence as a captured CUDA graph
- *   ozaki_stages    6 (default) / 4: depth of the split kernel's TMA ring
+ *   ozaki_stages    3 (default) / 2: depth of the split kernel's TMA ring
+ *                   (stages of 64 KB; always 2 for more than 8 digits)
  *   emu_tc          1 (default) / 0: emulator inference runs its layers on
  *                   tcgen05 (width a multiple of 64, at most 256) / every
  *                   layer through the WMMA product

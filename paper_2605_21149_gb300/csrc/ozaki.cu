@@ -20,16 +20,27 @@
 // digit slicing reads the float64 bit patterns with integer operations (the
 // float64 pipe of this part is narrow).
 //
+// Schedule.  The levels are taken in groups of four (2..5, 6..9, 10..11),
+// each level of a group in its own 128-column FP32 accumulator (the four use
+// all 512 TMEM columns).  For a group, every K step of 16 loads each digit
+// tile the group needs once -- A_1..A_d and B_1..B_d, d = min(S, last level
+// - 1), 4 KB each -- and runs every digit pair of the group's levels on them,
+// so a loaded tile serves all the pairs it belongs to (S = 8: 24 tile loads
+// per K step for 36 products, where one load per operand and pair would take
+// 72).  The tensor core reads a 128 x 128 x 16 product's 8 KB of operands from
+// shared memory at its full rate; what bounds the product is delivering the
+// tiles from L2, hence the reuse.
+//
 // Kernel layout: one CTA per 128 x 128 output tile, 320 threads.
-//   warp 0   TMA producer (one lane): bf16 digit tiles 128 x 64 of op(A) and
-//            op(B), 128-byte swizzle, 6-stage ring guarded by mbarriers (4
-//            when the tuning table's ozaki_stages says so);
+//   warp 0   TMA producer (one lane): 128 x 16 bf16 digit tiles, 32-byte
+//            swizzle, a ring of stages of up to stage_tiles tiles per operand
+//            (one or more K steps), guarded by mbarriers;
 //   warp 1   TMEM allocator and MMA issuer (one lane): tcgen05.mma kind::f16
-//            M=128 N=128 K=16 into one of two FP32 accumulators in TMEM
-//            (columns [0,128) and [128,256)), so a flush of one overlaps the
-//            MMAs of the next chunk;
+//            M=128 N=128 K=16 into the group's level accumulators; after each
+//            exact chunk it commits them to the epilogue and waits until they
+//            are read before the next chunk overwrites them;
 //   warps 2-9 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows)
-//            and 64 columns (half (w - 2) / 4 of the tile).
+//            and 64 columns (half (w - 2) / 4 of the tile) of each level.
 // Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the CTA records
 // QML_ETIMEOUT, drains what it issued, frees TMEM and returns.
 #include "internal.cuh"
@@ -45,8 +56,10 @@ namespace qmlgb {
 
 namespace {
 
-constexpr int OBM = 128, OBN = 128, OBK = 64;
-constexpr int kTileBytes = OBM * OBK * 2;  // 16 KB per operand tile
+constexpr int OBM = 128, OBN = 128, OBK = 64;  // output tile; K padding of the digit planes
+constexpr int KS = 16;                          // K per MMA instruction and per TMA box
+constexpr int kDigitTile = OBM * KS * 2;        // 4 KB: one 128 x 16 bf16 digit tile
+constexpr int kGroupLevels = 4;                 // levels per group: 4 x 128 TMEM columns
 // warps 0 and 1: TMA producer and MMA issuer; kEpiWarps epilogue warps, each
 // one TMEM lane quarter (32 tile rows) by kEpiCols columns, so a thread holds
 // kEpiCols int64 accumulators
@@ -58,6 +71,7 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 // most kChunkK 2^10 (n_L + 2) <= 2^10 2^10 12 < 2^24 for the n_L <= 10 pairs a
 // level has (S <= 10), and level 2 at most kChunkK 2^12 = 2^22: exact.
 constexpr int kChunkK = 1024;
+constexpr int kChunkSteps = kChunkK / KS;
 // most digits per operand element (beta S <= 62 with beta = 6)
 constexpr int kMaxSlices = 10;
 
@@ -68,10 +82,24 @@ constexpr int kMaxSlices = 10;
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
                             ((uint32_t)(OBM >> 4) << 24);
 
+// K-major bf16 tile of 16-element (32-byte) rows with the 32-byte swizzle
+// (8-row atoms of 256 B): start address, LBO 16 B (unused: one MMA's K is the
+// whole swizzle row), SBO 256 B, descriptor version 1, layout type 6.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
+  return d;
+}
+
 struct OzParams {
   int64_t M, N;            // logical output size
-  int Mpad, Npad, nk;      // padded rows of the digit arrays; K stages of 64
-  int S, beta, chunk;      // digits, bits per digit, stages per exact chunk
+  int Mpad, Npad, nk16;    // padded rows of the digit arrays; K steps of 16
+  int S, beta;             // digits, bits per digit
+  int stage_tiles;         // digit tiles per operand a ring stage holds
+  int nstages;             // ring depth
   int shift_top;           // left shift of level-2 chunk sums in the int64 accumulator
   int tiles_n, lower;
   double alpha, betac;
@@ -118,18 +146,73 @@ __device__ __forceinline__ void tile_of(const OzParams &p, int bid, int &tm, int
   tn = bid - r * (r + 1) / 2;
 }
 
-template <int OSTAGES>
+// Level group g: levels lb .. le (at most kGroupLevels), digits 1 .. nd of
+// each operand, and the K steps a ring stage holds for it.
+struct Group {
+  int lb, le, nd, sps;
+};
+__device__ __forceinline__ Group group_of(const OzParams &p, int S, int g) {
+  Group G;
+  G.lb = 2 + kGroupLevels * g;
+  G.le = min(S + 1, G.lb + kGroupLevels - 1);
+  G.nd = min(S, G.le - 1);
+  G.sps = max(1, p.stage_tiles / G.nd);
+  return G;
+}
+
+// Every digit product of levels LB..LE (S digits) for one K step, in
+// level-major order: pair (s, t) reads digit tile s - 1 of A and t - 1 of B,
+// at descriptor offsets of 256 (4 KB >> 4) per tile from the step's first
+// tiles (da, db).  Unrolled at compile time, so the issuing thread spends a
+// few instructions per MMA: with loop bounds, flags and descriptors computed
+// at run time it could not keep up with the tensor core (about 95 clocks of
+// issue per 64-clock MMA).  The first pair of each level writes its
+// accumulator when acc0 is 0 (first K step of a chunk), later pairs add.
+template <int LB, int LE, int S>
+__device__ __forceinline__ void issue_step(uint32_t tbase, uint64_t da, uint64_t db,
+                                           uint32_t acc0) {
+#pragma unroll
+  for (int L = LB; L <= LE; ++L) {
+#pragma unroll
+    for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S); ++s) {
+      const int t = L - s;
+      const bool first = (s == (L - S > 1 ? L - S : 1));
+      mma_bf16(tbase + 128 * (L - LB), da + (uint64_t)(256 * (s - 1)),
+               db + (uint64_t)(256 * (t - 1)), kIdesc, first ? acc0 : 1u);
+    }
+  }
+}
+
+// TMA loads of one stage: nsteps K steps of ND digit tiles per operand; yA[d],
+// yB[d] are the digit-plane rows of this CTA's tile for digit d.
+template <int ND>
+__device__ __forceinline__ void load_stage(const CUtensorMap *tmA, const CUtensorMap *tmB,
+                                           uint32_t sa, uint32_t sb, uint32_t bar, int k16,
+                                           int nsteps, const int *yA, const int *yB) {
+  for (int j = 0; j < nsteps; ++j) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const uint32_t off = (uint32_t)(j * ND + d) * kDigitTile;
+      tma_load_2d(sa + off, tmA, bar, (k16 + j) * KS, yA[d]);
+      tma_load_2d(sb + off, tmB, bar, (k16 + j) * KS, yB[d]);
+    }
+  }
+}
+
+// SC = 8: the default digit count with the unrolled schedule above; SC = 0:
+// any S (run-time loops).
+template <int SC>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *tilesA = smem;
-  unsigned char *tilesB = smem + OSTAGES * kTileBytes;
-  uint64_t *bars = (uint64_t *)(smem + 2 * OSTAGES * kTileBytes);
-  // bars: [0,ST) full, [ST,2ST) empty, 2ST+b acc_full[b], 2ST+2+b acc_empty[b], 2ST+4 drain
-  uint32_t *tmem_holder = (uint32_t *)(bars + 2 * OSTAGES + 5);
+  const int NST = p.nstages;
+  const int stage_bytes = 2 * p.stage_tiles * kDigitTile;  // A tiles, then B tiles
+  uint64_t *bars = (uint64_t *)(smem + (size_t)NST * stage_bytes);
+  // bars: [0,NST) full, [NST,2NST) empty, 2NST acc_full, 2NST+1 acc_empty, 2NST+2 drain
+  uint32_t *tmem_holder = (uint32_t *)(bars + 2 * NST + 3);
   int *s_eb = (int *)(tmem_holder + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -137,62 +220,75 @@ __global__ void __launch_bounds__(kThreads, 1)
   tile_of(p, blockIdx.x, tm, tn);
   const int m0 = tm * OBM, n0 = tn * OBN;
   DevStatus *st = p.status;
-  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OSTAGES]);
-  const uint32_t accf0 = smem_u32(&bars[2 * OSTAGES]), acce0 = smem_u32(&bars[2 * OSTAGES + 2]);
-  const uint32_t drain = smem_u32(&bars[2 * OSTAGES + 4]);
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[NST]);
+  const uint32_t accf = smem_u32(&bars[2 * NST]), acce = smem_u32(&bars[2 * NST + 1]);
+  const uint32_t drain = smem_u32(&bars[2 * NST + 2]);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < OSTAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 32 * kEpiWarps);
-    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 32 * kEpiWarps);
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int j = threadIdx.x; j < OBN; j += blockDim.x) s_eb[j] = p.eb[n0 + j];
-  if (warp == 1) tmem_alloc(smem_u32(tmem_holder), 256);
+  if (warp == 1) tmem_alloc(smem_u32(tmem_holder), kGroupLevels * 128);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_holder;
 
-  const int S = p.S;
-  const int nchunks = (p.nk + p.chunk - 1) / p.chunk;
+  const int S = SC ? SC : p.S;
+  const int ngroups = (S + kGroupLevels - 1) / kGroupLevels;  // levels 2 .. S+1
+  const int nchunks = (p.nk16 + kChunkSteps - 1) / kChunkSteps;
 
   if (warp == 0) {
     // ------------------------------------------------------- TMA producer
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      int last_phase[OSTAGES];
-      for (int q = 0; q < OSTAGES; ++q) last_phase[q] = -1;
+      int last_phase[4] = {-1, -1, -1, -1};
+      int yA[kMaxSlices], yB[kMaxSlices];  // digit-plane rows of this tile
+#pragma unroll
+      for (int d = 0; d < kMaxSlices; ++d) {
+        yA[d] = d * p.Mpad + m0;
+        yB[d] = d * p.Npad + n0;
+      }
       bool ok = (*((volatile int *)&st->code) == 0) && !p.no_loads;
-      for (int L = 2; L <= S + 1 && ok; ++L) {
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const Group G = group_of(p, S, g);
         for (int c = 0; c < nchunks && ok; ++c) {
-          const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
-          for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
-            const int t = L - s;
-            for (int ks = k0; ks < k1 && ok; ++ks) {
-              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st, p.wait_ns)) { ok = false; break; }
-              mbar_expect_tx(full0 + 8 * stage, 2 * kTileBytes);
-              tma_load_2d(smem_u32(tilesA + stage * kTileBytes), &tmA, full0 + 8 * stage, ks * OBK,
-                          (s - 1) * p.Mpad + m0);
-              tma_load_2d(smem_u32(tilesB + stage * kTileBytes), &tmB, full0 + 8 * stage, ks * OBK,
-                          (t - 1) * p.Npad + n0);
-              last_phase[stage] = (int)phase;
-              if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
+          const int k0 = c * kChunkSteps, k1 = min(k0 + kChunkSteps, p.nk16);
+          for (int ks = k0; ks < k1; ks += G.sps) {
+            const int nsteps = min(G.sps, k1 - ks);
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st, p.wait_ns)) { ok = false; break; }
+            mbar_expect_tx(full0 + 8 * stage, 2u * G.nd * nsteps * kDigitTile);
+            const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
+            const uint32_t sb = sa + p.stage_tiles * kDigitTile;
+            if (SC == 8 && G.nd == 4) {
+              load_stage<4>(&tmA, &tmB, sa, sb, full0 + 8 * stage, ks, nsteps, yA, yB);
+            } else if (SC == 8) {
+              load_stage<8>(&tmA, &tmB, sa, sb, full0 + 8 * stage, ks, nsteps, yA, yB);
+            } else {
+              for (int j = 0; j < nsteps; ++j)
+                for (int d = 0; d < G.nd; ++d) {
+                  const uint32_t off = (uint32_t)(j * G.nd + d) * kDigitTile;
+                  tma_load_2d(sa + off, &tmA, full0 + 8 * stage, (ks + j) * KS, yA[d]);
+                  tma_load_2d(sb + off, &tmB, full0 + 8 * stage, (ks + j) * KS, yB[d]);
+                }
             }
+            last_phase[stage] = (int)phase;
+            if (++stage == NST) { stage = 0; phase ^= 1; }
           }
         }
       }
       if (!ok) {
         // drain: wait (bounded) until the last load issued into each slot has
         // landed, so no copy is still writing shared memory when the CTA exits
-        for (int q = 0; q < OSTAGES; ++q) {
+        for (int q = 0; q < NST; ++q) {
           if (last_phase[q] < 0) continue;
           mbar_drain_wait(full0 + 8 * q, (uint32_t)last_phase[q]);
         }
@@ -203,39 +299,48 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t q = 0;  // chunk accumulations so far; buffer q & 1
+      uint32_t q = 0;  // chunk flushes so far
       bool ok = (*((volatile int *)&st->code) == 0);
-      for (int L = 2; L <= S + 1 && ok; ++L) {
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const Group G = group_of(p, S, g);
         for (int c = 0; c < nchunks && ok; ++c) {
-          const uint32_t b = q & 1;
-          // the epilogue must have read this buffer's previous chunk
-          if (q >= 2 && !mbar_wait(acce0 + 8 * b, ((q >> 1) - 1) & 1, st, p.wait_ns)) {
-            ok = false;
-            break;
-          }
+          // the epilogue must have read the accumulators of the previous chunk
+          if (q >= 1 && !mbar_wait(acce, (q - 1) & 1, st, p.wait_ns)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t dacc = tbase + 128 * b;
-          const int k0 = c * p.chunk, k1 = (k0 + p.chunk < p.nk) ? k0 + p.chunk : p.nk;
-          uint32_t acc_on = 0;  // the first MMA of the (level, chunk) sum overwrites
-          // every digit pair of this level adds into the same accumulator
-          for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S) && ok; ++s) {
-            for (int ks = k0; ks < k1; ++ks) {
-              if (!mbar_wait(full0 + 8 * stage, phase, st, p.wait_ns)) { ok = false; break; }
-              tc_fence_after();
-              const uint32_t a_addr = smem_u32(tilesA + stage * kTileBytes);
-              const uint32_t b_addr = smem_u32(tilesB + stage * kTileBytes);
-#pragma unroll
-              for (int kk = 0; kk < OBK / 16; ++kk) {
-                mma_bf16(dacc, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk), kIdesc,
-                         acc_on);
-                acc_on = 1u;
+          const int k0 = c * kChunkSteps, k1 = min(k0 + kChunkSteps, p.nk16);
+          for (int ks = k0; ks < k1 && ok; ks += G.sps) {
+            const int nsteps = min(G.sps, k1 - ks);
+            if (!mbar_wait(full0 + 8 * stage, phase, st, p.wait_ns)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
+            const uint32_t sb = sa + p.stage_tiles * kDigitTile;
+            const uint64_t da0 = smem_desc_sw32(sa), db0 = smem_desc_sw32(sb);
+            for (int j = 0; j < nsteps; ++j) {
+              const uint32_t acc0 = (ks == k0 && j == 0) ? 0u : 1u;
+              if (SC == 8 && g == 0) {
+                issue_step<2, 5, 8>(tbase, da0 + (uint64_t)(256 * 4 * j),
+                                    db0 + (uint64_t)(256 * 4 * j), acc0);
+              } else if (SC == 8) {
+                issue_step<6, 9, 8>(tbase, da0 + (uint64_t)(256 * 8 * j),
+                                    db0 + (uint64_t)(256 * 8 * j), acc0);
+              } else {
+                for (int L = G.lb; L <= G.le; ++L) {
+                  const int s0 = max(1, L - S);
+                  for (int s = s0; s <= min(S, L - 1); ++s) {
+                    const int t = L - s;
+                    mma_bf16(tbase + 128 * (L - G.lb),
+                             da0 + (uint64_t)(256 * (j * G.nd + s - 1)),
+                             db0 + (uint64_t)(256 * (j * G.nd + t - 1)), kIdesc,
+                             s == s0 ? acc0 : 1u);
+                  }
+                }
               }
-              mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
-              if (++stage == OSTAGES) { stage = 0; phase ^= 1; }
             }
+            mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
+            if (++stage == NST) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
-          mma_commit(accf0 + 8 * b);  // (level, chunk) sum ready for the epilogue
+          mma_commit(accf);  // the group's (level, chunk) sums ready for the epilogue
           ++q;
         }
       }
@@ -254,21 +359,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
     uint32_t q = 0;
     bool ok = true;
-    for (int L = 2; L <= S + 1 && ok; ++L) {
-      const int sh = p.shift_top - p.beta * (L - 2);
-      {
-        for (int c = 0; c < nchunks; ++c) {
-          const uint32_t b = q & 1;
-          int okw = 1;
-          if (lane == 0) okw = mbar_wait(accf0 + 8 * b, (q >> 1) & 1, st, p.wait_ns) ? 1 : 0;
-          okw = __shfl_sync(0xffffffffu, okw, 0);
-          __syncwarp();
-          if (!okw) { ok = false; break; }
-          tc_fence_after();
+    for (int g = 0; g < ngroups && ok; ++g) {
+      const Group G = group_of(p, S, g);
+      for (int c = 0; c < nchunks; ++c) {
+        int okw = 1;
+        if (lane == 0) okw = mbar_wait(accf, q & 1, st, p.wait_ns) ? 1 : 0;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        __syncwarp();
+        if (!okw) { ok = false; break; }
+        tc_fence_after();
+        for (int L = G.lb; L <= G.le; ++L) {
+          const int sh = p.shift_top - p.beta * (L - 2);
+          const uint32_t lbase = lane_base + 128 * (L - G.lb);
 #pragma unroll
           for (int cb = 0; cb < kEpiCols / 16; ++cb) {
             uint32_t a[16];
-            tmem_ld16(lane_base + 128 * b + 16 * cb, a);
+            tmem_ld16(lbase + 16 * cb, a);
             if (sh >= 0) {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
@@ -281,10 +387,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 acc[16 * cb + j] += ((long long)__float2int_rn(__uint_as_float(a[j])) + rnd) >> r;
             }
           }
-          tc_fence_before();
-          mbar_arrive(acce0 + 8 * b);
-          ++q;
         }
+        tc_fence_before();
+        mbar_arrive(acce);
+        ++q;
       }
     }
     if (ok) {
@@ -329,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tbase, 256);
+  if (warp == 1) tmem_dealloc(tbase, kGroupLevels * 128);
 }
 
 // ------------------------------------------------------------- digits ----
@@ -488,8 +594,9 @@ __global__ void slice_kernel(const double *X, int64_t R, int64_t K, int64_t sr, 
 }
 
 // ------------------------------------------------------- tensor maps -----
+// digit planes (rows x kpad bf16): 128 x 16 boxes, 32-byte swizzle
 bool make_map(CUtensorMap *map, void *base, int64_t rows, int64_t kpad) {
-  return make_map_bf16(map, base, kpad, rows, kpad * 2, OBK, OBM);
+  return make_map_bf16(map, base, kpad, rows, kpad * 2, KS, OBM, 32);
 }
 
 int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -519,15 +626,19 @@ EncodeTiledFn get_encode() {
 }  // namespace
 
 bool make_map_bf16(CUtensorMap *map, const void *base, int64_t inner, int64_t rows,
-                   int64_t row_bytes, int box_inner, int box_rows) {
+                   int64_t row_bytes, int box_inner, int box_rows, int swizzle_bytes) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
+  CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
+  if (swizzle_bytes == 64) sw = CU_TENSOR_MAP_SWIZZLE_64B;
+  else if (swizzle_bytes == 32) sw = CU_TENSOR_MAP_SWIZZLE_32B;
+  else if (swizzle_bytes != 128) return false;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -564,18 +675,33 @@ void launch_rowmax(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk
   count_launch();
 }
 
-template <int OSTAGES>
+// ring stages: stage_tiles digit tiles per operand (all digits of one K step
+// for the widest group; several K steps for narrower groups)
+constexpr int kMaxSmem = 1024 + 3 * 2 * 8 * kDigitTile + (2 * 3 + 3) * 8 + 16 + OBN * 4;
+
+size_t oz_smem(int stage_tiles, int nstages) {
+  return 1024 + (size_t)nstages * 2 * stage_tiles * kDigitTile + (2 * nstages + 3) * 8 + 16 +
+         OBN * 4;
+}
+
 cudaError_t launch_oz(int ntiles, const CUtensorMap &mA, const CUtensorMap &mB, const OzParams &p,
                       cudaStream_t st) {
-  const size_t smem = 1024 + 2 * OSTAGES * kTileBytes + (2 * OSTAGES + 5) * 8 + 16 + OBN * 4;
+  const size_t smem = oz_smem(p.stage_tiles, p.nstages);
+  if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<OSTAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ozaki_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kMaxSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  ozaki_gemm_kernel<OSTAGES><<<ntiles, kThreads, smem, st>>>(mA, mB, p);
+  if (p.S == 8)
+    ozaki_gemm_kernel<8><<<ntiles, kThreads, smem, st>>>(mA, mB, p);
+  else
+    ozaki_gemm_kernel<0><<<ntiles, kThreads, smem, st>>>(mA, mB, p);
   count_launch();
   return cudaGetLastError();
 }
@@ -630,16 +756,19 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.N = N;
   p.Mpad = (int)Mpad;
   p.Npad = (int)Npad;
-  p.nk = (int)(Kpad / OBK);
+  p.nk16 = (int)(Kpad / KS);
   p.S = S;
   p.beta = beta;
-  p.chunk = kChunkK / OBK;
+  // a stage holds every digit of one K step for the widest group (8 tiles per
+  // operand for S <= 8: 64 KB, three stages); S = 9, 10 take S tiles, two stages
+  p.stage_tiles = S > 8 ? S : 8;
+  p.nstages = S > 8 ? 2 : (tune_get("ozaki_stages", 3) == 2 ? 2 : 3);
   {
     // level-2 chunk sums are below 2^(2 beta) kChunkK = 2^22, level L >= 3
     // sums below 2^20 (L + 1) (a shift of beta (L - 2) bits further down):
     // with nchunks chunks the int64 total stays below 2^(shift_top + 22 +
     // lg) x 1.02 <= 2^61.03
-    const int nchunks = (p.nk + p.chunk - 1) / p.chunk;
+    const int nchunks = (p.nk16 + kChunkSteps - 1) / kChunkSteps;
     int lg = 0;
     while ((1 << lg) < nchunks) ++lg;
     p.shift_top = 39 - lg;
@@ -664,9 +793,7 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.wait_ns = p.no_loads ? 1000000ull : kWaitNs;  // 1 ms in the failure-path test
   const int tiles_m = (int)(Mpad / OBM);
   int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
-  // ring depth: 6 stages by default (the tuning table may pick 4)
-  if (tune_get("ozaki_stages", 6) == 4) return launch_oz<4>(ntiles, mA, mB, p, st);
-  return launch_oz<6>(ntiles, mA, mB, p, st);
+  return launch_oz(ntiles, mA, mB, p, st);
 }
 
 }  // namespace qmlgb

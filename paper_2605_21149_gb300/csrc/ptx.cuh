@@ -136,10 +136,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// K-major bf16 tensor map with 128-byte swizzle over a rows x inner array
-// (row stride row_bytes, a multiple of 16), box box_inner x box_rows; reads
-// outside the array fill zeros.  False when the driver rejects it.
+// K-major bf16 tensor map over a rows x inner array (row stride row_bytes, a
+// multiple of 16), box box_inner x box_rows, with the 128-, 64- or 32-byte
+// swizzle (box_inner x 2 bytes must not exceed it); reads outside the array
+// fill zeros.  False when the driver rejects it.
 bool make_map_bf16(CUtensorMap *map, const void *base, int64_t inner, int64_t rows,
-                   int64_t row_bytes, int box_inner, int box_rows);
+                   int64_t row_bytes, int box_inner, int box_rows, int swizzle_bytes = 128);
 
 }  // namespace qmlgb

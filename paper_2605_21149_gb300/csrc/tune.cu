@@ -9,7 +9,7 @@
 //                    heuristic only
 //   dgemm:<ta>,<tb>,<lower>,<M>,<N>,<K>,<alias>   measured tile, 10 RM + RN
 //   batch_streams    worker streams of pix_loglike_batch (default 4, 1..16)
-//   ozaki_stages     6 (default) / 4: depth of the split kernel's TMA ring
+//   ozaki_stages     3 (default) / 2: depth of the split kernel's TMA ring
 //   emu_tc           1 (default) / 0: emulator inference layers on tcgen05
 //                    / all through the WMMA product
 //   emu_tc0          1 (default) / 0: with emu_tc, the first layer too (its
