@@ -10,7 +10,7 @@
 // (products below the truncation level are dropped).  Every digit product
 // A_s B_t^T is an integer matrix, and all pairs of one level L = s + t carry
 // the same weight, so they accumulate into one FP32 TMEM accumulator; over a
-// K-chunk of kChunkK elements the level sum stays below 2^24, so the
+// K-chunk of 1536 (S <= 8) or 1024 elements the level sum stays below 2^24, so the
 // tensor-core accumulation is exact whatever its order or rounding mode.
 // Each exact (level, chunk) sum is converted to int32 and added, shifted left
 // by shift_L = shift_top - beta (L - 2) bits (right, rounded, when negative),
@@ -31,7 +31,7 @@
 // shared memory at its full rate; what bounds the product is delivering the
 // tiles from L2, hence the reuse.
 //
-// Kernel layout: one CTA per 128 x 128 output tile, 320 threads.
+// Kernel layout: one CTA per 128 x 128 output tile, 384 threads.
 //   warp 0   TMA producer (one lane): 128 x 16 bf16 digit tiles, 32-byte
 //            swizzle, a ring of stages of up to stage_tiles tiles per operand
 //            (one or more K steps), guarded by mbarriers;
@@ -39,10 +39,12 @@
 //            M=128 N=128 K=16 into the group's level accumulators; after each
 //            exact chunk it commits them to the epilogue and waits until they
 //            are read before the next chunk overwrites them;
-//   warps 2-9 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows)
-//            and 64 columns (half (w - 2) / 4 of the tile) of each level.
+//   warps 2-3 idle (they complete warpgroup 0 for the register split);
+//   warps 4-11 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows)
+//            and 64 columns (half (w - 4) / 4 of the tile) of each level.
 // Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the CTA records
 // QML_ETIMEOUT, drains what it issued, frees TMEM and returns.
+#include "fixconv.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -60,18 +62,30 @@ constexpr int OBM = 128, OBN = 128, OBK = 64;  // output tile; K padding of the 
 constexpr int KS = 16;                          // K per MMA instruction and per TMA box
 constexpr int kDigitTile = OBM * KS * 2;        // 4 KB: one 128 x 16 bf16 digit tile
 constexpr int kGroupLevels = 4;                 // levels per group: 4 x 128 TMEM columns
-// warps 0 and 1: TMA producer and MMA issuer; kEpiWarps epilogue warps, each
-// one TMEM lane quarter (32 tile rows) by kEpiCols columns, so a thread holds
-// kEpiCols int64 accumulators
+// Three warpgroups.  Warpgroup 0: warp 0 the TMA producer, warp 1 the TMEM
+// allocator and MMA issuer, warps 2-3 idle.  Warpgroups 1 and 2 (warps
+// 4-11): kEpiWarps epilogue warps, each one TMEM lane quarter (32 tile rows)
+// by kEpiCols columns, so a thread holds kEpiCols int64 accumulators.  The
+// block starts at kLaunchRegs registers a thread (12 warps, three on each SM
+// sub-partition of 16384 registers: 65536 / 384 rounded down to 8); then
+// warpgroup 0 gives registers back (setmaxnreg.dec to kIssueRegs) and the
+// epilogue takes them (setmaxnreg.inc to kEpiRegs), so that its 64 int64 sums
+// stay in registers.  The split adds up exactly:
+// 128 kIssueRegs + 256 kEpiRegs = 384 kLaunchRegs.
 constexpr int kEpiWarps = 8, kEpiCols = 128 * 4 / kEpiWarps;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kThreads = 128 + 32 * kEpiWarps;
+constexpr int kLaunchRegs = 168, kIssueRegs = 56, kEpiRegs = 224;
+static_assert(128 * kIssueRegs + 256 * kEpiRegs == kThreads * kLaunchRegs,
+              "register split must equal the launch's registers");
+static_assert(kThreads * kLaunchRegs <= 65536, "launch registers exceed the SM");
 // K elements per exact chunk.  All digit pairs (s, t) of one level L = s + t
 // accumulate in the same FP32 accumulator: with beta = 6, |a_1|, |b_1| <= 2^6
-// and the other digits <= 2^5, so a level-L sum over kChunkK elements is at
-// most kChunkK 2^10 (n_L + 2) <= 2^10 2^10 12 < 2^24 for the n_L <= 10 pairs a
-// level has (S <= 10), and level 2 at most kChunkK 2^12 = 2^22: exact.
-constexpr int kChunkK = 1024;
-constexpr int kChunkSteps = kChunkK / KS;
+// and the other digits <= 2^5, so a level-L sum over c elements is at most
+// c 2^10 (n_L + 2) for the n_L <= S pairs of a level L >= 3, and level 2 at
+// most c 2^12.  With S <= 8 (n_L <= 8) a chunk of 1536 stays below
+// 1536 2^10 10 < 2^24; with S = 9, 10 a chunk of 1024 below 2^10 2^10 12 <
+// 2^24: exact either way.
+__host__ __device__ constexpr int chunk_elems(int S) { return S <= 8 ? 1536 : 1024; }
 // most digits per operand element (beta S <= 62 with beta = 6)
 constexpr int kMaxSlices = 10;
 
@@ -102,6 +116,7 @@ struct OzParams {
   int nstages;             // ring depth
   int shift_top;           // left shift of level-2 chunk sums in the int64 accumulator
   int tiles_n, lower;
+  int ntiles;              // output tiles; the grid takes them round-robin
   double alpha, betac;
   int alpha_pow2, alpha_exp, alpha_neg;  // alpha = (-1)^neg 2^exp when alpha_pow2
   double *C;
@@ -115,20 +130,13 @@ struct OzParams {
   int no_loads;
 };
 
-// acc 2^E as a float64, sign flipped when neg: one int64 -> float64
-// conversion (rounded to nearest even), then E added to the exponent field and
-// the sign bit flipped with integer operations.  Returns false when the
-// result would leave the normal range; the caller then uses ldexp.
+// acc 2^E as a float64, sign flipped when neg, by integer operations
+// (fixconv.cuh); false when the result would leave the normal range, and the
+// caller then uses ldexp.
 __device__ __forceinline__ bool fixed_to_double(long long acc, int E, bool neg, double &out) {
-  const long long b = __double_as_longlong((double)acc);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) {  // acc == 0
-    out = neg ? -0.0 : 0.0;
-    return true;
-  }
-  const int nex = ex + E;
-  if (nex <= 0 || nex >= 2047) return false;
-  out = __longlong_as_double((b + ((long long)E << 52)) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+  uint64_t bits;
+  if (!fixed_to_double_bits(acc, E, neg, bits)) return false;
+  out = __longlong_as_double((long long)bits);
   return true;
 }
 
@@ -177,34 +185,76 @@ __device__ __forceinline__ void issue_step(uint32_t tbase, uint64_t da, uint64_t
     for (int s = (L - S > 1 ? L - S : 1); s <= (L - 1 < S ? L - 1 : S); ++s) {
       const int t = L - s;
       const bool first = (s == (L - S > 1 ? L - S : 1));
-      mma_bf16(tbase + 128 * (L - LB), da + (uint64_t)(256 * (s - 1)),
-               db + (uint64_t)(256 * (t - 1)), kIdesc, first ? acc0 : 1u);
+      mma_bf16_off(tbase + 128 * (L - LB), da, (uint64_t)(256 * (s - 1)), db,
+                   (uint64_t)(256 * (t - 1)), kIdesc, first ? acc0 : 1u);
     }
   }
 }
 
-// TMA loads of one stage: nsteps K steps of ND digit tiles per operand; yA[d],
-// yB[d] are the digit-plane rows of this CTA's tile for digit d.
+// TMA loads of one stage: nsteps K steps, each one box of ND digit tiles
+// (digits 1..ND, 128 rows, 16 elements of K) per operand from a 3-D map over
+// the digit planes (K, rows, digit); the box lands as ND consecutive 4 KB tiles.
 template <int ND>
 __device__ __forceinline__ void load_stage(const CUtensorMap *tmA, const CUtensorMap *tmB,
                                            uint32_t sa, uint32_t sb, uint32_t bar, int k16,
-                                           int nsteps, const int *yA, const int *yB) {
+                                           int nsteps, int m0, int n0) {
   for (int j = 0; j < nsteps; ++j) {
+    const uint32_t off = (uint32_t)(j * ND) * kDigitTile;
+    tma_load_3d(sa + off, tmA, bar, (k16 + j) * KS, m0, 0);
+    tma_load_3d(sb + off, tmB, bar, (k16 + j) * KS, n0, 0);
+  }
+}
+
+// Output of 8 consecutive columns of one row: C[gi + gj ldc] = alpha 2^(e)
+// acc + beta C for the live entries (gj < N, and gj <= gi for a lower C).  Not
+// inlined: its 8 calls share one copy of the code, which stays in the
+// instruction cache (unrolled 64 times, the output code ran once per tile and
+// was fetched cold).  The 8 C values are read before any is written, so
+// their loads are in flight together.
+__device__ __noinline__ void store_out8(const OzParams &p, int64_t gi, int64_t gj0, int ebase,
+                                        long long a0, long long a1, long long a2, long long a3,
+                                        long long a4, long long a5, long long a6, long long a7) {
+  const long long av[8] = {a0, a1, a2, a3, a4, a5, a6, a7};
+  const int eshift = p.alpha_pow2 ? p.alpha_exp : 0;
+  const bool aneg = p.alpha_pow2 && p.alpha_neg;
+  double cv[8];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      const uint32_t off = (uint32_t)(j * ND + d) * kDigitTile;
-      tma_load_2d(sa + off, tmA, bar, (k16 + j) * KS, yA[d]);
-      tma_load_2d(sb + off, tmB, bar, (k16 + j) * KS, yB[d]);
+  for (int u = 0; u < 8; ++u) {
+    const int64_t gj = gj0 + u;
+    const bool live = gj < p.N && !(p.lower && gi < gj);
+    cv[u] = (live && p.betac != 0.0) ? p.C[gi + gj * p.ldc] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int64_t gj = gj0 + u;
+    if (gj >= p.N || (p.lower && gi < gj)) continue;
+    const int eb = p.eb[gj];
+    double v;
+    if (fixed_to_double(av[u], ebase + eb + eshift, aneg, v)) {
+      if (!p.alpha_pow2) v *= p.alpha;
+    } else {
+      v = p.alpha * ldexp((double)av[u], ebase + eb);
     }
+    if (p.betac == 1.0) v += cv[u];
+    else if (p.betac != 0.0) v = fma(p.betac, cv[u], v);
+    p.C[gi + gj * p.ldc] = v;
   }
 }
 
 // SC = 8: the default digit count with the unrolled schedule above; SC = 0:
-// any S (run-time loops).
+// any S (run-time loops).  Persistent: each CTA takes tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the producer runs on into the next tile's
+// data and the MMAs of the next tile start as soon as the epilogue has read
+// the accumulators, while the epilogue converts and stores the finished tile
+// from its registers.
 template <int SC>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, OzParams p) {
+                      const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ CUtensorMap tmA4,
+                      const __grid_constant__ CUtensorMap tmB4,
+                      const __grid_constant__ CUtensorMap tmA8,
+                      const __grid_constant__ CUtensorMap tmB8, OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -213,12 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *bars = (uint64_t *)(smem + (size_t)NST * stage_bytes);
   // bars: [0,NST) full, [NST,2NST) empty, 2NST acc_full, 2NST+1 acc_empty, 2NST+2 drain
   uint32_t *tmem_holder = (uint32_t *)(bars + 2 * NST + 3);
-  int *s_eb = (int *)(tmem_holder + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int tm, tn;
-  tile_of(p, blockIdx.x, tm, tn);
-  const int m0 = tm * OBM, n0 = tn * OBN;
   DevStatus *st = p.status;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[NST]);
   const uint32_t accf = smem_u32(&bars[2 * NST]), acce = smem_u32(&bars[2 * NST + 1]);
@@ -234,7 +280,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int j = threadIdx.x; j < OBN; j += blockDim.x) s_eb[j] = p.eb[n0 + j];
   if (warp == 1) tmem_alloc(smem_u32(tmem_holder), kGroupLevels * 128);
   tc_fence_before();
   __syncthreads();
@@ -243,45 +288,48 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int S = SC ? SC : p.S;
   const int ngroups = (S + kGroupLevels - 1) / kGroupLevels;  // levels 2 .. S+1
-  const int nchunks = (p.nk16 + kChunkSteps - 1) / kChunkSteps;
+  const int csteps = chunk_elems(S) / KS;  // K steps per exact chunk
+  const int nchunks = (p.nk16 + csteps - 1) / csteps;
 
+  if (warp < 4) {
+  // warpgroup 0 hands registers to the epilogue warpgroups
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kIssueRegs));
   if (warp == 0) {
     // ------------------------------------------------------- TMA producer
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       int last_phase[4] = {-1, -1, -1, -1};
-      int yA[kMaxSlices], yB[kMaxSlices];  // digit-plane rows of this tile
-#pragma unroll
-      for (int d = 0; d < kMaxSlices; ++d) {
-        yA[d] = d * p.Mpad + m0;
-        yB[d] = d * p.Npad + n0;
-      }
       bool ok = (*((volatile int *)&st->code) == 0) && !p.no_loads;
-      for (int g = 0; g < ngroups && ok; ++g) {
-        const Group G = group_of(p, S, g);
-        for (int c = 0; c < nchunks && ok; ++c) {
-          const int k0 = c * kChunkSteps, k1 = min(k0 + kChunkSteps, p.nk16);
-          for (int ks = k0; ks < k1; ks += G.sps) {
-            const int nsteps = min(G.sps, k1 - ks);
-            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st, p.wait_ns)) { ok = false; break; }
-            mbar_expect_tx(full0 + 8 * stage, 2u * G.nd * nsteps * kDigitTile);
-            const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
-            const uint32_t sb = sa + p.stage_tiles * kDigitTile;
-            if (SC == 8 && G.nd == 4) {
-              load_stage<4>(&tmA, &tmB, sa, sb, full0 + 8 * stage, ks, nsteps, yA, yB);
-            } else if (SC == 8) {
-              load_stage<8>(&tmA, &tmB, sa, sb, full0 + 8 * stage, ks, nsteps, yA, yB);
-            } else {
-              for (int j = 0; j < nsteps; ++j)
-                for (int d = 0; d < G.nd; ++d) {
-                  const uint32_t off = (uint32_t)(j * G.nd + d) * kDigitTile;
-                  tma_load_2d(sa + off, &tmA, full0 + 8 * stage, (ks + j) * KS, yA[d]);
-                  tma_load_2d(sb + off, &tmB, full0 + 8 * stage, (ks + j) * KS, yB[d]);
-                }
+      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+        int tm, tn;
+        tile_of(p, tile, tm, tn);
+        const int m0 = tm * OBM, n0 = tn * OBN;
+        for (int g = 0; g < ngroups && ok; ++g) {
+          const Group G = group_of(p, S, g);
+          for (int c = 0; c < nchunks && ok; ++c) {
+            const int k0 = c * csteps, k1 = min(k0 + csteps, p.nk16);
+            for (int ks = k0; ks < k1; ks += G.sps) {
+              const int nsteps = min(G.sps, k1 - ks);
+              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, st, p.wait_ns)) { ok = false; break; }
+              mbar_expect_tx(full0 + 8 * stage, 2u * G.nd * nsteps * kDigitTile);
+              const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
+              const uint32_t sb = sa + p.stage_tiles * kDigitTile;
+              if (SC == 8 && G.nd == 4) {
+                load_stage<4>(&tmA4, &tmB4, sa, sb, full0 + 8 * stage, ks, nsteps, m0, n0);
+              } else if (SC == 8) {
+                load_stage<8>(&tmA8, &tmB8, sa, sb, full0 + 8 * stage, ks, nsteps, m0, n0);
+              } else {
+                for (int j = 0; j < nsteps; ++j)
+                  for (int d = 0; d < G.nd; ++d) {
+                    const uint32_t off = (uint32_t)(j * G.nd + d) * kDigitTile;
+                    tma_load_2d(sa + off, &tmA, full0 + 8 * stage, (ks + j) * KS, d * p.Mpad + m0);
+                    tma_load_2d(sb + off, &tmB, full0 + 8 * stage, (ks + j) * KS, d * p.Npad + n0);
+                  }
+              }
+              last_phase[stage] = (int)phase;
+              if (++stage == NST) { stage = 0; phase ^= 1; }
             }
-            last_phase[stage] = (int)phase;
-            if (++stage == NST) { stage = 0; phase ^= 1; }
           }
         }
       }
@@ -301,134 +349,118 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       uint32_t q = 0;  // chunk flushes so far
       bool ok = (*((volatile int *)&st->code) == 0);
-      for (int g = 0; g < ngroups && ok; ++g) {
-        const Group G = group_of(p, S, g);
-        for (int c = 0; c < nchunks && ok; ++c) {
-          // the epilogue must have read the accumulators of the previous chunk
-          if (q >= 1 && !mbar_wait(acce, (q - 1) & 1, st, p.wait_ns)) { ok = false; break; }
-          tc_fence_after();
-          const int k0 = c * kChunkSteps, k1 = min(k0 + kChunkSteps, p.nk16);
-          for (int ks = k0; ks < k1 && ok; ks += G.sps) {
-            const int nsteps = min(G.sps, k1 - ks);
-            if (!mbar_wait(full0 + 8 * stage, phase, st, p.wait_ns)) { ok = false; break; }
+      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+        for (int g = 0; g < ngroups && ok; ++g) {
+          const Group G = group_of(p, S, g);
+          for (int c = 0; c < nchunks && ok; ++c) {
+            // the epilogue must have read the accumulators of the previous chunk
+            if (q >= 1 && !mbar_wait(acce, (q - 1) & 1, st, p.wait_ns)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
-            const uint32_t sb = sa + p.stage_tiles * kDigitTile;
-            const uint64_t da0 = smem_desc_sw32(sa), db0 = smem_desc_sw32(sb);
-            for (int j = 0; j < nsteps; ++j) {
-              const uint32_t acc0 = (ks == k0 && j == 0) ? 0u : 1u;
-              if (SC == 8 && g == 0) {
-                issue_step<2, 5, 8>(tbase, da0 + (uint64_t)(256 * 4 * j),
-                                    db0 + (uint64_t)(256 * 4 * j), acc0);
-              } else if (SC == 8) {
-                issue_step<6, 9, 8>(tbase, da0 + (uint64_t)(256 * 8 * j),
-                                    db0 + (uint64_t)(256 * 8 * j), acc0);
-              } else {
-                for (int L = G.lb; L <= G.le; ++L) {
-                  const int s0 = max(1, L - S);
-                  for (int s = s0; s <= min(S, L - 1); ++s) {
-                    const int t = L - s;
-                    mma_bf16(tbase + 128 * (L - G.lb),
-                             da0 + (uint64_t)(256 * (j * G.nd + s - 1)),
-                             db0 + (uint64_t)(256 * (j * G.nd + t - 1)), kIdesc,
-                             s == s0 ? acc0 : 1u);
+            const int k0 = c * csteps, k1 = min(k0 + csteps, p.nk16);
+            for (int ks = k0; ks < k1 && ok; ks += G.sps) {
+              const int nsteps = min(G.sps, k1 - ks);
+              if (!mbar_wait(full0 + 8 * stage, phase, st, p.wait_ns)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
+              const uint32_t sb = sa + p.stage_tiles * kDigitTile;
+              const uint64_t da0 = smem_desc_sw32(sa), db0 = smem_desc_sw32(sb);
+              for (int j = 0; j < nsteps; ++j) {
+                const uint32_t acc0 = (ks == k0 && j == 0) ? 0u : 1u;
+                if (SC == 8 && g == 0) {
+                  issue_step<2, 5, 8>(tbase, da0 + (uint64_t)(256 * 4 * j),
+                                      db0 + (uint64_t)(256 * 4 * j), acc0);
+                } else if (SC == 8) {
+                  issue_step<6, 9, 8>(tbase, da0 + (uint64_t)(256 * 8 * j),
+                                      db0 + (uint64_t)(256 * 8 * j), acc0);
+                } else {
+                  for (int L = G.lb; L <= G.le; ++L) {
+                    const int s0 = max(1, L - S);
+                    for (int s = s0; s <= min(S, L - 1); ++s) {
+                      const int t = L - s;
+                      mma_bf16(tbase + 128 * (L - G.lb),
+                               da0 + (uint64_t)(256 * (j * G.nd + s - 1)),
+                               db0 + (uint64_t)(256 * (j * G.nd + t - 1)), kIdesc,
+                               s == s0 ? acc0 : 1u);
+                    }
                   }
                 }
               }
+              mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
+              if (++stage == NST) { stage = 0; phase ^= 1; }
             }
-            mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
-            if (++stage == NST) { stage = 0; phase ^= 1; }
+            if (!ok) break;
+            mma_commit(accf);  // the group's (level, chunk) sums ready for the epilogue
+            ++q;
           }
-          if (!ok) break;
-          mma_commit(accf);  // the group's (level, chunk) sums ready for the epilogue
-          ++q;
         }
       }
       // wait for every MMA this thread issued before TMEM is released
       mma_commit(drain);
       mbar_drain_wait(drain, 0);
     }
+  }
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kEpiRegs));
     // ---------------------------------------------------------- epilogue
     const int quad = warp & 3;            // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;     // which kEpiCols columns of the tile
+    const int half = (warp - 4) >> 2;     // which kEpiCols columns of the tile
     const int row = quad * 32 + lane;
     const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16) + kEpiCols * half;
-    long long acc[kEpiCols];
-#pragma unroll
-    for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
     uint32_t q = 0;
     bool ok = true;
-    for (int g = 0; g < ngroups && ok; ++g) {
-      const Group G = group_of(p, S, g);
-      for (int c = 0; c < nchunks; ++c) {
-        int okw = 1;
-        if (lane == 0) okw = mbar_wait(accf, q & 1, st, p.wait_ns) ? 1 : 0;
-        okw = __shfl_sync(0xffffffffu, okw, 0);
-        __syncwarp();
-        if (!okw) { ok = false; break; }
-        tc_fence_after();
-        for (int L = G.lb; L <= G.le; ++L) {
-          const int sh = p.shift_top - p.beta * (L - 2);
-          const uint32_t lbase = lane_base + 128 * (L - G.lb);
+    for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+      int tm, tn;
+      tile_of(p, tile, tm, tn);
+      const int m0 = tm * OBM, n0 = tn * OBN;
+      long long acc[kEpiCols];
 #pragma unroll
-          for (int cb = 0; cb < kEpiCols / 16; ++cb) {
-            uint32_t a[16];
-            tmem_ld16(lbase + 16 * cb, a);
-            if (sh >= 0) {
+      for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const Group G = group_of(p, S, g);
+        for (int c = 0; c < nchunks; ++c) {
+          int okw = 1;
+          if (lane == 0) okw = mbar_wait(accf, q & 1, st, p.wait_ns) ? 1 : 0;
+          okw = __shfl_sync(0xffffffffu, okw, 0);
+          __syncwarp();
+          if (!okw) { ok = false; break; }
+          tc_fence_after();
+          for (int L = G.lb; L <= G.le; ++L) {
+            const int sh = p.shift_top - p.beta * (L - 2);
+            const uint32_t lbase = lane_base + 128 * (L - G.lb);
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                acc[16 * cb + j] += (long long)__float2int_rn(__uint_as_float(a[j])) << sh;
-            } else {
-              const int r = -sh;
-              const long long rnd = 1LL << (r - 1);
+            for (int cb = 0; cb < kEpiCols / 16; ++cb) {
+              uint32_t a[16];
+              tmem_ld16(lbase + 16 * cb, a);
+              if (sh >= 0) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                acc[16 * cb + j] += ((long long)__float2int_rn(__uint_as_float(a[j])) + rnd) >> r;
+                for (int j = 0; j < 16; ++j)
+                  acc[16 * cb + j] += (long long)__float2int_rn(__uint_as_float(a[j])) << sh;
+              } else {
+                const int r = -sh;
+                const long long rnd = 1LL << (r - 1);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  acc[16 * cb + j] += ((long long)__float2int_rn(__uint_as_float(a[j])) + rnd) >> r;
+              }
             }
           }
+          tc_fence_before();
+          mbar_arrive(acce);  // the accumulators may be overwritten from here on
+          ++q;
         }
-        tc_fence_before();
-        mbar_arrive(acce);
-        ++q;
       }
-    }
-    if (ok) {
-      // output: alpha 2^(e_i + f_j - 2 beta - shift_top) acc + beta C
+      if (!ok) break;
+      // output: alpha 2^(e_i + f_j - 2 beta - shift_top) acc + beta C, while
+      // the MMAs of the next tile already run
       const int64_t gi = m0 + row;
       if (gi < p.M) {
         const int ebase = p.ea[gi] - 2 * p.beta - p.shift_top;
-        const int eshift = p.alpha_pow2 ? p.alpha_exp : 0;
-        const bool aneg = p.alpha_pow2 && p.alpha_neg;
-        // C is read in groups of 8 before any of them is written, so the
-        // loads are in flight together instead of one DRAM round trip each
+        const int64_t gj0 = n0 + kEpiCols * half;
 #pragma unroll
-        for (int g = 0; g < kEpiCols / 8; ++g) {
-          double cv[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int jl = kEpiCols * half + 8 * g + u;
-            const int64_t gj = n0 + jl;
-            const bool live = gj < p.N && !(p.lower && gi < gj);
-            cv[u] = (live && p.betac != 0.0) ? p.C[gi + gj * p.ldc] : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int j = 8 * g + u;
-            const int jl = kEpiCols * half + j;
-            const int64_t gj = n0 + jl;
-            if (gj >= p.N || (p.lower && gi < gj)) continue;
-            double v;
-            if (fixed_to_double(acc[j], ebase + s_eb[jl] + eshift, aneg, v)) {
-              if (!p.alpha_pow2) v *= p.alpha;
-            } else {
-              v = p.alpha * ldexp((double)acc[j], ebase + s_eb[jl]);
-            }
-            if (p.betac == 1.0) v += cv[u];
-            else if (p.betac != 0.0) v = fma(p.betac, cv[u], v);
-            p.C[gi + gj * p.ldc] = v;
-          }
-        }
+        for (int g = 0; g < kEpiCols / 8; ++g)
+          store_out8(p, gi, gj0 + 8 * g, ebase, acc[8 * g], acc[8 * g + 1], acc[8 * g + 2],
+                     acc[8 * g + 3], acc[8 * g + 4], acc[8 * g + 5], acc[8 * g + 6],
+                     acc[8 * g + 7]);
       }
     }
   }
@@ -642,6 +674,22 @@ bool make_map_bf16(CUtensorMap *map, const void *base, int64_t inner, int64_t ro
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+namespace {
+// the digit planes as a 3-D tensor (K, rows, digit): boxes of `depth` digits x
+// 128 rows x 16 elements of K, 32-byte swizzle
+bool make_map3(CUtensorMap *map, void *base, int64_t rpad, int64_t kpad, int S, int depth) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rpad, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)(kpad * 2), (cuuint64_t)(rpad * kpad * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)OBM, (cuuint32_t)depth};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
 void ozaki_choose(int64_t K, int nslices, int &S, int &beta) {
   // beta: digit bits (exact chunk 2^(24 - 2 beta) elements); S digits cover
   // about 48 bits unless the caller asks for another count
@@ -677,16 +725,25 @@ void launch_rowmax(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk
 
 // ring stages: stage_tiles digit tiles per operand (all digits of one K step
 // for the widest group; several K steps for narrower groups)
-constexpr int kMaxSmem = 1024 + 3 * 2 * 8 * kDigitTile + (2 * 3 + 3) * 8 + 16 + OBN * 4;
+constexpr int kMaxSmem = 1024 + 3 * 2 * 8 * kDigitTile + (2 * 3 + 3) * 8 + 16;
 
 size_t oz_smem(int stage_tiles, int nstages) {
-  return 1024 + (size_t)nstages * 2 * stage_tiles * kDigitTile + (2 * nstages + 3) * 8 + 16 +
-         OBN * 4;
+  return 1024 + (size_t)nstages * 2 * stage_tiles * kDigitTile + (2 * nstages + 3) * 8 + 16;
 }
 
-cudaError_t launch_oz(int ntiles, const CUtensorMap &mA, const CUtensorMap &mB, const OzParams &p,
-                      cudaStream_t st) {
+cudaError_t launch_oz(int ntiles, const CUtensorMap &mA, const CUtensorMap &mB,
+                      const CUtensorMap *m3, const OzParams &p, cudaStream_t st) {
   const size_t smem = oz_smem(p.stage_tiles, p.nstages);
+  // persistent: one CTA per SM (at most one fits: 512 TMEM columns, ~197 KB
+  // of shared memory), each taking every grid-th tile
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 148;
+  }
+  const int grid = ntiles < nsm ? ntiles : nsm;
   if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
@@ -696,12 +753,20 @@ cudaError_t launch_oz(int ntiles, const CUtensorMap &mA, const CUtensorMap &mB, 
       e = cudaFuncSetAttribute(ozaki_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kMaxSmem);
     if (e != cudaSuccess) return e;
+    // the warpgroups' register split (setmaxnreg) adds up to exactly
+    // kLaunchRegs a thread; a build that launches with any other count is
+    // refused rather than run (an increase that cannot be met never returns)
+    cudaFuncAttributes fa8, fa0;
+    if (cudaFuncGetAttributes(&fa8, ozaki_gemm_kernel<8>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa0, ozaki_gemm_kernel<0>) != cudaSuccess ||
+        fa8.numRegs != kLaunchRegs || fa0.numRegs != kLaunchRegs)
+      return cudaErrorInvalidConfiguration;
     attr_set = true;
   }
   if (p.S == 8)
-    ozaki_gemm_kernel<8><<<ntiles, kThreads, smem, st>>>(mA, mB, p);
+    ozaki_gemm_kernel<8><<<grid, kThreads, smem, st>>>(mA, mB, m3[0], m3[1], m3[2], m3[3], p);
   else
-    ozaki_gemm_kernel<0><<<ntiles, kThreads, smem, st>>>(mA, mB, p);
+    ozaki_gemm_kernel<0><<<grid, kThreads, smem, st>>>(mA, mB, mA, mB, mA, mB, p);
   count_launch();
   return cudaGetLastError();
 }
@@ -748,8 +813,11 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
     slice_kernel<<<gs, 256, 0, st>>>(B, N, K, bsr, bsk, mb, eb, S, beta, DB, (int)Npad, (int)Kpad);
     count_launch();
   }
-  CUtensorMap mA, mB;
+  CUtensorMap mA, mB, m3[4];
   if (!make_map(&mA, DA, (int64_t)S * Mpad, Kpad) || !make_map(&mB, DB, (int64_t)S * Npad, Kpad))
+    return cudaErrorInvalidValue;
+  if (S == 8 && (!make_map3(&m3[0], DA, Mpad, Kpad, S, 4) || !make_map3(&m3[1], DB, Npad, Kpad, S, 4) ||
+                 !make_map3(&m3[2], DA, Mpad, Kpad, S, 8) || !make_map3(&m3[3], DB, Npad, Kpad, S, 8)))
     return cudaErrorInvalidValue;
   OzParams p;
   p.M = M;
@@ -764,11 +832,12 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.stage_tiles = S > 8 ? S : 8;
   p.nstages = S > 8 ? 2 : (tune_get("ozaki_stages", 3) == 2 ? 2 : 3);
   {
-    // level-2 chunk sums are below 2^(2 beta) kChunkK = 2^22, level L >= 3
-    // sums below 2^20 (L + 1) (a shift of beta (L - 2) bits further down):
-    // with nchunks chunks the int64 total stays below 2^(shift_top + 22 +
-    // lg) x 1.02 <= 2^61.03
-    const int nchunks = (p.nk16 + kChunkSteps - 1) / kChunkSteps;
+    // level-2 chunk sums are below 2^(2 beta) c <= 2^22.6 (c = 1536 elements),
+    // level L >= 3 sums below c 2^10 (L + 1) (a shift of beta (L - 2) bits
+    // further down): with nchunks <= 2^lg chunks the int64 total stays below
+    // 2^(shift_top + 22.6 + lg) x 1.02 <= 2^61.7
+    const int csteps = chunk_elems(S) / KS;
+    const int nchunks = (p.nk16 + csteps - 1) / csteps;
     int lg = 0;
     while ((1 << lg) < nchunks) ++lg;
     p.shift_top = 39 - lg;
@@ -792,8 +861,9 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.no_loads = tune_get("test_wait_timeout", 0) != 0 ? 1 : 0;
   p.wait_ns = p.no_loads ? 1000000ull : kWaitNs;  // 1 ms in the failure-path test
   const int tiles_m = (int)(Mpad / OBM);
-  int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
-  return launch_oz(ntiles, mA, mB, p, st);
+  const int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
+  p.ntiles = ntiles;
+  return launch_oz(ntiles, mA, mB, m3, p, st);
 }
 
 }  // namespace qmlgb

@@ -52,12 +52,14 @@ def _dgemm_entries(lib):
     return {ln.split()[0] for ln in buf.value.decode().splitlines() if ln.startswith("dgemm:")}
 
 
-def _noalloc(lib, A):
-    out = _colmajor_dev(A)
-    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
-    st = lib.qml_potrf_noalloc(A.shape[0], out.data_ptr(), A.shape[0], ld.data_ptr(), _stream())
+def _dev_pair(A):
+    return _colmajor_dev(A), torch.zeros(1, dtype=torch.float64, device="cuda")
+
+
+def _noalloc(lib, out, ld):
+    n = out.shape[0]
+    st = lib.qml_potrf_noalloc(n, out.data_ptr(), n, ld.data_ptr(), _stream())
     assert st == 0, lib.qml_last_error()
-    return out, ld
 
 
 def _potrf(lib, A):
@@ -76,13 +78,15 @@ def _check_pair(lib, n, seed):
     device memory for code and for the static scratch array itself -- and
     must leave free device memory unchanged.  Both match qml_potrf."""
     mats = [_spd(n, seed), _spd(n, seed + 1)]
+    out0, ld0 = _dev_pair(mats[0])
+    out1, ld1 = _dev_pair(mats[1])  # every buffer exists before memory is read
     torch.cuda.synchronize()
     tuned0 = _dgemm_entries(lib)
-    out0, ld0 = _noalloc(lib, mats[0])
+    _noalloc(lib, out0, ld0)
     assert _dgemm_entries(lib) == tuned0, "qml_potrf_noalloc ran the allocating tile autotuner"
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
-    out1, ld1 = _noalloc(lib, mats[1])
+    _noalloc(lib, out1, ld1)
     free1 = torch.cuda.mem_get_info()[0]
     assert free1 >= free0, (free0, free1)
     for A, out, ld in ((mats[0], out0, ld0), (mats[1], out1, ld1)):
