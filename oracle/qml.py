@@ -227,6 +227,85 @@ def qml_for(wl, Y, maps=None, want_bias=True, edges=None):
     return qml(Y, wl.cl_fid, wl.comps, wl.lmin, wl.lmax, wl.N(), wl.spec, maps, want_bias, edges)
 
 
+def lambda_dense(cl, comps, lmin: int, lmax: int) -> np.ndarray:
+    """The (k x k) matrix Lambda of Eq. S_factored in the mode order of Y:
+    entry (a k0 + i, b k0 + i) = Lambda_l[a, b] for the modes i of multipole l."""
+    k0 = (lmax + 1) ** 2 - lmin ** 2
+    nc = len(comps)
+    lam = lambda_blocks(cl, comps, lmin, lmax)
+    lm = _l_of_mode(lmin, lmax) - lmin
+    L = np.zeros((nc * k0, nc * k0))
+    idx = np.arange(k0)
+    for a in range(nc):
+        for b in range(nc):
+            L[a * k0 + idx, b * k0 + idx] = lam[lm, a, b]
+    return L
+
+
+def qml_harmonic(Y, cl_fid, comps, lmin, lmax, N, spec, maps=None, want_bias=True, edges=None):
+    """The same estimator in the harmonic basis (Sects. 2.3.2-2.3.3 with the
+    stable evaluation of App. C.3), for the pixel-vs-harmonic cross-check.
+
+    M = Y^T N^-1 Y (the noise-weighted Gramian), and with Lambda the fiducial
+    spectrum matrix the projected inverse Y^T C^-1 Y = M - M K^-1 M,
+    K = Lambda^-1 + M (Eqs. smw, K_kernel, projected_inv_smw), is evaluated
+    without the subtraction as M (I + Lambda M)^-1 (Eq. smw_stable), one linear
+    solve with (I + Lambda M)^T; the weighted data Y^T C^-1 d =
+    (I + M Lambda)^-1 Y^T N^-1 d (Eq. smw_stable_data); the noise bias from
+    Cov(w | noise) = A M A^T with A = (I + M Lambda)^-1 (Eq. smw_stable_A).
+    With multipole switching N is N_eff (Sect. 2.3.4).
+    """
+    k = Y.shape[1]
+    cN = sla.cho_factor(N, lower=True)
+    NiY = sla.cho_solve(cN, Y)
+    M = Y.T @ NiY
+    M = 0.5 * (M + M.T)
+    Lam = lambda_dense(cl_fid, comps, lmin, lmax)
+    I = np.eye(k)
+    W = np.linalg.solve((I + Lam @ M).T, M.T).T
+    W = 0.5 * (W + W.T)
+    F = fisher_from_W(W, spec, comps, lmin, lmax, edges)
+    out = {"F": F, "W": W}
+    A = np.linalg.inv(I + M @ Lam)
+    if want_bias:
+        out["b"] = 0.5 * trace_selector(A @ M @ A.T, spec, comps, lmin, lmax, edges)
+    if maps is not None:
+        maps = maps.reshape(maps.shape[0], -1)
+        w = A @ (NiY.T @ maps)
+        y = quad_selector(w, spec, comps, lmin, lmax, edges)
+        out["w"] = w
+        out["y"] = y
+        if want_bias:
+            q = y - out["b"][:, None]
+            out["q"] = q
+            dec, decor, conv, Fm12 = normalisations(F, q)
+            out.update(cl_deconv=dec, cl_decorr=decor, q_conv=conv, F_inv_sqrt=Fm12)
+    return out
+
+
+def loglike_harmonic(Y, cl, comps, lmin, lmax, N, d):
+    """lnL of Eq. pixel_likelihood through the determinant lemma and the SMW
+    quadratic form (Eqs. logdet, quad_form_smw; App. C.2):
+    ln|C| = ln|N| + ln|I + Lambda M|, d^T C^-1 d = d^T N^-1 d - v^T K^-1 v with
+    v = Y^T N^-1 d and K^-1 = (Lambda^-1 + M)^-1 = Lambda (I + M Lambda)^-1.
+    Returns (lnL, chi2, logdet) like loglike()."""
+    d = d.reshape(d.shape[0], -1)
+    cN = sla.cho_factor(N, lower=True)
+    lnN = 2.0 * np.sum(np.log(np.abs(np.diag(cN[0]))))
+    NiY = sla.cho_solve(cN, Y)
+    M = Y.T @ NiY
+    M = 0.5 * (M + M.T)
+    Lam = lambda_dense(cl, comps, lmin, lmax)
+    I = np.eye(Y.shape[1])
+    sign, lnK = np.linalg.slogdet(I + Lam @ M)
+    assert sign > 0
+    v = NiY.T @ d
+    dNd = np.sum(d * sla.cho_solve(cN, d), axis=0)
+    chi2 = dNd - np.sum(v * (Lam @ np.linalg.solve(I + M @ Lam, v)), axis=0)
+    logdet = lnN + lnK
+    return -0.5 * (chi2 + logdet), chi2, logdet
+
+
 def cross_qml(Y, cl_fid, comps, lmin, lmax, N1, N2, spec, d1=None, d2=None):
     """Cross-QML of two data sets on one pixel set, filtered independently
     (Eq. q_cross): q_x = 1/2 d1^T C1^-1 P_a C2^-1 d2 with C_i = S + N_i and

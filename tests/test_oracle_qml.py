@@ -252,7 +252,7 @@ def test_mutation_bin_range_off_by_one_is_caught(monkeypatch):
         test_P10_binning_vs_brute()
 
 
-# ---- P11: multipole switching (Sect. 2.3.4, Eqs. C_switched, N_eff) -------
+# ---- P17: multipole switching (Sect. 2.3.4, Eqs. C_switched, N_eff) -------
 def _switch_setup():
     """Signal over l = 2..7, inference window l = 3..5 (one multipole fixed
     below it, two above), TQU with all six spectra."""
@@ -268,7 +268,7 @@ def _switch_setup():
     return t, rs, rf, win, out
 
 
-def test_P11_switching_is_the_window_of_the_full_estimator():
+def test_P17_switching_is_the_window_of_the_full_estimator():
     """C is the same matrix with or without switching, so F and y on the
     window equal the window blocks of the full-range estimator, and the noise
     bias (with N_eff) gains exactly the fixed signal's share:
@@ -283,7 +283,7 @@ def test_P11_switching_is_the_window_of_the_full_estimator():
     assert np.abs(rs["b"] - bref).max() <= 1e-11 * np.abs(bref).max()
 
 
-def test_P11_switching_expectation_identity():
+def test_P17_switching_expectation_identity():
     """1/2 tr[C^-1 P_a] = (F C_fid)_a + b_a on the window (P7 with N_eff):
     exact, because C = sum_{a in window} C_a P_a + N_eff."""
     t, rs, rf, win, out = _switch_setup()
@@ -292,7 +292,7 @@ def test_P11_switching_expectation_identity():
     assert np.abs(lhs - (rs["F"] @ cwin + rs["b"])).max() <= 1e-10 * np.abs(lhs).max()
 
 
-def test_P11_neff_vs_brute():
+def test_P17_neff_vs_brute():
     """N_eff built from the dense pixel derivatives P_l of the brute-force
     responses (Eq. N_eff term by term), independent of Y."""
     t, rs, rf, win, out = _switch_setup()
@@ -305,7 +305,7 @@ def test_P11_neff_vs_brute():
     assert np.abs(rs["N_eff"] - Neff).max() <= 1e-12 * np.abs(Neff).max()
 
 
-def test_P11_no_switching_is_plain_qml():
+def test_P17_no_switching_is_plain_qml():
     """A signal range equal to the window leaves N_eff = N: plain QML (up to
     the rounding of products over a copied Y)."""
     t = _tiny(has_P=False)
@@ -328,7 +328,7 @@ def test_mutation_switching_drops_high_side_is_caught(monkeypatch):
 
     monkeypatch.setattr(qml, "signal_cov", no_high)
     with pytest.raises(AssertionError):
-        test_P11_neff_vs_brute()
+        test_P17_neff_vs_brute()
 
 
 # ---- P16: cross-QML (Eq. q_cross) -----------------------------------------
@@ -399,3 +399,67 @@ def test_mutation_cross_filters_both_with_C1_is_caught(monkeypatch):
     monkeypatch.setattr(qml, "total_cov", same)
     with pytest.raises(AssertionError):
         test_P16_cross_vs_brute()
+
+
+# ---- P11: harmonic basis (SMW) against the pixel basis (Sects. 2.3.2-2.3.3,
+# App. C.2-C.3); the paper's own cross-check agrees to ~1e-13 on F ---------
+@pytest.mark.parametrize("has_T,has_P", [(True, False), (False, True), (True, True)])
+def test_P11_harmonic_basis_equals_pixel_basis(has_T, has_P):
+    """F, b, y and the three normalisations from the SMW stable form equal the
+    pixel-basis definition (C factored directly), all six spectra with non-zero
+    TB and EB; and lnL through the determinant lemma equals the Cholesky
+    log-likelihood."""
+    t = _tiny(has_T, has_P, nside=4, lmax=7)
+    rp = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"], maps=t["d"])
+    rh = qml.qml_harmonic(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["spec"],
+                          maps=t["d"])
+    for key in ("F", "b", "y", "cl_deconv", "q_conv"):
+        assert np.abs(rh[key] - rp[key]).max() <= 1e-11 * np.abs(rp[key]).max(), key
+    lp = qml.loglike(rp["C"], t["d"])
+    lh = qml.loglike_harmonic(t["Y"], t["cl"], t["comps"], 2, t["lmax"], t["N"], t["d"])
+    for a, b in zip(lh, lp):
+        assert np.abs(np.asarray(a) - np.asarray(b)).max() <= 1e-11 * np.abs(np.asarray(b)).max()
+
+
+def test_P11_harmonic_basis_high_signal_to_noise():
+    """Noise scaled down by 1e9 (the cosmic-variance-limited regime of
+    App. C.3): the stable form keeps F within 1e-11 of the pixel basis, while
+    the subtractive form M - M K^-1 M loses digits to cancellation."""
+    t = _tiny(True, True, nside=4, lmax=7)
+    N = t["N"] * 1e-9
+    rp = qml.qml(t["Y"], t["cl"], t["comps"], 2, t["lmax"], N, t["spec"])
+    rh = qml.qml_harmonic(t["Y"], t["cl"], t["comps"], 2, t["lmax"], N, t["spec"])
+    assert np.abs(rh["F"] - rp["F"]).max() <= 1e-11 * np.abs(rp["F"]).max()
+    # the subtractive form on the same inputs
+    M = t["Y"].T @ np.linalg.solve(N, t["Y"])
+    Lam = qml.lambda_dense(t["cl"], t["comps"], 2, t["lmax"])
+    K = np.linalg.inv(Lam) + M
+    Wsub = M - M @ np.linalg.solve(K, M)
+    Fsub = qml.fisher_from_W(0.5 * (Wsub + Wsub.T), t["spec"], t["comps"], 2, t["lmax"])
+    assert np.abs(Fsub - rp["F"]).max() > 100 * np.abs(rh["F"] - rp["F"]).max()
+
+
+def test_P11_harmonic_with_switching_equals_switched_pixel():
+    """With N_eff in place of N (Sect. 2.3.4) the harmonic basis on the window
+    modes reproduces the switched pixel-basis estimator."""
+    t, rs, rf, win, out = _switch_setup()
+    wcols, lo, hi = qml.window_columns(2, 7, 3, 5, len(t["comps"]))
+    rh = qml.qml_harmonic(t["Y"][:, wcols], t["cl"], t["comps"], 3, 5, rs["N_eff"], t["spec"],
+                          maps=t["d"])
+    for key in ("F", "b", "y", "cl_deconv"):
+        assert np.abs(rh[key] - rs[key]).max() <= 1e-11 * np.abs(rs[key]).max(), key
+
+
+def test_mutation_harmonic_lambda_transposed_is_caught(monkeypatch):
+    """Using (I + M Lambda) where the stable form needs (I + Lambda M) for the
+    projected inverse changes F once Lambda has off-diagonal (TE, TB, EB)
+    entries; the pixel-basis pin catches it."""
+    orig = qml.lambda_dense
+
+    def skewed(cl, comps, lmin, lmax):
+        L = orig(cl, comps, lmin, lmax)
+        return np.triu(L) + 0.5 * np.tril(L, -1)   # not the symmetric Lambda
+
+    monkeypatch.setattr(qml, "lambda_dense", skewed)
+    with pytest.raises(AssertionError):
+        test_P11_harmonic_basis_equals_pixel_basis(True, True)
