@@ -97,7 +97,29 @@ typedef struct {
    * on the binned F. */
   int32_t nbins;
   const int32_t *bin_edges;
+  /* Multipole switching (Sect. 2.3.4, Eqs. C_switched and N_eff), read by
+   * qml_fisher only: the signal band [lmin_sig, lmax_sig] contains the
+   * inference window [lmin, lmax]; 0 means equal to the window.  The fiducial
+   * signal outside the window is held fixed (in C, or in N_eff for the
+   * harmonic basis) and only the window is estimated.  transfer_* and cl_fid
+   * then hold lmax_sig + 1 entries per field and spectrum (cl_fid is
+   * [6][lmax_sig + 1]).  2 <= lmin_sig <= lmin, lmax <= lmax_sig <= 2048. */
+  int32_t lmin_sig, lmax_sig;
+  /* Computation basis of qml_fisher (Sect. 2.3, Sect. 3 "Computation
+   * basis"): QML_BASIS_PIXEL, QML_BASIS_HARMONIC or QML_BASIS_AUTO. */
+  int32_t basis;
 } qml_problem;
+
+typedef enum {
+  QML_BASIS_PIXEL = 0,     /* C = Y Lambda Y^T + N factored by Cholesky; W = X^T X */
+  QML_BASIS_HARMONIC = 1,  /* SMW: M = Y^T N^-1 Y, the inner matrix Kt = I + L^T M L
+                              (Lambda = L L^T per (l, m)) factored in float64, and
+                              W = L^-T Kt^-1 L^T M, the subtraction-free form of
+                              M - M K^-1 M (App. C.3); needs the fiducial Lambda
+                              positive definite at every window multipole */
+  QML_BASIS_AUTO = 2       /* the cheaper of the two by this library's cost model:
+                              harmonic when 3 n^2 > 7 k^2 (n pixels, k window modes) */
+} qml_basis;
 
 typedef struct qml_plan qml_plan;   /* opaque; owned by the library */
 
@@ -130,10 +152,15 @@ qml_status qml_synthesize(const qml_problem *prob, const double *alm, const doub
  * If plan is not NULL, *plan receives a plan holding L, X, F, the noise bias
  * and the normalisation matrices for qml_estimate (the analogue of handing a
  * Fisher object to the spectra stage).  na = nspec (lmax - lmin + 1) must
- * not exceed 2048 (QML_EINVAL).  With prob->nbins > 0 (Sect. 2.4) F is the
+ * not exceed 2048 (QML_EINVAL).  prob->basis selects the pixel or the
+ * harmonic (SMW) evaluation (Sect. 2.3.2); both give the same F, noise bias
+ * and estimates.  With a signal band wider than the window (lmin_sig,
+ * lmax_sig) the out-of-window fiducial signal is part of C (pixel basis) or
+ * of N_eff (harmonic basis) and F covers the window.  With prob->nbins > 0 (Sect. 2.4) F is the
  * binned Fisher matrix, na_b x na_b with na_b = nspec nbins, and the plan's
  * noise bias and normalisations are binned too.  Errors: QML_ENOTSPD if C is
- * not positive definite; QML_EINVAL for bad bin edges. */
+ * not positive definite; QML_EINVAL for bad bin edges, a bad signal band, or
+ * (harmonic basis) a fiducial block that is not positive definite. */
 qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan, void *stream);
 
 /* Quadratic estimates for nsims maps (n x nsims) against a plan from
@@ -150,6 +177,26 @@ qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims,
 
 /* Release a plan (NULL is accepted). */
 void qml_plan_free(qml_plan *plan);
+
+/* Cross-QML of two data sets observed through the same pixels (Sect. 2.2,
+ * Eq. q_cross): plan1 and plan2 come from qml_fisher on problems that differ
+ * only in their noise N_i (same pixels, fields, window and spectra; per-l,
+ * no bins; either basis or precision).  Each data set is filtered by its own
+ * C_i = S + N_i: W_i = Y^T C_i^-1 Y, w_i = Y^T C_i^-1 d_i, and
+ *   Wx (na x na)     = 1/2 tr[C1^-1 P_a C2^-1 P_b]  (mode-mixing matrix,
+ *                      not symmetric in general),
+ *   q  (na x nsims)  = 1/2 d1^T C1^-1 P_a C2^-1 d2,
+ *   cl (na x nsims)  = Wx^-1 q  (LU with partial pivoting).
+ * With independent noise there is no noise bias.  maps1, maps2 are n x nsims;
+ * nsims = 0 computes only Wx (maps, q, cl may then be NULL); q and cl may be
+ * NULL.  Errors: QML_EINVAL for plans that do not match, QML_ENOTSPD when Wx
+ * is singular. */
+qml_status qml_cross(qml_plan *plan1, qml_plan *plan2, const double *maps1, const double *maps2,
+                     int32_t nsims, double *Wx, double *q, double *cl, void *stream);
+
+/* The basis a plan was computed in (QML_BASIS_PIXEL or QML_BASIS_HARMONIC;
+ * -1 for NULL), e.g. to see what QML_BASIS_AUTO chose. */
+int32_t qml_plan_basis(const qml_plan *plan);
 
 /* Gaussian pixel log-likelihood of nmaps maps (n x nmaps) at spectra cl_theta
  * ([6][lmax+1]): lnL = -1/2 (d^T C^-1 d + ln|C|), constant dropped

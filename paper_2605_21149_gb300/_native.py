@@ -15,6 +15,7 @@ c_char_p = ctypes.c_char_p
 
 QML_OK, QML_EINVAL, QML_ENOTSPD, QML_ENOMEM, QML_ECUDA, QML_ETIMEOUT = range(6)
 QML_FP64, QML_SPLIT_BF16 = 0, 1
+QML_BASIS_PIXEL, QML_BASIS_HARMONIC, QML_BASIS_AUTO = 0, 1, 2
 STATUS_NAMES = {0: "QML_OK", 1: "QML_EINVAL", 2: "QML_ENOTSPD", 3: "QML_ENOMEM", 4: "QML_ECUDA",
                 5: "QML_ETIMEOUT"}
 
@@ -31,6 +32,7 @@ class QmlProblem(ctypes.Structure):
         ("cl_fid", c_void_p), ("N", c_void_p),
         ("precision", c_int32), ("nslices", c_int32),
         ("nbins", c_int32), ("bin_edges", c_void_p),
+        ("lmin_sig", c_int32), ("lmax_sig", c_int32), ("basis", c_int32),
     ]
 
 
@@ -51,6 +53,9 @@ SIGNATURES = {
     "qml_estimate": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_void_p, c_void_p]),
     "qml_plan_free": (None, [c_void_p]),
+    "qml_plan_basis": (c_int32, [c_void_p]),
+    "qml_cross": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                            c_void_p, c_void_p]),
     "pix_loglike": (c_int32, [ctypes.POINTER(QmlProblem), c_void_p, c_void_p, c_int32, c_void_p,
                               c_void_p, c_void_p, c_void_p]),
     "pix_loglike_batch": (c_int32, [ctypes.POINTER(LnlMask), c_int32, c_int32, c_void_p, c_void_p,

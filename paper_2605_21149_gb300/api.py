@@ -23,6 +23,10 @@ except ImportError:  # pragma: no cover - torch is part of the supported setup
     torch = None
 
 
+BASIS_PIXEL, BASIS_HARMONIC, BASIS_AUTO = (nat.QML_BASIS_PIXEL, nat.QML_BASIS_HARMONIC,
+                                           nat.QML_BASIS_AUTO)
+
+
 class QMLError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{nat.STATUS_NAMES.get(status, status)}: {msg}")
@@ -101,7 +105,8 @@ class Problem:
 
     def __init__(self, lmin, lmax, *, theta_T=None, phi_T=None, theta_P=None, phi_P=None,
                  transfer_T=None, transfer_P=None, spec=("TT",), cl_fid=None, N=None,
-                 precision=nat.QML_FP64, nslices=0, bin_edges=None):
+                 precision=nat.QML_FP64, nslices=0, bin_edges=None, lsig=None,
+                 basis=nat.QML_BASIS_PIXEL):
         self._keep = []
         has_T = theta_T is not None
         has_P = theta_P is not None
@@ -135,6 +140,11 @@ class Problem:
         p.N = _mat(N, self.n, self.n, self._keep) if N is not None else None
         p.precision = int(precision)
         p.nslices = int(nslices)
+        # multipole switching: signal band (lmin_sig, lmax_sig) around the window;
+        # transfer and cl_fid then cover it (cl_fid is [6][lmax_sig + 1])
+        if lsig is not None:
+            p.lmin_sig, p.lmax_sig = int(lsig[0]), int(lsig[1])
+        p.basis = int(basis)
         if edges is not None:
             self._keep.append(edges)
             p.nbins = len(edges) - 1
@@ -142,8 +152,11 @@ class Problem:
         self._p = p
 
     @classmethod
-    def from_workload(cls, wl, device=True, precision=nat.QML_FP64, nslices=0, bin_edges=None):
-        """Problem from a synth.Workload; device=True puts every array on cuda:0."""
+    def from_workload(cls, wl, device=True, precision=nat.QML_FP64, nslices=0, bin_edges=None,
+                      window=None, basis=nat.QML_BASIS_PIXEL):
+        """Problem from a synth.Workload; device=True puts every array on cuda:0.
+        window=(lmin, lmax) inside the workload's band estimates only that
+        window, the workload's band being the signal band (multipole switching)."""
         def conv(a):
             if a is None or len(a) == 0:
                 return None
@@ -151,7 +164,9 @@ class Problem:
                 return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
             return np.ascontiguousarray(a, dtype=np.float64)
         N = wl.N()
-        return cls(wl.lmin, wl.lmax,
+        lmin, lmax = (wl.lmin, wl.lmax) if window is None else window
+        lsig = None if window is None else (wl.lmin, wl.lmax)
+        return cls(lmin, lmax,
                    theta_T=conv(wl.theta_T) if wl.has_T else None,
                    phi_T=conv(wl.phi_T) if wl.has_T else None,
                    theta_P=conv(wl.theta_P) if wl.has_P else None,
@@ -160,7 +175,8 @@ class Problem:
                    transfer_P=conv(wl.transfer_P) if wl.has_P else None,
                    spec=wl.spec, cl_fid=conv(wl.cl_fid.reshape(-1)),
                    N=(torch.as_tensor(N, device="cuda") if device else N),
-                   precision=precision, nslices=nslices, bin_edges=bin_edges)
+                   precision=precision, nslices=nslices, bin_edges=bin_edges, lsig=lsig,
+                   basis=basis)
 
     @property
     def ref(self):
@@ -207,6 +223,11 @@ class Plan:
         out["b"] = out["b"][:, 0]
         return out
 
+    @property
+    def basis(self):
+        """QML_BASIS_PIXEL or QML_BASIS_HARMONIC: the basis qml_fisher used."""
+        return _lib().qml_plan_basis(self._h)
+
     def free(self):
         if self._h:
             _lib().qml_plan_free(self._h)
@@ -226,6 +247,26 @@ def fisher(prob: Problem, keep_plan: bool = True):
     _check(_lib().qml_fisher(prob.ref, _ptr(F), ctypes.byref(h) if keep_plan else None,
                              _stream(prob.device)))
     return F, (Plan(h, prob) if keep_plan else None)
+
+
+def cross(plan1: "Plan", plan2: "Plan", maps1=None, maps2=None):
+    """Cross-QML (qml_cross): dict Wx (na x na) and, with maps, q and cl
+    (na x nsims) for the columns of maps1 / maps2 filtered by each plan's C."""
+    keep = []
+    pr = plan1.prob
+    dev = pr.device
+    nsims = 0 if maps1 is None else (maps1.shape[1] if maps1.ndim == 2 else 1)
+    out = {"Wx": _empty(pr.na, pr.na, dev)}
+    d1 = d2 = None
+    if nsims:
+        d1 = _mat(maps1, pr.n, nsims, keep)
+        d2 = _mat(maps2, pr.n, nsims, keep)
+        out["q"] = _empty(pr.na, nsims, dev)
+        out["cl"] = _empty(pr.na, nsims, dev)
+    _check(_lib().qml_cross(plan1._h, plan2._h, d1, d2, nsims, _ptr(out["Wx"]),
+                            _ptr(out["q"]) if nsims else None, _ptr(out["cl"]) if nsims else None,
+                            _stream(dev)))
+    return out
 
 
 def loglike(prob: Problem, cl_theta, maps):

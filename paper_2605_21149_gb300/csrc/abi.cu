@@ -143,11 +143,16 @@ struct Call {
       if (hs.info > 0)
         snprintf(buf, sizeof buf, "matrix not positive definite (Cholesky pivot at column %d)",
                  hs.info - 1);
+      else if (hs.info == -2)
+        snprintf(buf, sizeof buf, "cross-spectrum mixing matrix is singular");
       else
         snprintf(buf, sizeof buf, "Fisher matrix not positive definite");
       return fail(QML_ENOTSPD, buf);
     }
     if (hs.code == QML_ETIMEOUT) return fail(QML_ETIMEOUT, "device wait exceeded its budget");
+    if (hs.code == QML_EINVAL)
+      return fail(QML_EINVAL, "harmonic basis: the fiducial spectrum block at l = " +
+                                  std::to_string(hs.info - 1) + " is not positive definite");
     if (hs.code != 0) return fail(QML_ECUDA, "device status " + std::to_string(hs.code));
     return QML_OK;
   }
@@ -162,7 +167,11 @@ struct Dims {
   int nc = 0, comps[3] = {0, 0, 0}, pos[3] = {-1, -1, -1};
   int lmin = 0, lmax = 0, nl = 0, k0 = 0, k = 0;
   int nspec_full = 0, full_ids[6];
+  int lsig0 = 0, lsig1 = 0;  // signal band (= the window unless switching)
 };
+
+// modes of one field over the multipoles l0 .. l1
+inline int band_k0(int l0, int l1) { return (l1 + 1) * (l1 + 1) - l0 * l0; }
 
 qml_status check_problem(const qml_problem *p, Dims &d, bool need_spec, bool need_N) {
   if (!p) return fail(QML_EINVAL, "problem is NULL");
@@ -176,6 +185,15 @@ qml_status check_problem(const qml_problem *p, Dims &d, bool need_spec, bool nee
   if (p->precision != QML_FP64 && p->precision != QML_SPLIT_BF16)
     return fail(QML_EINVAL, "precision must be QML_FP64 or QML_SPLIT_BF16");
   if (p->nslices < 0 || p->nslices > 10) return fail(QML_EINVAL, "nslices must be 0..10");
+  if (p->basis < QML_BASIS_PIXEL || p->basis > QML_BASIS_AUTO)
+    return fail(QML_EINVAL, "basis must be QML_BASIS_PIXEL, QML_BASIS_HARMONIC or QML_BASIS_AUTO");
+  d.lsig0 = p->lmin_sig > 0 ? p->lmin_sig : p->lmin;
+  d.lsig1 = p->lmax_sig > 0 ? p->lmax_sig : p->lmax;
+  if (p->lmin_sig < 0 || p->lmax_sig < 0 || d.lsig0 < 2 || d.lsig0 > p->lmin ||
+      d.lsig1 < p->lmax || d.lsig1 > 2048)
+    return fail(QML_EINVAL,
+                "signal band must contain the window: 2 <= lmin_sig <= lmin <= lmax <= lmax_sig "
+                "<= 2048");
   d.nT = p->has_T ? p->npix_T : 0;
   d.nP = p->has_P ? p->npix_P : 0;
   d.n = d.nT + 2 * d.nP;
@@ -228,9 +246,12 @@ struct Staged {
   const double *cl = nullptr, *N = nullptr;
 };
 
+// transfer arrays cover the signal band (lsig1 + 1 entries); cl holds
+// 6 x cl_ld entries (cl_ld = 0: lmax + 1)
 bool stage_problem(Call &c, const qml_problem *p, const Dims &d, Staged &s, const double *cl,
-                   bool need_N) {
-  const size_t L = (size_t)d.lmax + 1;
+                   bool need_N, size_t cl_ld = 0) {
+  const size_t L = (size_t)d.lsig1 + 1;
+  if (cl_ld == 0) cl_ld = (size_t)d.lmax + 1;
   s.y.has_T = p->has_T;
   s.y.has_P = p->has_P;
   s.y.npix_T = d.nT;
@@ -243,8 +264,8 @@ bool stage_problem(Call &c, const qml_problem *p, const Dims &d, Staged &s, cons
   s.y.theta_P = p->has_P ? c.in(p->theta_P, d.nP, "theta_P") : nullptr;
   s.y.phi_P = p->has_P ? c.in(p->phi_P, d.nP, "phi_P") : nullptr;
   s.y.transfer_P = p->has_P ? c.in(p->transfer_P, L, "transfer_P") : nullptr;
-  s.y.coef = c.alloc<unsigned char>(ybuild_coef_bytes(d.lmax), "recurrence coefficients");
-  if (cl) s.cl = c.in(cl, 6 * L, "cl");
+  s.y.coef = c.alloc<unsigned char>(ybuild_coef_bytes(d.lsig1), "recurrence coefficients");
+  if (cl) s.cl = c.in(cl, 6 * cl_ld, "cl");
   if (need_N) s.N = c.in(p->N, (size_t)d.n * d.n, "N");
   return c.err == QML_OK;
 }
@@ -287,6 +308,21 @@ void trsm_blocked(Call &c, const double *L, int64_t n, int64_t lda, const double
     if (j + jb < n)
       launch_dgemm(0, 0, n - j - jb, nrhs, jb, -1.0, L + (j + jb) + j * lda, lda, B + j, ldb, 1.0,
                    B + j + jb, ldb, 0, c.status, c.st);
+  }
+}
+
+// B <- L^-T B (backward substitution with the diagonal-block inverses):
+// from the last block up, B_j <- Linv_j^T B_j, then B_0..j-1 -= L_j,0..j-1^T B_j.
+void trsm_blocked_t(Call &c, const double *L, int64_t n, int64_t lda, const double *Linv,
+                    double *B, int64_t nrhs, int64_t ldb) {
+  const int64_t nb = (n + kNB - 1) / kNB;
+  for (int64_t bi = nb - 1; bi >= 0; --bi) {
+    const int64_t j = bi * kNB;
+    const int64_t jb = (n - j) < kNB ? (n - j) : kNB;
+    const double *Lb = Linv + bi * kNB * kNB;
+    launch_dgemm(1, 0, jb, nrhs, jb, 1.0, Lb, kNB, B + j, ldb, 0.0, B + j, ldb, 0, c.status, c.st);
+    if (j > 0)
+      launch_dgemm(1, 0, j, nrhs, jb, -1.0, L + j, lda, B + j, ldb, 1.0, B, ldb, 0, c.status, c.st);
   }
 }
 
@@ -462,6 +498,29 @@ void build_C_split(Call &c, Split &sp, const Staged &s, const Dims &d, double *Y
   sp.gemm(0, 1, d.n, d.n, d.k, 1.0, Y, d.n, Y, d.n, 1.0, C, d.n, 1);
 }
 
+// C += Y_b Lambda_b Y_b^T (lower triangle) for the multipoles l0 .. l1 of the
+// fiducial spectra s.cl ([6][ldcl]): Y_b built into the scratch Y (n x
+// nc band_k0(l0, l1)), mixed by the per-(l, m) factors of Lambda, and one
+// lower-triangle product (split precision when spl is given).  The pixel-basis
+// C over a signal band wider than the window, and the fixed-signal terms of
+// N_eff (Eq. N_eff), are sums of such bands.
+void add_band_signal(Call &c, Split *spl, const Staged &s, const Dims &d, int l0, int l1,
+                     int ldcl, double *Y, double *C) {
+  const int k0b = band_k0(l0, l1), kb = d.nc * k0b;
+  double *lamL = c.alloc<double>((size_t)(l1 - l0 + 1) * d.nc * d.nc, "lambda factors");
+  if (!lamL) return;
+  YArgs ya = s.y;
+  ya.lmin = l0;
+  ya.lmax = l1;
+  launch_ybuild(ya, Y, d.n, c.st);
+  launch_lambda_factor(s.cl, l0, l1, d.nc, d.comps, lamL, c.st, ldcl);
+  launch_mix_lambda(Y, d.n, d.n, d.nc, k0b, l0, l1, lamL, c.st);
+  if (spl)
+    spl->gemm(0, 1, d.n, d.n, kb, 1.0, Y, d.n, Y, d.n, 1.0, C, d.n, 1);
+  else
+    launch_dgemm(0, 1, d.n, d.n, kb, 1.0, Y, d.n, Y, d.n, 1.0, C, d.n, 1, c.status, c.st);
+}
+
 }  // namespace
 
 // ======================================================================
@@ -499,7 +558,72 @@ struct qml_plan {
   int na_l = 0;
   bool binned = false;
   int *bstart = nullptr, *bcount = nullptr;
+  // harmonic basis (Sect. 2.3.2): L holds the factor of N (or N_eff), X holds
+  // U = L_N^-1 Y; LK the float64 factor of Kt = I + L_Lambda^T M L_Lambda with
+  // its 64-block inverses, lamL / lamLi the per-l factors of Lambda and their
+  // inverses
+  bool harmonic = false;
+  double *LK = nullptr, *LKinv = nullptr, *lamL = nullptr, *lamLi = nullptr;
 };
+
+namespace {
+
+// Harmonic basis: W (k x k) holds M = Y^T N^-1 Y on entry and W = M (I +
+// Lambda M)^-1 = L_Lambda^-T Kt^-1 L_Lambda^T M (Eq. smw_stable) on return;
+// T is k x k scratch.
+void harmonic_W_from_M(Call &c, const qml_plan *plan, double *W, double *T) {
+  const Dims &d = plan->d;
+  launch_lambda_t_apply(W, d.k, d.nc, d.k0, d.lmin, plan->lamL, d.k, T, d.k, c.st);
+  trsm_blocked(c, plan->LK, d.k, d.k, plan->LKinv, T, d.k, d.k);
+  trsm_blocked_t(c, plan->LK, d.k, d.k, plan->LKinv, T, d.k, d.k);
+  launch_lambda_t_apply(T, d.k, d.nc, d.k0, d.lmin, plan->lamLi, d.k, W, d.k, c.st);
+  launch_symmetrize_avg(W, d.k, d.k, c.st);
+}
+
+// W = Y^T C^-1 Y (symmetric, k x k) from a plan's factors: X^T X (pixel
+// basis), or M = U^T U followed by the harmonic step above; T is k x k
+// scratch for the harmonic basis.
+void plan_W(Call &c, const qml_plan *plan, double *W, double *T) {
+  const Dims &d = plan->d;
+  if (plan->split) {
+    Split spl{&c, plan->nslices};
+    spl.gemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1);
+  } else {
+    launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1, c.status,
+                 c.st);
+  }
+  launch_symmetrize_lower(W, d.k, d.k, c.st);
+  if (plan->harmonic) harmonic_W_from_M(c, plan, W, T);
+}
+
+// w = Y^T C^-1 d for nsims maps D (device, n x nsims) through a plan; U is
+// n x nsims scratch (overwritten).  Pixel basis: w = X^T (L^-1 d).  Harmonic
+// basis: v = U_Y^T (L_N^-1 d) = Y^T N^-1 d, then w = (I + M Lambda)^-1 v =
+// L_Lambda^-T Kt^-1 L_Lambda^T v (Eq. smw_stable_data).
+void weighted_data(Call &c, const qml_plan *plan, const double *D, int nsims, double *U,
+                   double *w) {
+  const Dims &d = plan->d;
+  double *wv = plan->harmonic ? c.alloc<double>((size_t)d.k * nsims, "v") : w;
+  if (c.err != QML_OK) return;
+  launch_copy_matrix(D, d.n, U, d.n, d.n, nsims, c.st);
+  if (plan->split) {
+    Split spl{&c, plan->nslices};
+    trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, U, nsims, d.n);
+    spl.gemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, wv, d.k, 0);
+  } else {
+    trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, U, nsims, d.n);
+    launch_dgemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, wv, d.k, 0, c.status,
+                 c.st);
+  }
+  if (plan->harmonic) {
+    launch_lambda_t_apply(wv, d.k, d.nc, d.k0, d.lmin, plan->lamL, nsims, wv, d.k, c.st);
+    trsm_blocked(c, plan->LK, d.k, d.k, plan->LKinv, wv, nsims, d.k);
+    trsm_blocked_t(c, plan->LK, d.k, d.k, plan->LKinv, wv, nsims, d.k);
+    launch_lambda_t_apply(wv, d.k, d.nc, d.k0, d.lmin, plan->lamLi, nsims, w, d.k, c.st);
+  }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -544,6 +668,11 @@ qml_status qml_synthesize(const qml_problem *prob, const double *alm, const doub
   return c.finish();
 }
 
+int32_t qml_plan_basis(const qml_plan *plan) {
+  if (!plan) return -1;
+  return plan->harmonic ? QML_BASIS_HARMONIC : QML_BASIS_PIXEL;
+}
+
 void qml_plan_free(qml_plan *plan) {
   if (!plan) return;
   for (void *p : plan->mem) cudaFreeAsync(p, plan->st);
@@ -569,7 +698,8 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
     return fail(QML_EINVAL, "Fisher matrix larger than 2048 (nspec x (lmax - lmin + 1))");
   Call c(stream);
   Staged sp;
-  if (!stage_problem(c, prob, d, sp, prob->cl_fid, true)) return c.finish();
+  if (!stage_problem(c, prob, d, sp, prob->cl_fid, true, (size_t)d.lsig1 + 1))
+    return c.finish();
   double *Fout = c.out(F, (size_t)na * na, "F");
   if (!c.make_status()) return c.finish();
 
@@ -592,10 +722,25 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
   const int64_t nblocks = (d.n + kNB - 1) / kNB;
   plan->split = (prob->precision == QML_SPLIT_BF16);
   plan->nslices = prob->nslices;
+  // basis: the harmonic (SMW) route costs n^3/3 + n^2 k + n k^2 + 7 k^3 / 3
+  // flops, the pixel route n^3/3 + n^2 k_sig + n^2 k + n k^2 (the fixed-signal
+  // terms, n^2 (k_sig - k), are common): harmonic is cheaper when 3 n^2 > 7 k^2
+  int basis = prob->basis;
+  if (basis == QML_BASIS_AUTO)
+    basis = (3.0 * (double)d.n * d.n > 7.0 * (double)d.k * d.k) ? QML_BASIS_HARMONIC
+                                                                  : QML_BASIS_PIXEL;
+  plan->harmonic = (basis == QML_BASIS_HARMONIC);
+  const int ldcl = d.lsig1 + 1;
   plan->L = palloc((size_t)d.n * d.n);
   plan->Linv = palloc((size_t)nblocks * kNB * kNB);
   if (plan->split) plan->LinvB = palloc((size_t)((d.n + kNBS - 1) / kNBS) * kNBS * kNBS);
   plan->X = palloc((size_t)d.n * d.k);
+  if (plan->harmonic) {
+    plan->LK = palloc((size_t)d.k * d.k);
+    plan->LKinv = palloc((size_t)((d.k + kNB - 1) / kNB) * kNB * kNB);
+    plan->lamL = palloc((size_t)d.nl * d.nc * d.nc);
+    plan->lamLi = palloc((size_t)d.nl * d.nc * d.nc);
+  }
   plan->F = palloc((size_t)na * na);
   plan->b = palloc(na);
   plan->Finv = palloc((size_t)na * na);
@@ -657,29 +802,74 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
     return e;
   }
 
-  if (plan->split) {
-    Split spl{&c, prob->nslices};
-    build_C_split(c, spl, sp, d, plan->X, plan->L);
-    potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr);
+  Split spl{&c, prob->nslices};
+  Split *sp_or_null = plan->split ? &spl : nullptr;
+  // Signal-band pieces: the whole band for the pixel basis; for the harmonic
+  // basis the fixed signal below and above the window (Eq. N_eff).  They are
+  // built in a scratch Y of their own width, or in plan->X when that fits.
+  auto scratch_for = [&](int kb) -> double * {
+    return kb <= d.k ? plan->X : c.alloc<double>((size_t)d.n * kb, "signal-band Y");
+  };
+  launch_copy_lower(sp.N, d.n, plan->L, d.n, d.n, c.st);
+  if (!plan->harmonic) {
+    // C = Y_sig Lambda Y_sig^T + N ; L L^T = C ; X = L^-1 Y_win ; W = X^T X
+    add_band_signal(c, sp_or_null, sp, d, d.lsig0, d.lsig1, ldcl,
+                    scratch_for(d.nc * band_k0(d.lsig0, d.lsig1)), plan->L);
+    if (plan->split)
+      potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr);
+    else
+      potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
     launch_ybuild(sp.y, plan->X, d.n, c.st);
-    trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, plan->X, d.k, d.n);
-    spl.gemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1);
+    if (plan->split) {
+      trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, plan->X, d.k, d.n);
+      spl.gemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1);
+    } else {
+      trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
+      launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1,
+                   c.status, c.st);
+    }
+    launch_symmetrize_lower(W, d.k, d.k, c.st);
   } else {
-    // C = Y Lambda Y^T + N ; L L^T = C
-    build_C(c, sp, d, plan->X, plan->L);
-    potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
-    // X = L^-1 Y ; W = X^T X
+    // N_eff = N + fixed signal outside the window ; L_N L_N^T = N_eff
+    if (d.lsig0 < d.lmin)
+      add_band_signal(c, sp_or_null, sp, d, d.lsig0, d.lmin - 1, ldcl,
+                      scratch_for(d.nc * band_k0(d.lsig0, d.lmin - 1)), plan->L);
+    if (d.lsig1 > d.lmax)
+      add_band_signal(c, sp_or_null, sp, d, d.lmax + 1, d.lsig1, ldcl,
+                      scratch_for(d.nc * band_k0(d.lmax + 1, d.lsig1)), plan->L);
+    if (plan->split)
+      potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr);
+    else
+      potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
+    // U = L_N^-1 Y_win ; M = U^T U (the noise-weighted Gramian Y^T N^-1 Y)
     launch_ybuild(sp.y, plan->X, d.n, c.st);
-    trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
-    launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1, c.status,
-                 c.st);
+    if (plan->split) {
+      trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, plan->X, d.k, d.n);
+      spl.gemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1);
+    } else {
+      trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
+      launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1,
+                   c.status, c.st);
+    }
+    launch_symmetrize_lower(W, d.k, d.k, c.st);
+    // Kt = I + L_Lambda^T M L_Lambda, factored in float64 (the SMW inner
+    // matrix); then W = L_Lambda^-T Kt^-1 L_Lambda^T M = M (I + Lambda M)^-1
+    // (Eq. smw_stable) by two triangular solves and two per-(l, m) mixes
+    double *T = c.alloc<double>((size_t)d.k * d.k, "SMW product");
+    double *ldk = c.alloc<double>((size_t)((d.k + kNB - 1) / kNB));
+    if (c.err == QML_OK) {
+      launch_lambda_factor(sp.cl, d.lmin, d.lmax, d.nc, d.comps, plan->lamL, c.st, ldcl);
+      launch_lambda_inverse(plan->lamL, d.nl, d.nc, d.lmin, plan->lamLi, c.status, c.st);
+      launch_form_ktilde(W, d.k, d.nc, d.k0, d.lmin, plan->lamL, plan->LK, d.k, c.st);
+      potrf_blocked(c, plan->LK, d.k, d.k, plan->LKinv, ldk, nullptr);
+      harmonic_W_from_M(c, plan, W, T);
+    }
   }
-  launch_symmetrize_lower(W, d.k, d.k, c.st);
   // block sums -> F, noise bias
   launch_fisher_blocksum(W, d.k, d.nc, d.k0, d.lmin, d.lmax, parts, diag, c.st);
   launch_fisher_assemble(parts, diag, d.nc, d.nl, d.nspec_full, uv_full, Ffull, tfull, c.st);
   launch_fisher_select(Ffull, tfull, sp.cl, d.lmin, d.lmax, d.nspec_full, ids_full, prob->nspec,
-                       sel, Fl, bl, c.st);
+                       sel, Fl, bl, c.st, ldcl);
   if (binned) {  // P_b = sum_{l in b} P_l: F and the noise bias summed over bins
     launch_bin_fisher(Fl, na_l, plan->bstart, plan->bcount, na, plan->F, c.st);
     launch_bin_rows(bl, na_l, 1, plan->bstart, plan->bcount, na, plan->b, c.st);
@@ -719,16 +909,8 @@ qml_status qml_estimate(qml_plan *plan, const double *maps, int32_t nsims, doubl
   double *dec = c.out(cl_deconv, (size_t)na * nsims, "cl_deconv");
   double *dcr = c.out(cl_decorr, (size_t)na * nsims, "cl_decorr");
   if (!c.make_status()) return c.finish();
-  launch_copy_matrix(D, d.n, U, d.n, d.n, nsims, c.st);
-  // w = Y^T C^-1 d = X^T (L^-1 d)
-  if (plan->split) {
-    Split spl{&c, plan->nslices};
-    trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, U, nsims, d.n);
-    spl.gemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, w, d.k, 0);
-  } else {
-    trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, U, nsims, d.n);
-    launch_dgemm(1, 0, d.k, nsims, d.n, 1.0, plan->X, d.n, U, d.n, 0.0, w, d.k, 0, c.status, c.st);
-  }
+  // w = Y^T C^-1 d (pixel or harmonic basis)
+  weighted_data(c, plan, D, nsims, U, w);
   if (plan->binned) {  // per-l y, then summed over bins
     double *yl = c.alloc<double>((size_t)plan->na_l * nsims, "per-l y");
     if (c.err != QML_OK) return c.finish();
@@ -1034,6 +1216,59 @@ qml_status pix_loglike_batch(const lnl_mask *masks, int32_t nmask, int32_t nitem
   }
   cudaEventDestroy(setup_done);
   return res;
+}
+
+qml_status qml_cross(qml_plan *plan1, qml_plan *plan2, const double *maps1, const double *maps2,
+                     int32_t nsims, double *Wx, double *q, double *cl, void *stream) {
+  if (!plan1 || !plan2 || !Wx) return fail(QML_EINVAL, "qml_cross needs two plans and Wx");
+  if (nsims < 0 || (nsims > 0 && (!maps1 || !maps2)))
+    return fail(QML_EINVAL, "qml_cross needs maps1, maps2 and nsims >= 0");
+  const Dims &d = plan1->d, &d2 = plan2->d;
+  if (d.n != d2.n || d.nc != d2.nc || d.lmin != d2.lmin || d.lmax != d2.lmax ||
+      plan1->nspec != plan2->nspec || d.nT != d2.nT)
+    return fail(QML_EINVAL, "qml_cross: the plans need the same pixels, fields, window and spectra");
+  for (int i = 0; i < plan1->nspec; ++i)
+    if (plan1->spec[i] != plan2->spec[i])
+      return fail(QML_EINVAL, "qml_cross: the plans need the same spectra");
+  if (plan1->binned || plan2->binned)
+    return fail(QML_EINVAL, "qml_cross: per-multipole plans only (no bins)");
+  const int na = plan1->na;
+  Call c(stream);
+  double *Wxd = c.out(Wx, (size_t)na * na, "Wx");
+  double *W1 = c.alloc<double>((size_t)d.k * d.k, "W1");
+  double *W2 = c.alloc<double>((size_t)d.k * d.k, "W2");
+  double *T = (plan1->harmonic || plan2->harmonic) ? c.alloc<double>((size_t)d.k * d.k, "SMW product")
+                                                   : nullptr;
+  const int NP = d.nc * d.nc;
+  double *parts = c.alloc<double>((size_t)d.nl * (d.nl + 1) / 2 * NP * NP, "cross sums");
+  if (!c.make_status()) return c.finish();
+  // Wx_ab = 1/2 tr[W1 E_a W2 E_b] (Eq. q_cross)
+  plan_W(c, plan1, W1, T);
+  plan_W(c, plan2, W2, T);
+  launch_cross_blocksum(W1, W2, d.k, d.nc, d.k0, d.lmin, d.lmax, parts, c.st);
+  launch_cross_assemble(parts, d.nc, d.nl, plan1->nspec, plan1->uv, Wxd, c.st);
+  if (nsims > 0) {
+    const double *D1 = c.in(maps1, (size_t)d.n * nsims, "maps1");
+    const double *D2 = c.in(maps2, (size_t)d.n * nsims, "maps2");
+    double *U = c.alloc<double>((size_t)d.n * nsims, "U");
+    double *w1 = c.alloc<double>((size_t)d.k * nsims, "w1");
+    double *w2 = c.alloc<double>((size_t)d.k * nsims, "w2");
+    double *qd = c.out(q, (size_t)na * nsims, "q");
+    if (!qd) qd = c.alloc<double>((size_t)na * nsims, "q");
+    double *cld = c.out(cl, (size_t)na * nsims, "cl");
+    double *A = cld ? c.alloc<double>((size_t)na * na, "Wx factors") : nullptr;
+    if (c.err != QML_OK) return c.finish();
+    weighted_data(c, plan1, D1, nsims, U, w1);
+    weighted_data(c, plan2, D2, nsims, U, w2);
+    launch_quad_cross(w1, w2, d.k, nsims, d.nc, d.k0, d.lmin, d.lmax, plan1->nspec, plan1->uv,
+                      qd, c.st);
+    if (cld) {  // C_x = Wx^-1 q_x
+      launch_copy_matrix(Wxd, na, A, na, na, na, c.st);
+      launch_copy_matrix(qd, na, cld, na, na, nsims, c.st);
+      launch_lu_solve(A, na, cld, nsims, c.status, c.st);
+    }
+  }
+  return c.finish();
 }
 
 qml_status qml_potrf(int64_t n, double *A, int64_t lda, double *logdet, int32_t precision,

@@ -354,8 +354,9 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(double *A, int64_t l
         if (fail_col >= 0) {
           if (warp == 0 && lane == 0) {
             *bad = 1;
-            status->info = (int)(j0 + fail_col + 1);
-            atomicExch(&status->code, 2 /* QML_ENOTSPD */);
+            // the first error of the call is the one reported
+            if (atomicCAS(&status->code, 0, 2 /* QML_ENOTSPD */) == 0)
+              status->info = (int)(j0 + fail_col + 1);
           }
         } else if (live && (warp == 0 || lane >= kPW)) {
 #pragma unroll
@@ -607,8 +608,9 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_df_kernel(const double *A, 
       if (fail_col >= 0) {
         if (warp == 0 && lane == 0) {
           bad = 1;
-          status->info = (int)(j0 + fail_col + 1);
-          atomicExch(&status->code, 2 /* QML_ENOTSPD */);
+          // the first error of the call is the one reported
+          if (atomicCAS(&status->code, 0, 2 /* QML_ENOTSPD */) == 0)
+            status->info = (int)(j0 + fail_col + 1);
         }
       } else if (live && (warp == 0 || lane >= kPW)) {
 #pragma unroll
@@ -1092,6 +1094,29 @@ void launch_trtri_blocks(const double *L, int64_t lda, int64_t n, double *Linv,
 
 void launch_sum_logdet(const double *parts, int nparts, double *out, cudaStream_t st) {
   { sum_logdet_kernel<<<1, 32, 0, st>>>(parts, nparts, out); count_launch(); }
+}
+
+namespace {
+// A <- (A + A^T) / 2 (both triangles), one thread per strictly lower entry
+__global__ void symmetrize_avg_kernel(double *A, int64_t lda, int64_t n) {
+  const int64_t total = n * (n - 1) / 2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    // t -> (i, j), i > j, row by row of the strict lower triangle
+    int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) + 1.0) * 0.5);
+    while (i * (i - 1) / 2 > t) --i;
+    while ((i + 1) * i / 2 <= t) ++i;
+    const int64_t j = t - i * (i - 1) / 2;
+    const double v = 0.5 * (A[i + j * lda] + A[j + i * lda]);
+    A[i + j * lda] = v;
+    A[j + i * lda] = v;
+  }
+}
+}  // namespace
+
+void launch_symmetrize_avg(double *A, int64_t lda, int64_t n, cudaStream_t st) {
+  if (n < 2) return;
+  { symmetrize_avg_kernel<<<grid_for(n * (n - 1) / 2), 256, 0, st>>>(A, lda, n); count_launch(); }
 }
 
 void launch_copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t n,

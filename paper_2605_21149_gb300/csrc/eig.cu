@@ -380,8 +380,8 @@ __global__ void eig_factor_kernel(const double *A, int na, int n, double cut, do
     minmax[0] = xmin;
     minmax[1] = xmax;
     if (!(xmin > 0.0)) {
-      st->info = -1;
-      atomicExch(&st->code, 2 /* QML_ENOTSPD */);
+      // the first error of the call is the one reported
+      if (atomicCAS(&st->code, 0, 2 /* QML_ENOTSPD */) == 0) st->info = -1;
     }
   }
   for (int c = threadIdx.x; c < n; c += blockDim.x) {

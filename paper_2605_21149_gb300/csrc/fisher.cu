@@ -150,7 +150,8 @@ __global__ void fisher_assemble_kernel(const double *parts, const double *diag, 
 }
 
 __global__ void fisher_select_kernel(const double *F_full, const double *t_full,
-                                     const double *cl_fid, int lmin, int lmax, int nspec_full,
+                                     const double *cl_fid, int ldcl, int lmin, int lmax,
+                                     int nspec_full,
                                      const int *full_spec_ids, int nspec, const int *sel,
                                      double *F, double *b) {
   const int nl = lmax - lmin + 1;
@@ -171,7 +172,7 @@ __global__ void fisher_select_kernel(const double *F_full, const double *t_full,
       for (int fb = 0; fb < naf; ++fb) {
         int sid = full_spec_ids[fb / nl];
         int l = lmin + fb % nl;
-        s = fma(F_full[fa + (int64_t)fb * naf], cl_fid[sid * (lmax + 1) + l], s);
+        s = fma(F_full[fa + (int64_t)fb * naf], cl_fid[sid * ldcl + l], s);
       }
       b[a] = 0.5 * t_full[fa] - s;
     }
@@ -254,11 +255,13 @@ void launch_fisher_assemble(const double *parts, const double *diag, int nc, int
 
 void launch_fisher_select(const double *F_full, const double *t_full, const double *cl_fid,
                           int lmin, int lmax, int nspec_full, const int *full_spec_ids,
-                          int nspec, const int *sel, double *F, double *b, cudaStream_t st) {
+                          int nspec, const int *sel, double *F, double *b, cudaStream_t st,
+                          int ldcl) {
   int64_t na = (int64_t)nspec * (lmax - lmin + 1);
   int blocks = (int)((na * na + na + 255) / 256);
-  { fisher_select_kernel<<<blocks, 256, 0, st>>>(F_full, t_full, cl_fid, lmin, lmax, nspec_full,
-                                               full_spec_ids, nspec, sel, F, b); count_launch(); }
+  if (ldcl <= 0) ldcl = lmax + 1;
+  { fisher_select_kernel<<<blocks, 256, 0, st>>>(F_full, t_full, cl_fid, ldcl, lmin, lmax,
+                                               nspec_full, full_spec_ids, nspec, sel, F, b); count_launch(); }
 }
 
 void launch_quad_y(const double *w, int64_t ldw, int nsims, int nc, int k0, int lmin, int lmax,

@@ -43,8 +43,13 @@ void launch_ybuild(const YArgs &a, double *Y, int64_t ldy, cudaStream_t st);
 // Mix the columns of Y inside every (l, m) by the lower Cholesky factor of the
 // 3x3 spectrum block: G = Y L_Lambda, so that G G^T = Y Lambda Y^T.
 // lamL holds per l the nc x nc lower factor (row-major, nc*nc doubles).
+// cl is [6][ldcl] (ldcl <= 0: lmax + 1).
 void launch_lambda_factor(const double *cl, int lmin, int lmax, int nc, const int *comps,
-                          double *lamL, cudaStream_t st);
+                          double *lamL, cudaStream_t st, int ldcl = 0);
+// Per l the inverse of the nc x nc lower factor (same layout); a block that is
+// not positive definite sets status QML_EINVAL (info = l + 1).
+void launch_lambda_inverse(const double *lamL, int nl, int nc, int lmin, double *lamLi,
+                           DevStatus *status, cudaStream_t st);
 void launch_mix_lambda(double *Y, int64_t ldy, int n, int nc, int k0, int lmin, int lmax,
                        const double *lamL, cudaStream_t st);
 
@@ -125,6 +130,8 @@ void launch_bin_fisher(const double *F, int na, const int *bstart, const int *bc
 void launch_copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t n,
                        cudaStream_t st);
 void launch_symmetrize_lower(double *A, int64_t lda, int64_t n, cudaStream_t st);
+// A <- (A + A^T) / 2
+void launch_symmetrize_avg(double *A, int64_t lda, int64_t n, cudaStream_t st);
 void launch_copy_matrix(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t rows,
                         int64_t cols, cudaStream_t st);
 void launch_add_matrix(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t rows,
@@ -146,16 +153,30 @@ void launch_fisher_assemble(const double *parts, const double *diag, int nc, int
                             int nspec_full, const int *spec_uv /* 4 ints per spectrum */,
                             double *F_full, double *t_full, cudaStream_t st);
 // b = t/2 - F_full c_fid restricted; F = F_full restricted.
+// cl_fid is [6][ldcl] (ldcl <= 0: lmax + 1).
 void launch_fisher_select(const double *F_full, const double *t_full, const double *cl_fid,
                           int lmin, int lmax, int nspec_full, const int *full_spec_ids,
                           int nspec, const int *sel /* positions into full */, double *F,
-                          double *b, cudaStream_t st);
+                          double *b, cudaStream_t st, int ldcl = 0);
 // y_a = 1/2 w^T E_a w for every column of w (k x nsims).
 void launch_quad_y(const double *w, int64_t ldw, int nsims, int nc, int k0, int lmin, int lmax,
                    int nspec, const int *spec_uv, double *y, cudaStream_t st);
 // q = y - b (columns), nsims columns of na.
 void launch_sub_bias(const double *y, const double *b, int na, int nsims, double *q,
                      cudaStream_t st);
+
+// ----------------------------------------------------------------- cross --
+// Cross-QML (cross.cu): per (l >= l') block the nc^4 sums of W1 x W2
+// component products; the mixing matrix Wx from them; q_x = 1/2 w1^T E_a w2;
+// a general dense solve A X = B (one CTA, LU with partial pivoting).
+void launch_cross_blocksum(const double *W1, const double *W2, int64_t ldw, int nc, int k0,
+                           int lmin, int lmax, double *parts, cudaStream_t st);
+void launch_cross_assemble(const double *parts, int nc, int nl, int nspec, const int *spec_uv,
+                           double *Wx, cudaStream_t st);
+void launch_quad_cross(const double *w1, const double *w2, int64_t ldw, int nsims, int nc, int k0,
+                       int lmin, int lmax, int nspec, const int *spec_uv, double *q,
+                       cudaStream_t st);
+void launch_lu_solve(double *A, int n, double *B, int nrhs, DevStatus *status, cudaStream_t st);
 
 // ------------------------------------------------------------------- eig --
 // Symmetric eigendecomposition of F (na x na) by parallel cyclic Jacobi

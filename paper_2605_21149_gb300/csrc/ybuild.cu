@@ -232,12 +232,12 @@ namespace {
 // Per l: the nc x nc block of spectra (fields comps[]) and its lower
 // Cholesky factor; a pivot that is not positive (a spectrum set to zero)
 // gives a zero column, i.e. a factor of the positive semi-definite block.
-__global__ void lambda_factor_kernel(const double *cl, int lmin, int lmax, int nc, int c0,
-                                     int c1, int c2, double *lamL) {
+__global__ void lambda_factor_kernel(const double *cl, int ldcl, int lmin, int lmax, int nc,
+                                     int c0, int c1, int c2, double *lamL) {
   int il = blockIdx.x * blockDim.x + threadIdx.x;
   int l = lmin + il;
   if (l > lmax) return;
-  const int L = lmax + 1;
+  const int L = ldcl;  // row stride of the [6][.] spectrum array
   const int comps[3] = {c0, c1, c2};
   // spectrum index of the (x, y) component pair
   auto sidx = [](int x, int y) {
@@ -270,6 +270,32 @@ __global__ void lambda_factor_kernel(const double *cl, int lmin, int lmax, int n
     for (int j = 0; j < nc; ++j) lamL[(size_t)il * nc * nc + i * nc + j] = Lf[i][j];
 }
 
+// Per l: Li = L_l^-1 of the nc x nc lower factor (lower triangular, row-major
+// like lamL).  A pivot <= 0 (a fiducial block that is not positive definite)
+// sets the status word to QML_EINVAL with info = l + 1 and leaves zeros.
+__global__ void lambda_inverse_kernel(const double *lamL, int nl, int nc, int lmin,
+                                      double *lamLi, DevStatus *status) {
+  const int il = blockIdx.x * blockDim.x + threadIdx.x;
+  if (il >= nl) return;
+  const double *Lf = lamL + (size_t)il * nc * nc;
+  double X[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  bool ok = true;
+  for (int j = 0; j < nc; ++j) ok = ok && Lf[j * nc + j] > 0.0;
+  if (ok) {
+    // forward substitution column by column: L X = I
+    for (int c = 0; c < nc; ++c)
+      for (int i = c; i < nc; ++i) {
+        double v = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) v -= Lf[i * nc + k] * X[k][c];
+        X[i][c] = v / Lf[i * nc + i];
+      }
+  } else if (status) {
+    if (atomicCAS(&status->code, 0, 1 /* QML_EINVAL */) == 0) status->info = lmin + il + 1;
+  }
+  for (int i = 0; i < nc; ++i)
+    for (int j = 0; j < nc; ++j) lamLi[(size_t)il * nc * nc + i * nc + j] = X[i][j];
+}
+
 // G[p, (X, l, i)] = sum_X' Y[p, (X', l, i)] L_l[X', X], in place: one thread
 // owns one (row, mode) and all components of it.
 __global__ void mix_lambda_kernel(double *Y, int64_t ldy, int n, int nc, int k0, int lmin,
@@ -300,11 +326,17 @@ __global__ void mix_lambda_kernel(double *Y, int64_t ldy, int n, int nc, int k0,
 size_t ybuild_coef_bytes(int lmax) { return (size_t)(lmax + 1) * (lmax + 1) * sizeof(RecCoef); }
 
 void launch_lambda_factor(const double *cl, int lmin, int lmax, int nc, const int *comps,
-                          double *lamL, cudaStream_t st) {
+                          double *lamL, cudaStream_t st, int ldcl) {
   int nl = lmax - lmin + 1;
-  { lambda_factor_kernel<<<(nl + 63) / 64, 64, 0, st>>>(cl, lmin, lmax, nc, comps[0],
+  if (ldcl <= 0) ldcl = lmax + 1;
+  { lambda_factor_kernel<<<(nl + 63) / 64, 64, 0, st>>>(cl, ldcl, lmin, lmax, nc, comps[0],
                                                       nc > 1 ? comps[1] : 0,
                                                       nc > 2 ? comps[2] : 0, lamL); count_launch(); }
+}
+
+void launch_lambda_inverse(const double *lamL, int nl, int nc, int lmin, double *lamLi,
+                           DevStatus *status, cudaStream_t st) {
+  { lambda_inverse_kernel<<<(nl + 63) / 64, 64, 0, st>>>(lamL, nl, nc, lmin, lamLi, status); count_launch(); }
 }
 
 void launch_mix_lambda(double *Y, int64_t ldy, int n, int nc, int k0, int lmin, int lmax,
