@@ -342,6 +342,10 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *                   per-item kernel sequence as a captured CUDA graph
  *   ozaki_stages    3 (default) / 2: depth of the split kernel's TMA ring
  *                   (stages of 64 KB; always 2 for more than 8 digits)
+ *   ozaki_pairs     1 (default) / 0: the split kernel runs in clusters of two
+ *                   CTAs on pairs of tile rows that share their B digit tiles
+ *                   (loaded once from L2, multicast to both) / one CTA per
+ *                   tile; the results are bit-identical
  *   emu_tc          1 (default) / 0: emulator inference runs its layers on
  *                   tcgen05 (width a multiple of 64, at most 256) / every
  *                   layer through the WMMA product

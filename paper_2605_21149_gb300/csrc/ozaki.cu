@@ -20,11 +20,12 @@
 // digit slicing reads the float64 bit patterns with integer operations (the
 // float64 pipe of this part is narrow).
 //
-// Schedule.  The levels are taken in groups of four (2..5, 6..9, 10..11),
-// each level of a group in its own 128-column FP32 accumulator (the four use
-// all 512 TMEM columns).  For a group, every K step of 16 loads each digit
-// tile the group needs once -- A_1..A_d and B_1..B_d, d = min(S, last level
-// - 1), 4 KB each -- and runs every digit pair of the group's levels on them,
+// Schedule.  The levels are taken in groups of four, largest first (6..9,
+// then 10..11, then 2..5; see group_at), each level of a group in its own
+// 128-column FP32 accumulator (the four use all 512 TMEM columns).  For a
+// group, every K step of 16 loads each digit tile the group needs once --
+// A_1..A_d and B_1..B_d, d = min(S, last level - 1), 4 KB each -- and runs
+// every digit pair of the group's levels on them,
 // so a loaded tile serves all the pairs it belongs to (S = 8: 24 tile loads
 // per K step for 36 products, where one load per operand and pair would take
 // 72).  The tensor core reads a 128 x 128 x 16 product's 8 KB of operands from
@@ -116,9 +117,13 @@ struct OzParams {
   int nstages;             // ring depth
   int shift_top;           // left shift of level-2 chunk sums in the int64 accumulator
   int tiles_n, lower;
-  int ntiles;              // output tiles; the grid takes them round-robin
+  int ntiles;              // work items (tiles, or tile pairs); the grid takes them round-robin
   double alpha, betac;
   int alpha_pow2, alpha_exp, alpha_neg;  // alpha = (-1)^neg 2^exp when alpha_pow2
+  // 0: C is not read (beta = 0); 1: v + C (beta = 1); 2: fma(beta, C, v).  A
+  // float64 compare is a float64-pipe instruction (tens of clocks a warp on
+  // this part), so the output takes this integer instead of testing beta.
+  int beta_mode;
   double *C;
   int64_t ldc;
   const int *ea, *eb;
@@ -153,6 +158,50 @@ __device__ __forceinline__ void tile_of(const OzParams &p, int bid, int &tm, int
   tm = r;
   tn = bid - r * (r + 1) / 2;
 }
+// Pairs of tiles for the two CTAs of a cluster: pair idx is tile rows 2 TM
+// and 2 TM + 1 of tile column tn (one B tile shared by both).  Lower C: the
+// pairs with tn <= 2 TM + 1, row pair by row pair (2 TM + 2 of them, fewer
+// in a last row pair of one tile row); a tile above the diagonal or past the
+// last tile row is computed on zeros or discarded, and stores nothing.
+__device__ __forceinline__ void pair_of(const OzParams &p, int idx, int &TM, int &tn) {
+  if (!p.lower) {
+    TM = idx / p.tiles_n;
+    tn = idx % p.tiles_n;
+    return;
+  }
+  // TM (TM + 1) <= idx < (TM + 1) (TM + 2)
+  int r = (int)((sqrt(4.0 * idx + 1.0) - 1.0) * 0.5);
+  while ((r + 1) * (r + 2) <= idx) ++r;
+  while (r * (r + 1) > idx) --r;
+  TM = r;
+  tn = idx - r * (r + 1);
+}
+// This CTA's rank in its pair, its first work item and the stride between
+// its items (read from special registers where used: held in registers
+// across the role loops they pushed the 56-register warpgroup into spills).
+template <int CL>
+__device__ __forceinline__ int pair_rank() {
+  return CL == 2 ? (int)cluster_ctarank() : 0;
+}
+template <int CL>
+__device__ __forceinline__ int item_first() {
+  return CL == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+}
+template <int CL>
+__device__ __forceinline__ int item_stride() {
+  return CL == 2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+}
+// the output tile of this CTA for work item `item` (a tile, or a pair for CL = 2)
+template <int CL>
+__device__ __forceinline__ void item_tile(const OzParams &p, int item, int rank, int &tm, int &tn) {
+  if (CL == 1) {
+    tile_of(p, item, tm, tn);
+  } else {
+    int TM;
+    pair_of(p, item, TM, tn);
+    tm = 2 * TM + rank;
+  }
+}
 
 // Level group g: levels lb .. le (at most kGroupLevels), digits 1 .. nd of
 // each operand, and the K steps a ring stage holds for it.
@@ -166,6 +215,16 @@ __device__ __forceinline__ Group group_of(const OzParams &p, int S, int g) {
   G.nd = min(S, G.le - 1);
   G.sps = max(1, p.stage_tiles / G.nd);
   return G;
+}
+// The order the groups are taken in: group 1 (levels 6..9, the most digit
+// pairs) first, group 0 (levels 2..5) last.  The epilogue writes a finished
+// tile out before it reads the next tile's first group, and the MMAs of that
+// group cannot start on accumulators still unread; with the largest group
+// first they keep the tensor core busy for longer than the output takes.  The
+// int64 sums are the same whatever the order.
+__device__ __forceinline__ int group_at(int i, int ngroups) {
+  if (ngroups == 1) return 0;
+  return i == 0 ? 1 : (i == ngroups - 1 ? 0 : i + 1);
 }
 
 // Every digit product of levels LB..LE (S digits) for one K step, in
@@ -210,33 +269,39 @@ __device__ __forceinline__ void load_stage(const CUtensorMap *tmA, const CUtenso
 // inlined: its 8 calls share one copy of the code, which stays in the
 // instruction cache (unrolled 64 times, the output code ran once per tile and
 // was fetched cold).  The 8 C values are read before any is written, so
-// their loads are in flight together.
+// their loads are in flight together; the 8 column exponents f_j come in as
+// arguments (the caller has them by warp shuffle), not as loads between the
+// stores.
 __device__ __noinline__ void store_out8(const OzParams &p, int64_t gi, int64_t gj0, int ebase,
                                         long long a0, long long a1, long long a2, long long a3,
-                                        long long a4, long long a5, long long a6, long long a7) {
+                                        long long a4, long long a5, long long a6, long long a7,
+                                        int f0, int f1, int f2, int f3, int f4, int f5, int f6,
+                                        int f7) {
   const long long av[8] = {a0, a1, a2, a3, a4, a5, a6, a7};
+  const int fv[8] = {f0, f1, f2, f3, f4, f5, f6, f7};
   const int eshift = p.alpha_pow2 ? p.alpha_exp : 0;
   const bool aneg = p.alpha_pow2 && p.alpha_neg;
+  const int bmode = p.beta_mode;
   double cv[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int64_t gj = gj0 + u;
     const bool live = gj < p.N && !(p.lower && gi < gj);
-    cv[u] = (live && p.betac != 0.0) ? p.C[gi + gj * p.ldc] : 0.0;
+    cv[u] = (live && bmode != 0) ? p.C[gi + gj * p.ldc] : 0.0;
   }
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int64_t gj = gj0 + u;
     if (gj >= p.N || (p.lower && gi < gj)) continue;
-    const int eb = p.eb[gj];
+    const int eb = fv[u];
     double v;
     if (fixed_to_double(av[u], ebase + eb + eshift, aneg, v)) {
       if (!p.alpha_pow2) v *= p.alpha;
     } else {
       v = p.alpha * ldexp((double)av[u], ebase + eb);
     }
-    if (p.betac == 1.0) v += cv[u];
-    else if (p.betac != 0.0) v = fma(p.betac, cv[u], v);
+    if (bmode == 1) v += cv[u];
+    else if (bmode == 2) v = fma(p.betac, cv[u], v);
     p.C[gi + gj * p.ldc] = v;
   }
 }
@@ -247,14 +312,26 @@ __device__ __noinline__ void store_out8(const OzParams &p, int64_t gi, int64_t g
 // data and the MMAs of the next tile start as soon as the epilogue has read
 // the accumulators, while the epilogue converts and stores the finished tile
 // from its registers.
-template <int SC>
+//
+// CL = 2: clusters of two CTAs on the tile rows 2 TM, 2 TM + 1 of one tile
+// column, which need the same B digit tiles.  Each CTA loads its own A tiles
+// and half of the B digits, multicast into both CTAs' shared memory at the
+// same offsets (the stage's full barrier in each CTA expects all of its
+// bytes), so B leaves L2 once for the two tiles: a quarter less L2 traffic,
+// which is what bounds the long-K products.  A stage is free again only when
+// both CTAs' MMAs are done with it: the MMA commits arrive on the empty
+// barriers of both CTAs (two arrivals a phase).  Cluster barriers order the
+// barrier initialisation before any remote arrival and keep both CTAs alive
+// until neither can reach the other's shared memory.
+template <int SC, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ CUtensorMap tmA4,
                       const __grid_constant__ CUtensorMap tmB4,
                       const __grid_constant__ CUtensorMap tmA8,
-                      const __grid_constant__ CUtensorMap tmB8, OzParams p) {
+                      const __grid_constant__ CUtensorMap tmB8,
+                      const __grid_constant__ CUtensorMap tmB2, OzParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -273,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, CL);
     }
     mbar_init(accf, 1);
     mbar_init(acce, 32 * kEpiWarps);
@@ -283,6 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_alloc(smem_u32(tmem_holder), kGroupLevels * 128);
   tc_fence_before();
   __syncthreads();
+  if (CL == 2) cluster_sync_all();  // both CTAs' barriers exist before any remote arrival
   tc_fence_after();
   const uint32_t tbase = *tmem_holder;
 
@@ -301,11 +379,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int last_phase[4] = {-1, -1, -1, -1};
       bool ok = (*((volatile int *)&st->code) == 0) && !p.no_loads;
-      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+      for (int item = item_first<CL>(); item < p.ntiles && ok; item += item_stride<CL>()) {
         int tm, tn;
-        tile_of(p, tile, tm, tn);
+        item_tile<CL>(p, item, pair_rank<CL>(), tm, tn);
         const int m0 = tm * OBM, n0 = tn * OBN;
-        for (int g = 0; g < ngroups && ok; ++g) {
+        for (int gi = 0; gi < ngroups && ok; ++gi) {
+          const int g = group_at(gi, ngroups);
           const Group G = group_of(p, S, g);
           for (int c = 0; c < nchunks && ok; ++c) {
             const int k0 = c * csteps, k1 = min(k0 + csteps, p.nk16);
@@ -315,16 +394,32 @@ __global__ void __launch_bounds__(kThreads, 1)
               mbar_expect_tx(full0 + 8 * stage, 2u * G.nd * nsteps * kDigitTile);
               const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
               const uint32_t sb = sa + p.stage_tiles * kDigitTile;
-              if (SC == 8 && G.nd == 4) {
-                load_stage<4>(&tmA4, &tmB4, sa, sb, full0 + 8 * stage, ks, nsteps, m0, n0);
+              const uint32_t fb = full0 + 8 * stage;
+              if (CL == 2 && SC == 8) {
+                // own A box; B digits [rank h, rank h + h) for both CTAs
+                const int h = G.nd >> 1, rank = pair_rank<CL>();
+                const CUtensorMap *mA = G.nd == 4 ? &tmA4 : &tmA8;
+                const CUtensorMap *mBh = G.nd == 4 ? &tmB2 : &tmB4;
+                for (int j = 0; j < nsteps; ++j) {
+                  const uint32_t off = (uint32_t)(j * G.nd) * kDigitTile;
+                  tma_load_3d(sa + off, mA, fb, (ks + j) * KS, m0, 0);
+                  tma_load_3d_mc(sb + off + (uint32_t)(rank * h) * kDigitTile, mBh, fb,
+                                 (ks + j) * KS, n0, rank * h, (uint16_t)3);
+                }
+              } else if (SC == 8 && G.nd == 4) {
+                load_stage<4>(&tmA4, &tmB4, sa, sb, fb, ks, nsteps, m0, n0);
               } else if (SC == 8) {
-                load_stage<8>(&tmA8, &tmB8, sa, sb, full0 + 8 * stage, ks, nsteps, m0, n0);
+                load_stage<8>(&tmA8, &tmB8, sa, sb, fb, ks, nsteps, m0, n0);
               } else {
                 for (int j = 0; j < nsteps; ++j)
                   for (int d = 0; d < G.nd; ++d) {
                     const uint32_t off = (uint32_t)(j * G.nd + d) * kDigitTile;
-                    tma_load_2d(sa + off, &tmA, full0 + 8 * stage, (ks + j) * KS, d * p.Mpad + m0);
-                    tma_load_2d(sb + off, &tmB, full0 + 8 * stage, (ks + j) * KS, d * p.Npad + n0);
+                    tma_load_2d(sa + off, &tmA, fb, (ks + j) * KS, d * p.Mpad + m0);
+                    if (CL == 1)
+                      tma_load_2d(sb + off, &tmB, fb, (ks + j) * KS, d * p.Npad + n0);
+                    else if ((d & 1) == pair_rank<CL>())  // B digit d from CTA d mod 2, to both
+                      tma_load_2d_mc(sb + off, &tmB, fb, (ks + j) * KS, d * p.Npad + n0,
+                                     (uint16_t)3);
                   }
               }
               last_phase[stage] = (int)phase;
@@ -349,8 +444,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       uint32_t q = 0;  // chunk flushes so far
       bool ok = (*((volatile int *)&st->code) == 0);
-      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-        for (int g = 0; g < ngroups && ok; ++g) {
+      for (int item = item_first<CL>(); item < p.ntiles && ok; item += item_stride<CL>()) {
+        for (int gi = 0; gi < ngroups && ok; ++gi) {
+          const int g = group_at(gi, ngroups);
           const Group G = group_of(p, S, g);
           for (int c = 0; c < nchunks && ok; ++c) {
             // the epilogue must have read the accumulators of the previous chunk
@@ -385,7 +481,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                   }
                 }
               }
-              mma_commit(empty0 + 8 * stage);  // frees the smem slot when these MMAs finish
+              // frees the smem slot when these MMAs finish (in both CTAs of a pair)
+              if (CL == 2)
+                mma_commit_mc(empty0 + 8 * stage, (uint16_t)3);
+              else
+                mma_commit(empty0 + 8 * stage);
               if (++stage == NST) { stage = 0; phase ^= 1; }
             }
             if (!ok) break;
@@ -408,15 +508,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16) + kEpiCols * half;
     uint32_t q = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+    for (int item = item_first<CL>(); item < p.ntiles && ok; item += item_stride<CL>()) {
       int tm, tn;
-      tile_of(p, tile, tm, tn);
+      item_tile<CL>(p, item, pair_rank<CL>(), tm, tn);
       const int m0 = tm * OBM, n0 = tn * OBN;
+      // the column exponents f_j of this warp's kEpiCols columns, two a lane
+      const int64_t gjl = n0 + kEpiCols * half + lane;
+      const int f_lo = gjl < p.N ? p.eb[gjl] : 0;
+      const int f_hi = gjl + 32 < p.N ? p.eb[gjl + 32] : 0;
       long long acc[kEpiCols];
 #pragma unroll
       for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
-      for (int g = 0; g < ngroups && ok; ++g) {
-        const Group G = group_of(p, S, g);
+      for (int gi = 0; gi < ngroups && ok; ++gi) {
+        const Group G = group_of(p, S, group_at(gi, ngroups));
         for (int c = 0; c < nchunks; ++c) {
           int okw = 1;
           if (lane == 0) okw = mbar_wait(accf, q & 1, st, p.wait_ns) ? 1 : 0;
@@ -452,20 +556,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       // output: alpha 2^(e_i + f_j - 2 beta - shift_top) acc + beta C, while
       // the MMAs of the next tile already run
+      // (every lane takes part in the shuffles; rows past M store nothing)
       const int64_t gi = m0 + row;
-      if (gi < p.M) {
-        const int ebase = p.ea[gi] - 2 * p.beta - p.shift_top;
-        const int64_t gj0 = n0 + kEpiCols * half;
+      const bool live_row = gi < p.M;
+      const int ebase = live_row ? p.ea[gi] - 2 * p.beta - p.shift_top : 0;
+      const int64_t gj0 = n0 + kEpiCols * half;
 #pragma unroll
-        for (int g = 0; g < kEpiCols / 8; ++g)
+      for (int g = 0; g < kEpiCols / 8; ++g) {
+        int f[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int cix = 8 * g + u;
+          f[u] = __shfl_sync(0xffffffffu, cix < 32 ? f_lo : f_hi, cix & 31);
+        }
+        if (live_row)
           store_out8(p, gi, gj0 + 8 * g, ebase, acc[8 * g], acc[8 * g + 1], acc[8 * g + 2],
                      acc[8 * g + 3], acc[8 * g + 4], acc[8 * g + 5], acc[8 * g + 6],
-                     acc[8 * g + 7]);
+                     acc[8 * g + 7], f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7]);
       }
     }
   }
   tc_fence_before();
   __syncthreads();
+  // neither CTA of a pair leaves while the other may still write its shared
+  // memory or arrive on its barriers
+  if (CL == 2) cluster_sync_all();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tbase, kGroupLevels * 128);
 }
@@ -725,50 +840,96 @@ void launch_rowmax(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk
 
 // ring stages: stage_tiles digit tiles per operand (all digits of one K step
 // for the widest group; several K steps for narrower groups)
-constexpr int kMaxSmem = 1024 + 3 * 2 * 8 * kDigitTile + (2 * 3 + 3) * 8 + 16;
-
-size_t oz_smem(int stage_tiles, int nstages) {
+__host__ __device__ constexpr size_t oz_smem_c(int stage_tiles, int nstages) {
   return 1024 + (size_t)nstages * 2 * stage_tiles * kDigitTile + (2 * nstages + 3) * 8 + 16;
 }
+// the largest configuration: S = 8, three stages of eight digit tiles per operand
+constexpr int kMaxSmem = (int)oz_smem_c(8, 3);
+static_assert(oz_smem_c(8, 3) <= 232448, "split kernel exceeds 227 KB of shared memory");
+static_assert(oz_smem_c(10, 2) <= oz_smem_c(8, 3), "S = 10 layout must fit the attribute");
 
-cudaError_t launch_oz(int ntiles, const CUtensorMap &mA, const CUtensorMap &mB,
+size_t oz_smem(int stage_tiles, int nstages) { return oz_smem_c(stage_tiles, nstages); }
+
+// Launch attributes of the four instantiations, set once: the shared-memory
+// size, and the check that the warpgroups' register split (setmaxnreg) adds
+// up to exactly kLaunchRegs a thread (a build that launches with any other
+// count is refused rather than run: an increase that cannot be met never
+// returns).  Also the most clusters of two that can be resident at once.
+template <int SC, int CL>
+cudaError_t oz_prepare(int &max_items) {
+  cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<SC, CL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, ozaki_gemm_kernel<SC, CL>);
+  if (e != cudaSuccess) return e;
+  if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if (CL == 1) {
+    max_items = nsm;
+    return cudaSuccess;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * (unsigned)nsm);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kMaxSmem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int ncl = 0;
+  e = cudaOccupancyMaxActiveClusters(&ncl, ozaki_gemm_kernel<SC, CL>, &cfg);
+  if (e != cudaSuccess) return e;
+  max_items = ncl > 0 ? ncl : 1;
+  return cudaSuccess;
+}
+
+template <int SC, int CL>
+cudaError_t launch_oz_t(int nitems, const CUtensorMap &mA, const CUtensorMap &mB,
+                        const CUtensorMap *m3, const OzParams &p, size_t smem, cudaStream_t st) {
+  static int max_items = 0;
+  static cudaError_t prep = cudaErrorNotReady;
+  static std::once_flag once;
+  std::call_once(once, [] { prep = oz_prepare<SC, CL>(max_items); });
+  if (prep != cudaSuccess) return prep;
+  // persistent: one CTA per SM (one fits: 512 TMEM columns, ~197 KB of
+  // shared memory), the CTAs (or pairs) taking every grid-th work item
+  const int items = nitems < max_items ? nitems : max_items;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(CL * items));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const CUtensorMap &a4 = SC == 8 ? m3[0] : mA, &b4 = SC == 8 ? m3[1] : mB;
+  const CUtensorMap &a8 = SC == 8 ? m3[2] : mA, &b8 = SC == 8 ? m3[3] : mB;
+  const CUtensorMap &b2 = SC == 8 ? m3[4] : mB;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<SC, CL>, mA, mB, a4, b4, a8, b8, b2, p);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_oz(int nitems, bool pairs, const CUtensorMap &mA, const CUtensorMap &mB,
                       const CUtensorMap *m3, const OzParams &p, cudaStream_t st) {
   const size_t smem = oz_smem(p.stage_tiles, p.nstages);
-  // persistent: one CTA per SM (at most one fits: 512 TMEM columns, ~197 KB
-  // of shared memory), each taking every grid-th tile
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-      nsm = 148;
-  }
-  const int grid = ntiles < nsm ? ntiles : nsm;
   if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<8>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ozaki_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kMaxSmem);
-    if (e != cudaSuccess) return e;
-    // the warpgroups' register split (setmaxnreg) adds up to exactly
-    // kLaunchRegs a thread; a build that launches with any other count is
-    // refused rather than run (an increase that cannot be met never returns)
-    cudaFuncAttributes fa8, fa0;
-    if (cudaFuncGetAttributes(&fa8, ozaki_gemm_kernel<8>) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa0, ozaki_gemm_kernel<0>) != cudaSuccess ||
-        fa8.numRegs != kLaunchRegs || fa0.numRegs != kLaunchRegs)
-      return cudaErrorInvalidConfiguration;
-    attr_set = true;
-  }
   if (p.S == 8)
-    ozaki_gemm_kernel<8><<<grid, kThreads, smem, st>>>(mA, mB, m3[0], m3[1], m3[2], m3[3], p);
-  else
-    ozaki_gemm_kernel<0><<<grid, kThreads, smem, st>>>(mA, mB, mA, mB, mA, mB, p);
-  count_launch();
-  return cudaGetLastError();
+    return pairs ? launch_oz_t<8, 2>(nitems, mA, mB, m3, p, smem, st)
+                 : launch_oz_t<8, 1>(nitems, mA, mB, m3, p, smem, st);
+  return pairs ? launch_oz_t<0, 2>(nitems, mA, mB, m3, p, smem, st)
+               : launch_oz_t<0, 1>(nitems, mA, mB, m3, p, smem, st);
 }
 
 cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
@@ -813,11 +974,12 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
     slice_kernel<<<gs, 256, 0, st>>>(B, N, K, bsr, bsk, mb, eb, S, beta, DB, (int)Npad, (int)Kpad);
     count_launch();
   }
-  CUtensorMap mA, mB, m3[4];
+  CUtensorMap mA, mB, m3[5];
   if (!make_map(&mA, DA, (int64_t)S * Mpad, Kpad) || !make_map(&mB, DB, (int64_t)S * Npad, Kpad))
     return cudaErrorInvalidValue;
   if (S == 8 && (!make_map3(&m3[0], DA, Mpad, Kpad, S, 4) || !make_map3(&m3[1], DB, Npad, Kpad, S, 4) ||
-                 !make_map3(&m3[2], DA, Mpad, Kpad, S, 8) || !make_map3(&m3[3], DB, Npad, Kpad, S, 8)))
+                 !make_map3(&m3[2], DA, Mpad, Kpad, S, 8) || !make_map3(&m3[3], DB, Npad, Kpad, S, 8) ||
+                 !make_map3(&m3[4], DB, Npad, Kpad, S, 2)))
     return cudaErrorInvalidValue;
   OzParams p;
   p.M = M;
@@ -846,6 +1008,7 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.lower = lower;
   p.alpha = alpha;
   p.betac = beta_c;
+  p.beta_mode = beta_c == 0.0 ? 0 : (beta_c == 1.0 ? 1 : 2);
   {
     int ax = 0;
     const double fr = frexp(alpha, &ax);  // alpha = fr 2^ax, |fr| in [0.5, 1)
@@ -862,8 +1025,17 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.wait_ns = p.no_loads ? 1000000ull : kWaitNs;  // 1 ms in the failure-path test
   const int tiles_m = (int)(Mpad / OBM);
   const int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
-  p.ntiles = ntiles;
-  return launch_oz(ntiles, mA, mB, m3, p, st);
+  // clusters of two on tile-row pairs (B shared through multicast) unless
+  // switched off or the output has a single tile row
+  const bool pairs = tune_get("ozaki_pairs", 1) != 0 && tiles_m >= 2;
+  if (pairs) {
+    const int T2 = (tiles_m + 1) / 2;
+    p.ntiles = lower ? (tiles_m % 2 == 0 ? T2 * (T2 + 1) : (T2 - 1) * T2 + tiles_m)
+                     : T2 * p.tiles_n;
+  } else {
+    p.ntiles = ntiles;
+  }
+  return launch_oz(p.ntiles, pairs, mA, mB, m3, p, st);
 }
 
 }  // namespace qmlgb

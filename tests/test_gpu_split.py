@@ -85,3 +85,51 @@ def test_split_syrk_shared_digits_lower(api):
     il, iu = np.tril_indices(k), np.triu_indices(k, 1)
     assert np.abs(out[il] - ref[il]).max() <= 1e-12 * np.abs(ref).max()
     assert np.array_equal(out[iu], W0[iu])
+
+
+@pytest.mark.parametrize("ta,tb,m,n,k,lower,beta", [
+    (1, 0, 700, 700, 300, True, 0.0),    # X^T X, 6 tile rows, shared digits
+    (0, 1, 640, 640, 512, True, 1.0),    # trailing-update shape, 5 tile rows
+    (0, 0, 300, 257, 1000, False, 1.0),  # 3 tile rows, ragged N
+    (1, 1, 129, 77, 33, False, 0.0),     # 2 tile rows, the second holds one row
+    (0, 0, 100, 300, 64, False, 0.0),    # one tile row: one CTA per tile
+])
+def test_split_pairs_match_single(api, ta, tb, m, n, k, lower, beta):
+    """Tile-row pairs in clusters of two (B digit tiles shared by multicast,
+    tuning key ozaki_pairs = 1, the default) give the same bits as one CTA
+    per tile (ozaki_pairs = 0), including tiles past the last row and, for a
+    lower C, tiles above the diagonal (computed, not stored)."""
+    rng = np.random.default_rng(m + 3 * n + 7 * k)
+    if lower and ta == 1:
+        A = rng.normal(size=(k, m))
+        B = A
+    elif lower:
+        A = rng.normal(size=(m, k))
+        B = A
+    else:
+        A = rng.normal(size=(k, m) if ta else (m, k))
+        B = rng.normal(size=(n, k) if tb else (k, n))
+    tbv = (not ta) if lower else bool(tb)
+    C0 = rng.normal(size=(m, n))
+    Ad = td(A)
+    Bd = Ad if B is A else td(B)
+    outs = []
+    try:
+        for pairs in (1, 0):
+            api.tune_set("ozaki_pairs", pairs)
+            Cd = td(C0)
+            api.gemm(Ad, Bd, Cd, transA=bool(ta), transB=tbv, alpha=-1.0 if beta else 1.0,
+                     beta=beta, lower=lower, precision=SPLIT)
+            outs.append(Cd.cpu().numpy())
+    finally:
+        api.tune_set("ozaki_pairs", 1)
+    assert np.array_equal(outs[0], outs[1])
+    opA = A.T if ta else A
+    opB = B.T if tbv else B
+    ref = (-1.0 if beta else 1.0) * (opA @ opB) + beta * C0
+    if lower:
+        il, iu = np.tril_indices(m), np.triu_indices(m, 1)
+        assert np.abs(outs[0][il] - ref[il]).max() <= 1e-12 * np.abs(ref).max()
+        assert np.array_equal(outs[0][iu], C0[iu])
+    else:
+        assert np.abs(outs[0] - ref).max() <= 1e-12 * np.abs(ref).max()
