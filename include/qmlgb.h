@@ -351,6 +351,14 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *                   layer through the WMMA product
  *   emu_tc0         1 (default) / 0: with emu_tc, the first layer (16
  *                   inputs, widened with zeros to 64) on tcgen05 too / WMMA
+ *   split_lookahead 1 (default) / 0: the split-precision Cholesky runs the
+ *                   next panel's float64 diagonal chain on a second,
+ *                   high-priority stream beside the trailing update and the
+ *                   forward substitution (not while the stream is being
+ *                   captured) / everything in order on the caller's stream;
+ *                   the results are bit-identical
+ *   split_lookahead_sms  8 (default): SMs the split kernel leaves free for
+ *                   that chain while they overlap
  *   split_diag_df   0 (default) / 1: the split-precision Cholesky factors
  *                   its 64-wide diagonal blocks and their row solves in
  *                   float64 / in float-float (about 2^-46 per operation)

@@ -334,25 +334,27 @@ void trsm_blocked_t(Call &c, const double *L, int64_t n, int64_t lda, const doub
 // left block -R^-1 T, each one batched product over the pairs (a last pair
 // whose second block is shorter than b gets its own two products).  log2 of
 // the block count steps instead of one per block row; T (scratch) holds
-// (kNBS/2)^2 doubles.
+// (kNBS/2)^2 doubles.  On stream st; with fixed the float64 products skip
+// the tile autotuner (which synchronises), as work on a second stream must.
 void trinv_doubling(Call &c, const double *L, int64_t jb, int64_t lda, const double *Linv,
-                    double *X, int64_t ldx, double *T) {
-  launch_place_diag_inverses(Linv, jb, X, ldx, c.st);
+                    double *X, int64_t ldx, double *T, cudaStream_t st, bool fixed) {
+  auto gemm = fixed ? launch_dgemm_fixed : launch_dgemm;
+  launch_place_diag_inverses(Linv, jb, X, ldx, st);
   for (int64_t b = kNB; b < jb; b *= 2) {
     const int64_t full = jb / (2 * b);  // pairs with both blocks b long
     if (full > 0) {
       const int64_t sL = 2 * b + 2 * b * lda, sX = 2 * b + 2 * b * ldx;
       launch_dgemm_batched(0, 0, b, b, b, 1.0, L + b, lda, sL, X, ldx, sX, 0.0, T, b, b * b,
-                           (int)full, c.status, c.st);
+                           (int)full, c.status, st);
       launch_dgemm_batched(0, 0, b, b, b, -1.0, X + b + b * ldx, ldx, sX, T, b, b * b, 0.0, X + b,
-                           ldx, sX, (int)full, c.status, c.st);
+                           ldx, sX, (int)full, c.status, st);
     }
     const int64_t r0 = full * 2 * b, b2 = jb - r0 - b;  // a last pair with a short R
     if (b2 > 0) {
-      launch_dgemm(0, 0, b2, b, b, 1.0, L + (r0 + b) + r0 * lda, lda, X + r0 + r0 * ldx, ldx, 0.0,
-                   T, b2, 0, c.status, c.st);
-      launch_dgemm(0, 0, b2, b, b2, -1.0, X + (r0 + b) + (r0 + b) * ldx, ldx, T, b2, 0.0,
-                   X + (r0 + b) + r0 * ldx, ldx, 0, c.status, c.st);
+      gemm(0, 0, b2, b, b, 1.0, L + (r0 + b) + r0 * lda, lda, X + r0 + r0 * ldx, ldx, 0.0, T, b2,
+           0, c.status, st);
+      gemm(0, 0, b2, b, b2, -1.0, X + (r0 + b) + (r0 + b) * ldx, ldx, T, b2, 0.0,
+           X + (r0 + b) + r0 * ldx, ldx, 0, c.status, st);
     }
   }
 }
@@ -379,6 +381,8 @@ constexpr int64_t kNBS = 512;
 struct Split {
   Call *c;
   int nslices;
+  // SMs the split kernel leaves free (for float64 work on a second stream)
+  int reserve_sms = 0;
   void *ws = nullptr;
   size_t ws_bytes = 0;
   double *tinv = nullptr;  // (kNBS/2)^2 scratch of the block-inverse doubling
@@ -407,69 +411,151 @@ struct Split {
     const bool shared = (A == B && lda == ldb && ta != tb && M == N);
     if (!reserve(M, N, K, shared)) return;
     c->cuda_ok(ozaki_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower, nslices,
-                          ws, c->status, c->st),
+                          ws, c->status, c->st, reserve_sms),
                "split-precision gemm");
   }
 };
 
+// The float64 part of the split Cholesky for the panel of columns j .. j + jb
+// of A (its diagonal block already updated by every earlier panel), on stream
+// st: the diagonal block factored 64 columns at a time (the 64-block factor
+// leaves the coefficients of its row solve in the slot of its inverse; the
+// rows below are solved by forward substitution, in place and into T (m2 x 64
+// <= (kNBS - kNB) x kNB), whose product with itself updates the rest, out of
+// place so it can take small tiles), then the inverses of the 64-blocks (one
+// launch, a CTA each) and the explicit inverse of the whole block into
+// LinvB's slot (float64, recursive doubling).  With split_diag_df the
+// 64-blocks and their row solves run in float-float instead (about 2^-46 per
+// operation; the factor goes to the inverse slot, the coefficients to S behind
+// T's panel part).  fixed: float64 products without the tile autotuner.
+void panel_chain(Call &c, Split &sp, double *A, int64_t lda, int64_t j, int64_t jb,
+                 double *Linv64, double *LinvB, double *ldparts, bool dfdiag, cudaStream_t st,
+                 bool fixed) {
+  auto gemm = fixed ? launch_dgemm_fixed : launch_dgemm;
+  double *Ajj = A + j + j * lda;
+  double *T = sp.tinv_scratch();  // (kNBS/2)^2 doubles: the panel block below, then the doubling
+  if (!T) return;
+  double *S = T + (int64_t)(kNBS - kNB) * kNB;
+  for (int64_t i = 0; i < jb; i += kNB) {
+    const int64_t ib = (jb - i) < kNB ? (jb - i) : kNB;
+    double *Lb = Linv64 + ((j + i) / kNB) * kNB * kNB;
+    double *Ab = A + (j + i) + (j + i) * lda;
+    if (dfdiag)
+      launch_potrf_diag_df(Ab, lda, j + jb, j + i, Lb, S, c.status, st);
+    else
+      launch_potrf_diag_factor(Ab, lda, j + jb, j + i, Lb, ldparts + (j + i) / kNB, c.status, st);
+    if (i + ib < jb) {
+      const int64_t m2 = jb - i - ib;
+      double *A21 = Ajj + (i + ib) + i * lda;
+      double *A22 = Ajj + (i + ib) + (i + ib) * lda;
+      if (dfdiag)
+        launch_trsm_rows_df(S, ib, A21, lda, m2, T, m2, c.status, st);
+      else
+        launch_trsm_rows(Lb, ib, A21, lda, m2, T, m2, c.status, st);
+      gemm(0, 1, m2, m2, ib, -1.0, T, m2, T, m2, 1.0, A22, lda, 1, c.status, st);
+    }
+  }
+  if (dfdiag)
+    launch_trtri_blocks_df(Ajj, lda, jb, Linv64 + (j / kNB) * kNB * kNB, ldparts + j / kNB,
+                           c.status, st);
+  else
+    launch_trtri_blocks(Ajj, lda, jb, Linv64 + (j / kNB) * kNB * kNB, c.status, st);
+  trinv_doubling(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, LinvB + (j / kNBS) * kNBS * kNBS,
+                 kNBS, T, st, fixed);
+}
+
 // Cholesky A = L L^T (lower, in place).  Linv64: inverses of the 64-blocks
 // (n/64 blocks of 64x64); LinvB: explicit inverses of the kNBS diagonal blocks
-// (ceil(n/kNBS) blocks of kNBS x kNBS, ld kNBS).
+// (ceil(n/kNBS) blocks of kNBS x kNBS, ld kNBS).  Panels of kNBS columns: the
+// float64 chain of the diagonal block (panel_chain), then the panel solve
+// A21 <- A21 L_jj^-T (a product with the explicit inverse) and the trailing
+// update A22 <- A22 - A21 A21^T (lower) as split-precision products.  With a
+// right-hand side B (n x nrhs, ld ldb) the forward substitution B <- L^-1 B
+// runs panel by panel in the same loop: B_j <- L_jj^-1 B_j and
+// B_below <- B_below - A21 B_j as soon as panel j is final.
+//
+// Lookahead (tuning key split_lookahead, default 1; off while the stream is
+// being captured): the trailing update is split into the next panel's columns
+// and the rest; right after the first part, the next panel's float64 chain
+// starts on a second, high-priority stream, while the main stream runs the
+// rest of the trailing update and panel j's substitution on B with
+// split_lookahead_sms SMs (default 8) left free for the chain.  The float64
+// chain (about 0.8 ms a panel at n = 5952) then hides behind split products.
+// Every output is the same product as without lookahead (the split product
+// of an element depends only on its own row and column), so the results are
+// bit-identical.
 void potrf_split(Call &c, Split &sp, double *A, int64_t n, int64_t lda, double *Linv64,
-                 double *LinvB, double *ldparts, double *logdet) {
+                 double *LinvB, double *ldparts, double *logdet, double *B = nullptr,
+                 int64_t nrhs = 0, int64_t ldb = 0) {
   const bool dfdiag = tune_get("split_diag_df", 0) != 0;
-  for (int64_t j = 0; j < n; j += kNBS) {
+  if (!sp.tinv_scratch()) return;  // allocated on the main stream before any use
+  bool look = tune_get("split_lookahead", 1) != 0 && n > kNBS;
+  if (look) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c.st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      look = false;
+  }
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t e_next = nullptr, e_diag = nullptr;
+  if (look) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    look = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi) == cudaSuccess &&
+           cudaEventCreateWithFlags(&e_next, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&e_diag, cudaEventDisableTiming) == cudaSuccess;
+  }
+  const int reserve = look ? (int)tune_get("split_lookahead_sms", 8) : 0;
+  panel_chain(c, sp, A, lda, 0, n < kNBS ? n : kNBS, Linv64, LinvB, ldparts, dfdiag, c.st, false);
+  for (int64_t j = 0; j < n && c.err == QML_OK; j += kNBS) {
     const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
-    double *Ajj = A + j + j * lda;
-    double *T = sp.tinv_scratch();  // (kNBS/2)^2 doubles: the panel block below, then the doubling
-    if (!T) return;
-    // blocked factorisation of the diagonal block, 64-wide, in float64.  The
-    // 64-block factor leaves the coefficients of its row solve in the slot of
-    // its inverse; the rows below are solved by forward substitution, in
-    // place and into T (m2 x 64 <= (kNBS - kNB) x kNB), whose product with
-    // itself updates the rest (out of place, so it can take small tiles).
-    // With split_diag_df the 64-blocks and their row solves run in
-    // float-float instead (about 2^-46 per operation; the factor goes to the
-    // inverse slot, the coefficients to S behind T's panel part).
-    double *S = T + (int64_t)(kNBS - kNB) * kNB;
-    for (int64_t i = 0; i < jb; i += kNB) {
-      const int64_t ib = (jb - i) < kNB ? (jb - i) : kNB;
-      double *Lb = Linv64 + ((j + i) / kNB) * kNB * kNB;
-      double *Ab = A + (j + i) + (j + i) * lda;
-      if (dfdiag)
-        launch_potrf_diag_df(Ab, lda, j + jb, j + i, Lb, S, c.status, c.st);
-      else
-        launch_potrf_diag_factor(Ab, lda, j + jb, j + i, Lb, ldparts + (j + i) / kNB, c.status,
-                                 c.st);
-      if (i + ib < jb) {
-        const int64_t m2 = jb - i - ib;
-        double *A21 = Ajj + (i + ib) + i * lda;
-        double *A22 = Ajj + (i + ib) + (i + ib) * lda;
-        if (dfdiag)
-          launch_trsm_rows_df(S, ib, A21, lda, m2, T, m2, c.status, c.st);
-        else
-          launch_trsm_rows(Lb, ib, A21, lda, m2, T, m2, c.status, c.st);
-        launch_dgemm(0, 1, m2, m2, ib, -1.0, T, m2, T, m2, 1.0, A22, lda, 1, c.status, c.st);
+    const double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
+    // panel j's chain ran on the second stream
+    if (look && j > 0) c.cuda_ok(cudaStreamWaitEvent(c.st, e_diag, 0), "lookahead");
+    double *A21 = A + (j + jb) + j * lda;
+    const int64_t m2 = n - j - jb;
+    if (m2 > 0) {
+      double *A22 = A + (j + jb) + (j + jb) * lda;
+      const int64_t jb2 = m2 < kNBS ? m2 : kNBS;
+      // panel: A21 <- A21 L_jj^-T
+      sp.gemm(0, 1, m2, jb, jb, 1.0, A21, lda, Xinv, kNBS, 0.0, A21, lda, 0);
+      if (look) {
+        // the next panel's columns first: its diagonal block (lower) and the
+        // rows below it; then its chain starts on the second stream
+        sp.gemm(0, 1, jb2, jb2, jb, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1);
+        if (m2 > jb2)
+          sp.gemm(0, 1, m2 - jb2, jb2, jb, -1.0, A21 + jb2, lda, A21, lda, 1.0, A22 + jb2, lda,
+                  0);
+        c.cuda_ok(cudaEventRecord(e_next, c.st), "lookahead");
+        c.cuda_ok(cudaStreamWaitEvent(s2, e_next, 0), "lookahead");
+        panel_chain(c, sp, A, lda, j + jb, jb2, Linv64, LinvB, ldparts, dfdiag, s2, true);
+        c.cuda_ok(cudaEventRecord(e_diag, s2), "lookahead");
+        sp.reserve_sms = reserve;
+        if (m2 > jb2)
+          sp.gemm(0, 1, m2 - jb2, m2 - jb2, jb, -1.0, A21 + jb2, lda, A21 + jb2, lda, 1.0,
+                  A22 + jb2 + jb2 * lda, lda, 1);
+      } else {
+        sp.gemm(0, 1, m2, m2, jb, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1);
       }
     }
-    // inverses of the 64-blocks (one launch, a CTA each; from the float-float
-    // slots also the float64 factor and its log det parts), then the explicit
-    // inverse of the diagonal block (float64)
-    if (dfdiag)
-      launch_trtri_blocks_df(Ajj, lda, jb, Linv64 + (j / kNB) * kNB * kNB, ldparts + j / kNB,
-                             c.status, c.st);
-    else
-      launch_trtri_blocks(Ajj, lda, jb, Linv64 + (j / kNB) * kNB * kNB, c.status, c.st);
-    double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
-    trinv_doubling(c, Ajj, jb, lda, Linv64 + (j / kNB) * kNB * kNB, Xinv, kNBS, T);
-    if (j + jb < n) {
-      const int64_t m2 = n - j - jb;
-      double *A21 = A + (j + jb) + j * lda;
-      double *A22 = A + (j + jb) + (j + jb) * lda;
-      // panel: A21 <- A21 L_jj^-T ; trailing: A22 <- A22 - A21 A21^T (lower)
-      sp.gemm(0, 1, m2, jb, jb, 1.0, A21, lda, Xinv, kNBS, 0.0, A21, lda, 0);
-      sp.gemm(0, 1, m2, m2, jb, -1.0, A21, lda, A21, lda, 1.0, A22, lda, 1);
+    if (B) {
+      // forward substitution, panel j: B_j <- L_jj^-1 B_j ; B_below -= A21 B_j
+      sp.gemm(0, 0, jb, nrhs, jb, 1.0, Xinv, kNBS, B + j, ldb, 0.0, B + j, ldb, 0);
+      if (m2 > 0)
+        sp.gemm(0, 0, m2, nrhs, jb, -1.0, A21, lda, B + j, ldb, 1.0, B + j + jb, ldb, 0);
     }
+    sp.reserve_sms = 0;
+    if (!look && m2 > 0)
+      panel_chain(c, sp, A, lda, j + jb, m2 < kNBS ? m2 : kNBS, Linv64, LinvB, ldparts, dfdiag,
+                  c.st, false);
+  }
+  if (look) {
+    // nothing of the second stream outlives this call: the main stream waits
+    // for all of it (the last chain was waited for already; this covers an
+    // early exit on error)
+    if (cudaEventRecord(e_diag, s2) == cudaSuccess) cudaStreamWaitEvent(c.st, e_diag, 0);
+    cudaEventDestroy(e_next);
+    cudaEventDestroy(e_diag);
+    cudaStreamDestroy(s2);
   }
   if (logdet) launch_sum_logdet(ldparts, (int)((n + kNB - 1) / kNB), logdet, c.st);
 }
@@ -815,15 +901,15 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
     // C = Y_sig Lambda Y_sig^T + N ; L L^T = C ; X = L^-1 Y_win ; W = X^T X
     add_band_signal(c, sp_or_null, sp, d, d.lsig0, d.lsig1, ldcl,
                     scratch_for(d.nc * band_k0(d.lsig0, d.lsig1)), plan->L);
-    if (plan->split)
-      potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr);
-    else
-      potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
-    launch_ybuild(sp.y, plan->X, d.n, c.st);
+    launch_ybuild(sp.y, plan->X, d.n, c.st);  // X no longer holds the band signal
     if (plan->split) {
-      trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, plan->X, d.k, d.n);
+      // factor and X = L^-1 Y in one panel loop (the forward substitution
+      // runs beside the next panel's float64 chain)
+      potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr, plan->X,
+                  d.k, d.n);
       spl.gemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1);
     } else {
+      potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
       trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
       launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1,
                    c.status, c.st);
@@ -837,16 +923,14 @@ qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan_out, v
     if (d.lsig1 > d.lmax)
       add_band_signal(c, sp_or_null, sp, d, d.lmax + 1, d.lsig1, ldcl,
                       scratch_for(d.nc * band_k0(d.lmax + 1, d.lsig1)), plan->L);
-    if (plan->split)
-      potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr);
-    else
-      potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
     // U = L_N^-1 Y_win ; M = U^T U (the noise-weighted Gramian Y^T N^-1 Y)
     launch_ybuild(sp.y, plan->X, d.n, c.st);
     if (plan->split) {
-      trsm_split(c, spl, plan->L, d.n, d.n, plan->LinvB, plan->X, d.k, d.n);
+      potrf_split(c, spl, plan->L, d.n, d.n, plan->Linv, plan->LinvB, ldparts, nullptr, plan->X,
+                  d.k, d.n);
       spl.gemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1);
     } else {
+      potrf_blocked(c, plan->L, d.n, d.n, plan->Linv, ldparts, nullptr);
       trsm_blocked(c, plan->L, d.n, d.n, plan->Linv, plan->X, d.k, d.n);
       launch_dgemm(1, 0, d.k, d.k, d.n, 1.0, plan->X, d.n, plan->X, d.n, 0.0, W, d.k, 1,
                    c.status, c.st);
@@ -953,9 +1037,8 @@ qml_status pix_loglike(const qml_problem *prob, const double *cl_theta, const do
     double *LinvB = c.alloc<double>((size_t)((d.n + kNBS - 1) / kNBS) * kNBS * kNBS);
     if (!LinvB) return c.finish();
     build_C_split(c, spl, sp, d, Y, C);
-    potrf_split(c, spl, C, d.n, d.n, Linv, LinvB, ldparts, o_ld);
     launch_copy_matrix(D, d.n, U, d.n, d.n, nmaps, c.st);
-    trsm_split(c, spl, C, d.n, d.n, LinvB, U, nmaps, d.n);
+    potrf_split(c, spl, C, d.n, d.n, Linv, LinvB, ldparts, o_ld, U, nmaps, d.n);
   } else {
     build_C(c, sp, d, Y, C);
     potrf_blocked(c, C, d.n, d.n, Linv, ldparts, o_ld);
@@ -1325,7 +1408,8 @@ qml_status qml_trsm(int64_t n, int64_t nrhs, const double *L, int64_t lda, doubl
     for (int64_t j = 0; j < n; j += kNBS) {
       const int64_t jb = (n - j) < kNBS ? (n - j) : kNBS;
       double *Xinv = LinvB + (j / kNBS) * kNBS * kNBS;
-      trinv_doubling(c, Ld + j + j * lda, jb, lda, Linv + (j / kNB) * kNB * kNB, Xinv, kNBS, T);
+      trinv_doubling(c, Ld + j + j * lda, jb, lda, Linv + (j / kNB) * kNB * kNB, Xinv, kNBS, T,
+                     c.st, false);
     }
     trsm_split(c, spl, Ld, n, lda, LinvB, Bd, nrhs, ldb);
   } else {

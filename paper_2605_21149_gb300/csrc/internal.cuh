@@ -205,9 +205,10 @@ void launch_batch_finish(const double *rr, const double *dnd, const double *lnN,
 // must hold ozaki_workspace_bytes(...) bytes.  nslices = 0 picks the default.
 void ozaki_choose(int64_t K, int nslices, int &S, int &beta);
 size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K, int nslices, bool shared_operand);
+// reserve_sms: SMs the persistent kernel leaves free for other work.
 cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta_c,
                        double *C, int64_t ldc, int lower, int nslices, void *work,
-                       DevStatus *status, cudaStream_t st);
+                       DevStatus *status, cudaStream_t st, int reserve_sms = 0);
 
 }  // namespace qmlgb

@@ -670,73 +670,91 @@ __device__ __forceinline__ long long scaled_round(double x, int sh) {
   return bits < 0 ? -(long long)q : (long long)q;
 }
 
-// digits of one logical matrix X (R x K, element (r,k) at X[r sr + k sk]) into
-// D[s][r][k] (bf16, rows Rpad, K-contiguous rows of Kpad): F = round(x 2^(beta S
-// - e_r)) as an integer, then signed digits from the bottom, each in
-// [-2^(beta-1), 2^(beta-1)), the top one in [-2^beta, 2^beta].  Tile 32 x 64 via
-// shared memory so both the read and the K-contiguous write coalesce.
-__global__ void slice_kernel(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk,
-                             const unsigned long long *bits, int *e, int S, int beta,
-                             __nv_bfloat16 *D, int Rpad, int Kpad) {
-  __shared__ double tile[32][65];
-  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
+// The S digits of two adjacent elements x0, x1 (k, k + 1) of row r with row
+// exponent er into the digit planes D[s][r][k] (rows Rpad, Kpad per row):
+// F = round(x 2^(beta S - er)) as an integer, then signed digits from the
+// bottom, each in [-2^(beta-1), 2^(beta-1)), the top one in [-2^beta, 2^beta].
+// Digit i (from the bottom, i < S - 1) by the signed base-2^beta recurrence
+// d = ((F + 2^(beta-1)) mod 2^beta) - 2^(beta-1), F <- (F - d) / 2^beta, run
+// on chunks of up to 4 digits in 32-bit arithmetic (the chunk's carry joins
+// the rest of F at its end); digit S - 1 is what remains.
+__device__ __forceinline__ void slice_pair(double x0, double x1, int er, int S, int beta,
+                                           __nv_bfloat16 *D, int Rpad, int Kpad, int64_t r,
+                                           int64_t k) {
+  long long Fh[2];
+  int lo[2] = {0, 0};
+  Fh[0] = scaled_round(x0, beta * S - er);
+  Fh[1] = scaled_round(x1, beta * S - er);
+  const int half = 1 << (beta - 1), mask = (1 << beta) - 1;
+#pragma unroll
+  for (int i = 0; i < kMaxSlices; ++i) {
+    if (i >= S) break;
+    int d[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (i < S - 1) {
+        if ((i & 3) == 0) {
+          const int nd = (S - 1 - i) < 4 ? (S - 1 - i) : 4;
+          const int nb = beta * nd;
+          lo[h] = (int)(Fh[h] & ((1LL << nb) - 1));
+          Fh[h] >>= nb;
+        }
+        d[h] = ((lo[h] + half) & mask) - half;
+        lo[h] = (lo[h] - d[h]) >> beta;
+        if ((i & 3) == 3 || i == S - 2) Fh[h] += lo[h];
+      } else {
+        d[h] = (int)Fh[h];
+      }
+    }
+    // digit i from the bottom is digit s = S - i of the expansion
+    __nv_bfloat162 v = __floats2bfloat162_rn((float)d[0], (float)d[1]);
+    *(__nv_bfloat162 *)(D + ((int64_t)(S - i - 1) * Rpad + r) * Kpad + k) = v;
+  }
+}
+
+// One 32 x 64 tile of X (rows r0.., k0..; element (r, k) at X[r sr + k sk],
+// zero outside R x K) into shared memory, read coalesced along whichever of
+// r and k is contiguous.
+__device__ __forceinline__ void load_tile32x64(double (*tile)[65], const double *X, int64_t R,
+                                               int64_t K, int64_t sr, int64_t sk, int64_t r0,
+                                               int64_t k0) {
   const int tid = threadIdx.x;  // 256 threads
   if (sk == 1) {
     // k contiguous: 64 consecutive k per row
     for (int t = tid; t < 32 * 64; t += 256) {
-      int rr = t / 64, kk = t % 64;
-      int64_t r = r0 + rr, k = k0 + kk;
+      const int rr = t / 64, kk = t % 64;
+      const int64_t r = r0 + rr, k = k0 + kk;
       tile[rr][kk] = (r < R && k < K) ? X[r * sr + k] : 0.0;
     }
   } else {
     // r contiguous: 32 consecutive r per k
     for (int t = tid; t < 32 * 64; t += 256) {
-      int rr = t % 32, kk = t / 32;
-      int64_t r = r0 + rr, k = k0 + kk;
+      const int rr = t % 32, kk = t / 32;
+      const int64_t r = r0 + rr, k = k0 + kk;
       tile[rr][kk] = (r < R && k < K) ? X[r + k * sk] : 0.0;
     }
   }
+}
+
+// digits of one logical matrix X (R x K) into D[s][r][k] (bf16, rows Rpad,
+// K-contiguous rows of Kpad), from row maxima already in bits: one 32 x 64
+// tile per block via shared memory, so both the read and the K-contiguous
+// write coalesce.
+__global__ void slice_kernel(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+                             const unsigned long long *bits, int *e, int S, int beta,
+                             __nv_bfloat16 *D, int Rpad, int Kpad) {
+  __shared__ double tile[32][65];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
+  load_tile32x64(tile, X, R, K, sr, sk, r0, k0);
   __syncthreads();
-  // each thread: one row rr, two adjacent k (kk, kk+1)
-  const int rr = tid / 32, kp = (tid % 32) * 2;
+  // each thread: one row rq, two adjacent k (kp, kp + 1)
+  const int tid = threadIdx.x, rr = tid / 32, kp = (tid % 32) * 2;
   for (int rq = rr; rq < 32; rq += 8) {
     const int64_t r = r0 + rq;
     if (r >= Rpad) continue;
     const int er = (r < R) ? exponent_of(bits[r]) : 0;
     if (blockIdx.x == 0 && kp == 0) e[r] = er;
-    // digit i (from the bottom, i < S - 1): the signed base-2^beta recurrence
-    // d = ((F + 2^(beta-1)) mod 2^beta) - 2^(beta-1), F <- (F - d) / 2^beta,
-    // run on chunks of up to 4 digits in 32-bit arithmetic (the chunk's carry
-    // joins the rest of F at its end); digit S - 1 is what remains
-    long long Fh[2];
-    int lo[2] = {0, 0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) Fh[h] = scaled_round(tile[rq][kp + h], beta * S - er);
-    const int half = 1 << (beta - 1), mask = (1 << beta) - 1;
-#pragma unroll
-    for (int i = 0; i < kMaxSlices; ++i) {
-      if (i >= S) break;
-      int d[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (i < S - 1) {
-          if ((i & 3) == 0) {
-            const int nd = (S - 1 - i) < 4 ? (S - 1 - i) : 4;
-            const int nb = beta * nd;
-            lo[h] = (int)(Fh[h] & ((1LL << nb) - 1));
-            Fh[h] >>= nb;
-          }
-          d[h] = ((lo[h] + half) & mask) - half;
-          lo[h] = (lo[h] - d[h]) >> beta;
-          if ((i & 3) == 3 || i == S - 2) Fh[h] += lo[h];
-        } else {
-          d[h] = (int)Fh[h];
-        }
-      }
-      // digit i from the bottom is digit s = S - i of the expansion
-      __nv_bfloat162 v = __floats2bfloat162_rn((float)d[0], (float)d[1]);
-      *(__nv_bfloat162 *)(D + ((int64_t)(S - i - 1) * Rpad + r) * Kpad + k0 + kp) = v;
-    }
+    slice_pair(tile[rq][kp], tile[rq][kp + 1], er, S, beta, D, Rpad, Kpad, r, k0 + kp);
   }
 }
 
@@ -891,7 +909,7 @@ cudaError_t oz_prepare(int &max_items) {
 }
 
 template <int SC, int CL>
-cudaError_t launch_oz_t(int nitems, const CUtensorMap &mA, const CUtensorMap &mB,
+cudaError_t launch_oz_t(int nitems, int reserve_sms, const CUtensorMap &mA, const CUtensorMap &mB,
                         const CUtensorMap *m3, const OzParams &p, size_t smem, cudaStream_t st) {
   static int max_items = 0;
   static cudaError_t prep = cudaErrorNotReady;
@@ -899,8 +917,11 @@ cudaError_t launch_oz_t(int nitems, const CUtensorMap &mA, const CUtensorMap &mB
   std::call_once(once, [] { prep = oz_prepare<SC, CL>(max_items); });
   if (prep != cudaSuccess) return prep;
   // persistent: one CTA per SM (one fits: 512 TMEM columns, ~197 KB of
-  // shared memory), the CTAs (or pairs) taking every grid-th work item
-  const int items = nitems < max_items ? nitems : max_items;
+  // shared memory), the CTAs (or pairs) taking every grid-th work item;
+  // reserve_sms SMs (rounded up to whole pairs) stay free for other streams
+  int cap = max_items - (reserve_sms + CL - 1) / CL;
+  if (cap < 1) cap = 1;
+  const int items = nitems < cap ? nitems : cap;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(CL * items));
   cfg.blockDim = dim3(kThreads);
@@ -921,21 +942,23 @@ cudaError_t launch_oz_t(int nitems, const CUtensorMap &mA, const CUtensorMap &mB
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t launch_oz(int nitems, bool pairs, const CUtensorMap &mA, const CUtensorMap &mB,
-                      const CUtensorMap *m3, const OzParams &p, cudaStream_t st) {
+cudaError_t launch_oz(int nitems, bool pairs, int reserve_sms, const CUtensorMap &mA,
+                      const CUtensorMap &mB, const CUtensorMap *m3, const OzParams &p,
+                      cudaStream_t st) {
   const size_t smem = oz_smem(p.stage_tiles, p.nstages);
   if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
+  const int rsv = reserve_sms > 0 ? reserve_sms : 0;
   if (p.S == 8)
-    return pairs ? launch_oz_t<8, 2>(nitems, mA, mB, m3, p, smem, st)
-                 : launch_oz_t<8, 1>(nitems, mA, mB, m3, p, smem, st);
-  return pairs ? launch_oz_t<0, 2>(nitems, mA, mB, m3, p, smem, st)
-               : launch_oz_t<0, 1>(nitems, mA, mB, m3, p, smem, st);
+    return pairs ? launch_oz_t<8, 2>(nitems, rsv, mA, mB, m3, p, smem, st)
+                 : launch_oz_t<8, 1>(nitems, rsv, mA, mB, m3, p, smem, st);
+  return pairs ? launch_oz_t<0, 2>(nitems, rsv, mA, mB, m3, p, smem, st)
+               : launch_oz_t<0, 1>(nitems, rsv, mA, mB, m3, p, smem, st);
 }
 
 cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta_c,
                        double *C, int64_t ldc, int lower, int nslices, void *work,
-                       DevStatus *status, cudaStream_t st) {
+                       DevStatus *status, cudaStream_t st, int reserve_sms) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   int S, beta;
   ozaki_choose(K, nslices, S, beta);
@@ -967,12 +990,13 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
     dim3 gs((unsigned)(Kpad / 64), (unsigned)(Mpad / 32));
     slice_kernel<<<gs, 256, 0, st>>>(A, M, K, asr, ask, ma, ea, S, beta, DA, (int)Mpad, (int)Kpad);
     count_launch();
-  }
-  if (!shared) {
-    launch_rowmax(B, N, K, bsr, bsk, mb, Npad, st);
-    dim3 gs((unsigned)(Kpad / 64), (unsigned)(Npad / 32));
-    slice_kernel<<<gs, 256, 0, st>>>(B, N, K, bsr, bsk, mb, eb, S, beta, DB, (int)Npad, (int)Kpad);
-    count_launch();
+    if (!shared) {
+      launch_rowmax(B, N, K, bsr, bsk, mb, Npad, st);
+      dim3 gb((unsigned)(Kpad / 64), (unsigned)(Npad / 32));
+      slice_kernel<<<gb, 256, 0, st>>>(B, N, K, bsr, bsk, mb, eb, S, beta, DB, (int)Npad,
+                                       (int)Kpad);
+      count_launch();
+    }
   }
   CUtensorMap mA, mB, m3[5];
   if (!make_map(&mA, DA, (int64_t)S * Mpad, Kpad) || !make_map(&mB, DB, (int64_t)S * Npad, Kpad))
@@ -1035,7 +1059,7 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   } else {
     p.ntiles = ntiles;
   }
-  return launch_oz(p.ntiles, pairs, mA, mB, m3, p, st);
+  return launch_oz(p.ntiles, pairs, reserve_sms, mA, mB, m3, p, st);
 }
 
 }  // namespace qmlgb

@@ -133,3 +133,4 @@ def test_split_pairs_match_single(api, ta, tb, m, n, k, lower, beta):
         assert np.array_equal(outs[0][iu], C0[iu])
     else:
         assert np.abs(outs[0] - ref).max() <= 1e-12 * np.abs(ref).max()
+

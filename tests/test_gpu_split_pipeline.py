@@ -75,3 +75,50 @@ def test_split_tqu_nside16_float_float_diagonal(api):
         _check(api, synth.workload(1), nsims=4)
     finally:
         api.tune_set("split_diag_df", 0)
+
+
+@pytest.mark.parametrize("basis", [0, 1])
+def test_split_lookahead_bit_identical(api, basis):
+    """Lookahead in the split Cholesky (the next panel's float64 chain on a
+    second stream beside the trailing update and the forward substitution,
+    tuning key split_lookahead = 1, the default) changes when kernels run, not
+    what they compute: F, b, y, every normalisation and lnL equal the
+    single-stream order bit for bit (TQU Nside 16, twelve 512 panels; the
+    harmonic basis factors N the same way)."""
+    wl = synth.workload(1)
+    Y, alm, noise, maps = P.oracle_maps(wl, 3)
+    prob = api.Problem.from_workload(wl, precision=SPLIT, basis=basis)
+    cl = torch.as_tensor(wl.cl_fid.reshape(-1), device="cuda")
+    outs = []
+    try:
+        for look in (1, 0):
+            api.tune_set("split_lookahead", look)
+            F, plan = api.fisher(prob)
+            est = plan.estimate(td(maps))
+            plan.free()
+            lnl, chi2, ld = api.loglike(prob, cl, td(maps))
+            outs.append([P.to_np(F)] + [P.to_np(est[k]) for k in sorted(est)] +
+                        [P.to_np(lnl), P.to_np(chi2), np.atleast_1d(P.to_np(ld))])
+    finally:
+        api.tune_set("split_lookahead", 1)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_split_potrf_lookahead_bit_identical(api):
+    """qml_potrf in split precision (n = 1700: four panels, the last one
+    ragged) with and without lookahead: the same factor and log det."""
+    rng = np.random.default_rng(5)
+    n = 1700
+    G = rng.normal(size=(n, n + 50))
+    A = G @ G.T / n + np.eye(n)
+    outs = []
+    try:
+        for look in (1, 0):
+            api.tune_set("split_lookahead", look)
+            Ad = td(A)
+            ld = api.potrf(Ad, precision=SPLIT)
+            outs.append((np.tril(P.to_np(Ad)), float(P.to_np(ld))))
+    finally:
+        api.tune_set("split_lookahead", 1)
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
