@@ -32,6 +32,11 @@ METRIC = "Fisher+Cl solves/s (TQU Nside16 l2-47, 100 sims)"
 DGEMM_SYRK_TRAFFIC = 8.550515e9 + 0.187149e9
 DGEMM_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                              "--set full capture of this launch")
+# the same for the split kernel (ozaki_gemm_kernel<8, 2>, clusters of two) on
+# W = X^T X at this workload; None when the kernel changes until recaptured
+OZ_SYRK_TRAFFIC = 8.636111e9 + 0.178114e9
+OZ_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one --set full "
+                          "capture of the kernel alone (slicing not included)")
 UNIT = "solves/s"
 
 
@@ -804,7 +809,8 @@ def run_ours(args):
             "unit": "TFLOP/s", "frac": tensor_flops / dur_s / 1e12 / bf16_peak,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured",
             "fp64_equivalent_tflops": float(wl.k) * wl.k * wl.n / dur_s / 1e12,
-            "ms_per_launch": dur_s * 1e3}
+            "ms_per_launch": dur_s * 1e3,
+            "traffic": OZ_SYRK_TRAFFIC, "traffic_source": OZ_SYRK_TRAFFIC_SOURCE}
         del X, W
         torch.cuda.empty_cache()
 
