@@ -351,6 +351,13 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *                   layer through the WMMA product
  *   emu_tc0         1 (default) / 0: with emu_tc, the first layer (16
  *                   inputs, widened with zeros to 64) on tcgen05 too / WMMA
+ *   eig_onesided    0 (default) / 1: the eigendecomposition of F for the
+ *                   decorrelated and deconvolved normalisations by two-sided
+ *                   parallel Jacobi on F (a grid barrier a rotation round) /
+ *                   by one-sided Jacobi on its Cholesky factor (column pairs
+ *                   moving between neighbouring CTAs, one grid barrier a
+ *                   sweep; slower on this part); both within the parity
+ *                   tolerances
  *   split_lookahead 1 (default) / 0: the split-precision Cholesky runs the
  *                   next panel's float64 diagonal chain on a second,
  *                   high-priority stream beside the trailing update and the

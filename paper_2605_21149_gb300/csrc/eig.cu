@@ -3,6 +3,13 @@
 // F^-1/2 = U Xi^-1/2 U^T with eigenvalues below 1e-12 x max set to zero) and
 // the inverse used by the deconvolved normalisation (Eq. deconvolved).
 //
+// Two forms.  The default is the two-sided form that follows.  The other
+// (tuning key eig_onesided = 1) is a one-sided Jacobi on the Cholesky factor
+// of F (ojacobi_kernel below) with one grid barrier a sweep; on this part it
+// is the slower one (TQU Nside 16: qml_fisher 52.3 against 45.8 ms), since
+// each of its rounds pays for block reductions and a rotation in dependent
+// float64 operations, which cost more than the grid barrier it saves.
+//
 // Parallel cyclic Jacobi (round-robin pair ordering): in each of the n-1
 // rounds of a sweep the n indices form n/2 disjoint pairs; every pair gets the
 // Jacobi rotation that zeroes its off-diagonal entry, and because the pairs
@@ -203,9 +210,11 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
       to += ((volatile double *)red)[2 * b];
       td += ((volatile double *)red)[2 * b + 1];
     }
-    // converged, or stalled at the float64 rounding floor (quadratic
-    // convergence ends there; every block takes the same decision)
-    if (to <= 1e-32 * td) break;
+    // converged: off(A) <= eps ||A||_F with eps = 2^-52 (the cyclic-Jacobi
+    // tolerance of Golub & Van Loan, Sect. 8.5, in squares: 2^-104), which
+    // is where the float64 rounding floor of the off-diagonal sum lies; or
+    // stalled at that floor (every block takes the same decision)
+    if (to <= 0x1p-104 * (td + to)) break;
     if (sweep > 0 && to > 0.25 * prev_off && to <= 1e-20 * td) break;
     prev_off = to;
     fill_tables(0);
@@ -342,6 +351,191 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double *A0, doub
   }
 }
 
+// ---------------------------------------------------- one-sided Jacobi --
+// F = L L^T = G^T G with G = L^T (Cholesky of the padded F, computed first).
+// One-sided (Hestenes) Jacobi rotates pairs of columns of G until they are
+// orthogonal: G V = W, so V^T F V = W^T W is diagonal, F = V diag(|w_j|^2) V^T
+// (eigenvalues |w_j|^2, eigenvectors the columns of V).  The rotation of a
+// pair is the two-sided Jacobi rotation of its 2 x 2 Gram matrix
+// [[|g_p|^2, g_p.g_q], [g_p.g_q, |g_q|^2]] (the same `rotation` as above).
+//
+// Parallel form: CTA a holds the columns in slots a and n-1-a (G and V, in
+// shared memory), rotates them, then the columns move one slot along the
+// round-robin ring (slot 0 fixed, x -> x+1, n-1 -> 1), so after n-1 rounds
+// every pair has met once and every column is back in its own slot.  A
+// column moves to a neighbouring CTA through a mailbox in global memory
+// (two buffers by round parity) and a flag the sender raises with a release
+// store; the receiver waits for its own flags only.  Sending and receiving
+// are mutual between neighbours, so a sender cannot overwrite a buffer
+// before its reader has taken it.  One grid barrier a sweep decides
+// convergence: max over the sweep's pairs of (g_p.g_q)^2 / (|g_p|^2 |g_q|^2)
+// at most tol2.  Every wait is bounded (QML_ETIMEOUT).
+constexpr int kOjThreads = 256;
+constexpr int kOjFlagStride = 32;
+
+__device__ __forceinline__ int oj_owner(int y, int h) { return y < h ? y : 2 * h - 1 - y; }
+
+// wait until flag >= want (acquire); false on timeout or another failure
+__device__ bool oj_wait_flag(const unsigned *flag, unsigned want, DevStatus *st) {
+  for (long long spins = 0;; ++spins) {
+    if ((int)(ld_acquire(flag) - want) >= 0) return true;
+    if ((spins & 63) == 63) {
+      if (*((volatile int *)&st->code) != 0) return false;
+      if (spins > kSpinLimit) {
+        atomicCAS(&st->code, 0, 5 /* QML_ETIMEOUT */);
+        return false;
+      }
+    }
+  }
+}
+
+// Deterministic block sum of three per-thread partials (warp shuffles, then
+// the warps' partials in a fixed order by every thread).
+__device__ __forceinline__ void oj_sum3(double &x, double &y, double &z, double (*sh)[kOjThreads / 32]) {
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+    z += __shfl_down_sync(0xffffffffu, z, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][w] = x;
+    sh[1][w] = y;
+    sh[2][w] = z;
+  }
+  __syncthreads();
+  x = y = z = 0.0;
+  for (int q = 0; q < kOjThreads / 32; ++q) {
+    x += sh[0][q];
+    y += sh[1][q];
+    z += sh[2][q];
+  }
+  __syncthreads();
+}
+
+// L: the Cholesky factor (n x n lower, ld n; only i >= j read).  mbox: 8 h n
+// doubles (two parities of 2 h entries of 2 n); pflags: 2 h kOjFlagStride words (zero on entry); red / gflags: the
+// grid barrier's partials and flags (flags zero on entry).  Output: V (n x n),
+// and the eigenvalues on the diagonal of D (D[j + j n]).
+__global__ void __launch_bounds__(kOjThreads) ojacobi_kernel(const double *L, int n, int max_sweeps,
+                                                          double tol2, double *mbox,
+                                                          unsigned *pflags, double *red,
+                                                          unsigned *gflags, double *V, double *D,
+                                                          DevStatus *st) {
+  extern __shared__ double ojs[];
+  double *g0 = ojs, *g1 = ojs + n, *v0 = ojs + 2 * n, *v1 = ojs + 3 * n;
+  __shared__ double sred[3][kOjThreads / 32];
+  __shared__ double srot[2];
+  const int h = n / 2, a = blockIdx.x, tid = threadIdx.x;
+  const int slot[2] = {a, n - 1 - a};
+  const size_t col = 2 * (size_t)n;  // one mailbox entry: a G column, then a V column
+  // initial columns: g_x = row x of L, v_x = e_x
+  for (int pos = 0; pos < 2; ++pos) {
+    double *g = pos ? g1 : g0, *v = pos ? v1 : v0;
+    const int x = slot[pos];
+    for (int i = tid; i < n; i += kOjThreads) {
+      g[i] = i <= x ? L[x + (size_t)i * n] : 0.0;
+      v[i] = i == x ? 1.0 : 0.0;
+    }
+  }
+  __syncthreads();
+  unsigned R = 0, epoch = 0;  // rounds so far (all sweeps); grid-barrier epoch
+  double worst = 0.0, wprev = 0.0;
+  if (*((volatile int *)&st->code) != 0) return;  // e.g. F not positive definite
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < n - 1; ++r) {
+      double al = 0.0, be = 0.0, ga = 0.0;
+      for (int i = tid; i < n; i += kOjThreads) {
+        const double x = g0[i], y = g1[i];
+        al = fma(x, x, al);
+        be = fma(y, y, be);
+        ga = fma(x, y, ga);
+      }
+      oj_sum3(al, be, ga, sred);
+      if (tid == 0) {
+        rotation(al, be, ga, srot);
+        const double ab = al * be;
+        if (ab > 0.0) worst = fmax(worst, (ga * ga) / ab);
+      }
+      __syncthreads();
+      const double c = srot[0], s = srot[1];
+      // [g0 g1] <- [g0 g1] J, J = [[c, s], [-s, c]]; the same for V
+      for (int i = tid; i < n; i += kOjThreads) {
+        const double x = g0[i], y = g1[i];
+        g0[i] = c * x - s * y;
+        g1[i] = s * x + c * y;
+        const double p = v0[i], q = v1[i];
+        v0[i] = c * p - s * q;
+        v1[i] = s * p + c * q;
+      }
+      __syncthreads();
+      // send: the column in slot x goes to slot x + 1 (n - 1 -> 1; slot 0 stays)
+      const size_t par = (size_t)(R & 1u) * 2 * h * col;  // 2h entries a parity
+      for (int pos = 0; pos < 2; ++pos) {
+        const int x = slot[pos];
+        if (x == 0) continue;
+        const int y = (x == n - 1) ? 1 : x + 1;
+        const int b = oj_owner(y, h), q = y < h ? 0 : 1;
+        double *dst = mbox + par + ((size_t)b * 2 + q) * col;
+        const double *g = pos ? g1 : g0, *v = pos ? v1 : v0;
+        for (int i = tid; i < n; i += kOjThreads) {
+          dst[i] = g[i];
+          dst[n + i] = v[i];
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        for (int pos = 0; pos < 2; ++pos) {
+          const int x = slot[pos];
+          if (x == 0) continue;
+          const int y = (x == n - 1) ? 1 : x + 1;
+          st_release(pflags + ((size_t)oj_owner(y, h) * 2 + (y < h ? 0 : 1)) * kOjFlagStride, R + 1);
+        }
+      }
+      // receive into both positions (slot 0 keeps its column)
+      int ok = 1;
+      if (tid == 0)
+        for (int pos = 0; pos < 2; ++pos)
+          if (slot[pos] != 0 && !oj_wait_flag(pflags + ((size_t)a * 2 + pos) * kOjFlagStride, R + 1, st))
+            ok = 0;
+      if (!__syncthreads_and(ok)) return;
+      for (int pos = 0; pos < 2; ++pos) {
+        if (slot[pos] == 0) continue;
+        const double *src = mbox + par + ((size_t)a * 2 + pos) * col;
+        double *g = pos ? g1 : g0, *v = pos ? v1 : v0;
+        for (int i = tid; i < n; i += kOjThreads) {
+          g[i] = src[i];
+          v[i] = src[n + i];
+        }
+      }
+      __syncthreads();
+      ++R;
+    }
+    // every column is home again: one grid barrier decides convergence
+    if (tid == 0) red[a] = worst;
+    if (!grid_barrier(st, gflags, epoch, gridDim.x)) return;
+    double w = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) w = fmax(w, ((volatile double *)red)[b]);
+    // the partials are read before anyone writes the next sweep's
+    if (!grid_barrier(st, gflags, epoch, gridDim.x)) return;
+    worst = 0.0;
+    // converged, or stalled at the rounding floor of the dot products
+    if (w <= tol2 || (sweep > 0 && w > 0.25 * wprev && w <= 1e-20)) break;
+    wprev = w;
+  }
+  // eigenvalues |w_x|^2 on D's diagonal, eigenvectors into V
+  for (int pos = 0; pos < 2; ++pos) {
+    const double *g = pos ? g1 : g0, *v = pos ? v1 : v0;
+    const int x = slot[pos];
+    double nn = 0.0, d1 = 0.0, d2 = 0.0;
+    for (int i = tid; i < n; i += kOjThreads) nn = fma(g[i], g[i], nn);
+    oj_sum3(nn, d1, d2, sred);
+    if (tid == 0) D[x + (size_t)x * n] = nn;
+    for (int i = tid; i < n; i += kOjThreads) V[i + (size_t)x * n] = v[i];
+  }
+}
+
 __global__ void eig_setup_kernel(const double *F, int na, int n, double *A, double *V) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -405,9 +599,33 @@ __global__ void eig_scale_kernel(const double *V, int n, const double *fac, doub
 }  // namespace
 
 size_t fisher_eig_work_doubles(int na) {
-  size_t n = (size_t)(na + (na & 1));
-  return 5 * n * n + 2 * 4096 + 4 * n;
+  const size_t n = (size_t)(na + (na & 1)), h = n / 2, nb = (n + kNB - 1) / kNB;
+  // two-sided: A0, A1, V, S1, S2, the barrier area, rotations; one-sided adds
+  // the 64-block inverses and log parts of the Cholesky, pair flags, grid
+  // flags and the mailboxes
+  return 5 * n * n + 2 * 4096 + 4 * n + nb * kNB * kNB + nb + 8 + 32 * h + 16 * h + 8 * h * n;
 }
+
+namespace {
+// F = L L^T in place in A (n x n, ld n, lower) by 64-wide blocks: factor and
+// invert each diagonal block, solve the rows below with the inverse, update
+// the rest (the float64 kernels of the Cholesky path).  A non-positive pivot
+// sets QML_ENOTSPD.
+void small_potrf(double *A, int n, double *Linv, double *ldp, DevStatus *status, cudaStream_t st) {
+  for (int j = 0; j < n; j += kNB) {
+    const int jb = (n - j) < kNB ? (n - j) : kNB;
+    double *Lb = Linv + (size_t)(j / kNB) * kNB * kNB;
+    launch_potrf_diag(A + j + (size_t)j * n, n, n, j, Lb, ldp + j / kNB, status, st);
+    if (j + jb < n) {
+      const int m2 = n - j - jb;
+      double *A21 = A + (j + jb) + (size_t)j * n;
+      double *A22 = A + (j + jb) + (size_t)(j + jb) * n;
+      launch_dgemm(0, 1, m2, jb, jb, 1.0, A21, n, Lb, kNB, 0.0, A21, n, 0, status, st);
+      launch_dgemm(0, 1, m2, m2, jb, -1.0, A21, n, A21, n, 1.0, A22, n, 1, status, st);
+    }
+  }
+}
+}  // namespace
 
 cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, double *Fm12,
                            double *eig_minmax, DevStatus *status, cudaStream_t st) {
@@ -422,21 +640,58 @@ cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, 
   cudaGetDevice(&dev);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, kJacobiThreads, 0);
-  int nblocks = nsm * (occ > 0 ? 1 : 0);
-  if (nblocks > kMaxJacobiBlocks) nblocks = kMaxJacobiBlocks;
-  if (nblocks < 1) return cudaErrorLaunchFailure;
-  // barrier flags start at zero
-  cudaMemsetAsync(red + kFlagOffset, 0, (size_t)kMaxJacobiBlocks * kFlagStride * sizeof(unsigned), st);
   int max_sweeps = 30;
   int nn_arg = n;
-  void *args[] = {(void *)&A0, (void *)&A1, (void *)&V, (void *)&nn_arg, (void *)&max_sweeps,
-                  (void *)&red, (void *)&rot, (void *)&status};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void *)jacobi_kernel, dim3(nblocks),
-                                              dim3(kJacobiThreads), args, 0, st);
-  if (e != cudaSuccess) return e;
-  count_launch();
+  cudaError_t e = cudaSuccess;
+  // one-sided form (opt-in, tuning key eig_onesided) when the n / 2 column
+  // pairs fit on the GPU at once, which the pairwise waits require
+  const int h = n / 2;
+  const size_t oj_smem = 4 * (size_t)n * sizeof(double);
+  bool one = tune_get("eig_onesided", 0) != 0;
+  if (one) {
+    if (oj_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(ojacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)oj_smem) != cudaSuccess)
+      one = false;
+    int occ1 = 0;
+    if (one && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, ojacobi_kernel, kOjThreads,
+                                                              oj_smem) != cudaSuccess ||
+                (long long)occ1 * nsm < h))
+      one = false;
+  }
+  if (one) {
+    const size_t nb = (size_t)(n + kNB - 1) / kNB;
+    double *Linv = rot + 4 * (size_t)n;
+    double *ldp = Linv + nb * kNB * kNB;
+    unsigned *pflags = (unsigned *)(ldp + nb + 8);
+    unsigned *gflags = pflags + 64 * (size_t)h;
+    double *mbox = (double *)(gflags + 32 * (size_t)h);
+    small_potrf(A0, n, Linv, ldp, status, st);
+    cudaMemsetAsync(pflags, 0, 96 * (size_t)h * sizeof(unsigned), st);  // pair and grid flags
+    double tol2 = (double)n * 0x1p-104;  // |cos| <= sqrt(n) eps between every pair
+    void *args[] = {(void *)&A0, (void *)&nn_arg, (void *)&max_sweeps, (void *)&tol2,
+                    (void *)&mbox, (void *)&pflags, (void *)&red, (void *)&gflags, (void *)&V,
+                    (void *)&A0, (void *)&status};
+    e = cudaLaunchCooperativeKernel((const void *)ojacobi_kernel, dim3(h), dim3(kOjThreads), args,
+                                    oj_smem, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+  } else {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, kJacobiThreads, 0);
+    int nblocks = nsm * (occ > 0 ? 1 : 0);
+    if (nblocks > kMaxJacobiBlocks) nblocks = kMaxJacobiBlocks;
+    if (nblocks < 1) return cudaErrorLaunchFailure;
+    // barrier flags start at zero
+    cudaMemsetAsync(red + kFlagOffset, 0, (size_t)kMaxJacobiBlocks * kFlagStride * sizeof(unsigned),
+                    st);
+    void *args[] = {(void *)&A0, (void *)&A1, (void *)&V, (void *)&nn_arg, (void *)&max_sweeps,
+                    (void *)&red, (void *)&rot, (void *)&status};
+    e = cudaLaunchCooperativeKernel((const void *)jacobi_kernel, dim3(nblocks),
+                                    dim3(kJacobiThreads), args, 0, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+  }
   // red is free again: per-column factors
   eig_factor_kernel<<<1, 256, 0, st>>>(A0, na, n, 1e-12, red, eig_minmax, status);
   count_launch();

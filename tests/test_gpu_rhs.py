@@ -104,17 +104,28 @@ def test_decorrelated_vs_extended_small(api, cfg, scale):
     assert e_gpu <= max(P.TOL, 20 * P.EPS * kappa), (e_gpu, kappa)
 
 
-def test_decorrelated_vs_extended_tqu16(api, tqu16):
+@pytest.mark.parametrize("onesided", [0, 1])
+def test_decorrelated_vs_extended_tqu16(api, tqu16, onesided):
     """TQU Nside 16 (kappa(F) ~ 7e8): the GPU's float64 F^-1/2 q against the
     extended-precision value; the measured error stays within the bound
-    20 eps kappa(F) that the float64 parity tests use, and within a few times
-    the oracle's own float64 error."""
+    20 eps kappa(F) that the float64 parity tests use.  Both eigensolvers:
+    the two-sided Jacobi on F (default) and the one-sided Jacobi on its
+    Cholesky factor (tuning key eig_onesided = 1); with each, the deconvolved
+    estimate stays within the parity tolerance too."""
     wl, maps, ref = tqu16
     sub = {"F": ref["F"], "q": ref["q"][:, :100], "cl_decorr": ref["cl_decorr"][:, :100]}
-    e_gpu, e_ora, kappa = _decorr_errors(api, wl, maps[:, :100], sub)
-    print(f"decorrelated vs long double: {wl.name}: kappa {kappa:.3g}, GPU {e_gpu:.3g}, "
-          f"oracle float64 {e_ora:.3g}, bound {20 * P.EPS * kappa:.3g}")
+    api.tune_set("eig_onesided", onesided)
+    try:
+        e_gpu, e_ora, kappa = _decorr_errors(api, wl, maps[:, :100], sub)
+        F, plan = api.fisher(api.Problem.from_workload(wl))
+        est = plan.estimate(td(maps[:, :100]))
+        plan.free()
+    finally:
+        api.tune_set("eig_onesided", 0)
+    print(f"decorrelated vs long double: {wl.name}: onesided {onesided}, kappa {kappa:.3g}, "
+          f"GPU {e_gpu:.3g}, oracle float64 {e_ora:.3g}, bound {20 * P.EPS * kappa:.3g}")
     assert e_gpu <= 20 * P.EPS * kappa, (e_gpu, kappa)
+    assert P.cl_deconv_error(est["cl_deconv"], ref["cl_deconv"][:, :100], ref["F"]) <= P.TOL
 
 
 def test_free_plans():
