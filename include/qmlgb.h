@@ -396,13 +396,14 @@ qml_status qml_tune_load(const char *text);
  * qml_potrf with precision QML_FP64, except that it never runs the float64
  * GEMM tile autotuner (which allocates): each product uses the tuning table's
  * tile for its shape when present, else the heuristic tile, which changes the
- * time only.  A (n x n, lda) and logdet (may be NULL) must be DEVICE pointers.  Its scratch is a static device array sized for
- * n <= 4096 (2.1 MB held on every GPU that loads the library until exit);
- * larger n returns QML_EINVAL.  All calls share that array, so calls that
- * overlap on the GPU race and must be serialised by the caller.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and should come before any stream capture.  Like the other calls it reads
- * its status back and synchronises `stream` before returning. */
+ * time only.  A (n x n, lda) and logdet (may be NULL) must be DEVICE
+ * pointers.  Its scratch is a static device array sized for n <= 4096
+ * (2.1 MB held on every GPU that loads the library until exit); larger n
+ * returns QML_EINVAL.  All calls share that array, so calls that overlap on
+ * the GPU race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress).  Like
+ * the other calls it reads its status back and synchronises `stream` before
+ * returning. */
 qml_status qml_potrf_noalloc(int64_t n, double *A, int64_t lda, double *logdet, void *stream);
 
 #ifdef __cplusplus

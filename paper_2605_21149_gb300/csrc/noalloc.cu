@@ -23,9 +23,8 @@
 // Host code may not use the array's name as a device address (in host code
 // it names a host-side shadow); the device address comes from
 // cudaGetSymbolAddress, taken once per device with that device current, on
-// the first call on that device.  That first call should therefore come
-// before any stream capture the caller performs.  Every call reads the status
-// word back and synchronises `stream` before it returns.
+// the first call on that device.  Every call reads the status word back and
+// synchronises `stream` before it returns.
 #include "qmlgb.h"
 #include "internal.cuh"
 
