@@ -124,6 +124,7 @@ struct OzParams {
   // float64 compare is a float64-pipe instruction (tens of clocks a warp on
   // this part), so the output takes this integer instead of testing beta.
   int beta_mode;
+  int prefetch_c;  // fetch each output tile's C into L2 when the tile starts
   double *C;
   int64_t ldc;
   const int *ea, *eb;
@@ -516,6 +517,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t gjl = n0 + kEpiCols * half + lane;
       const int f_lo = gjl < p.N ? p.eb[gjl] : 0;
       const int f_hi = gjl + 32 < p.N ? p.eb[gjl + 32] : 0;
+      // beta C is read only when the tile is written out, after all of its
+      // MMAs; fetch this thread's C entries into L2 now, so that those reads
+      // wait on L2 rather than on DRAM
+      if (p.prefetch_c && m0 + row < p.M) {
+        const int64_t pi = m0 + row;
+        for (int j = 0; j < kEpiCols; ++j) {
+          const int64_t pj = n0 + kEpiCols * half + j;
+          if (pj >= p.N || (p.lower && pi < pj)) break;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p.C + pi + pj * p.ldc)));
+        }
+      }
       long long acc[kEpiCols];
 #pragma unroll
       for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
@@ -1033,6 +1045,7 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.alpha = alpha;
   p.betac = beta_c;
   p.beta_mode = beta_c == 0.0 ? 0 : (beta_c == 1.0 ? 1 : 2);
+  p.prefetch_c = (p.beta_mode != 0 && tune_get("ozaki_prefetch_c", 1) != 0) ? 1 : 0;
   {
     int ax = 0;
     const double fr = frexp(alpha, &ax);  // alpha = fr 2^ax, |fr| in [0.5, 1)
