@@ -283,10 +283,14 @@ int64_t emu_param_count(const qml_emu *emu);
 qml_status emu_params(qml_emu *emu, int32_t head, float *out);
 /* The float64 baseline polynomial and residual scale of a trained emulator
  * (host outputs): lnL = q(x) + sigma (f_0(x) + f_1(x)) / 2 with q(x) =
- * sum_k coef[k] phi_k(x), the features phi in the order 1, x_i, x_i x_j
- * (i <= j), x_i x_j x_l (i <= j <= l, cubic part only for d <= 5); coef holds
- * at least 56 doubles, *nfeat receives the count used.  Exposes the model so
- * that its inference can be checked term by term. */
+ * sum_k coef[k] phi_k(x), phi_k(x) = prod_i P_{m_ki}(x_i) (Legendre
+ * polynomials of the normalised coordinates) over the multi-indices m of
+ * total degree <= D: by total degree t = 0..D, within a degree m_k0 from t
+ * down to 0, then m_k1 from what is left down to 0, and so on, the last
+ * component taking the rest.  D is the highest degree with at most 256 terms
+ * and at least 16 training labels (after the held-out eighth) per term; *nfeat
+ * receives the term count C(D + d, d), coef must hold 256 doubles.  Exposes
+ * the model so that its inference can be checked term by term. */
 qml_status emu_baseline(const qml_emu *emu, double *coef, int32_t *nfeat, double *sigma);
 /* Mean squared error of head `head` on n given normalised inputs (host, n x 16
  * row-major) and targets (host, n), and its gradient (float32, host or

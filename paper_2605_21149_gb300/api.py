@@ -420,7 +420,7 @@ class Emulator:
     def baseline(self):
         """(coef, sigma): the float64 baseline polynomial's coefficients (feature
         order of emu_baseline) and the residual scale of the network term."""
-        coef = np.zeros(64, dtype=np.float64)
+        coef = np.zeros(256, dtype=np.float64)
         nf = ctypes.c_int32(0)
         sig = ctypes.c_double(0.0)
         _check(_lib().emu_baseline(self._h, coef.ctypes.data, ctypes.byref(nf), ctypes.byref(sig)))

@@ -4,8 +4,10 @@
 //
 // Model: x = (theta - centre) / half_width in [-1, 1]^d (zero-padded to 16
 // inputs); lnL(theta) = q(x) + sigma_r f(x), where q is a float64 least-squares
-// polynomial in x (cubic for d <= 5, else quadratic) fitted to the training
-// labels and f is an MLP with `depth`
+// polynomial in x fitted to the training labels -- products of Legendre
+// polynomials of total degree up to the highest that keeps 16 labels per
+// coefficient and at most 256 terms (degree 6 for d = 4 from 3360 labels) --
+// and f is an MLP with `depth`
 // hidden GELU layers of `width` units (gelu(z) = z Phi(z)) and a linear output,
 // trained on the normalised residuals (lnL - q) / sigma_r.  The residual is
 // small next to lnL itself, so bf16 weights with FP32 accumulation are enough.
@@ -32,6 +34,7 @@
 #include <cmath>
 #include <type_traits>
 #include <string>
+#include <functional>
 #include <vector>
 
 namespace qmlgb {
@@ -44,12 +47,45 @@ using namespace nvcuda;
 namespace {
 
 constexpr int kIn0 = 16, kOut0 = 16, kMaxDim = 8;
-// baseline polynomial: cubic up to kCubicDim parameters, quadratic above
-constexpr int kCubicDim = 5;
-__host__ __device__ constexpr int nfeat(int d) {
-  return 1 + d + d * (d + 1) / 2 + (d <= kCubicDim ? d * (d + 1) * (d + 2) / 6 : 0);
+// baseline polynomial: products of Legendre polynomials P_k(x_i) of total
+// degree <= deg (well conditioned on the box), at most kMaxFeat terms
+constexpr int kMaxFeat = 256, kMaxDeg = 12;
+// number of multi-indices of d components with sum <= deg: C(deg + d, d)
+inline int nfeat_of(int d, int deg) {
+  long long c = 1;
+  for (int i = 1; i <= d; ++i) c = c * (deg + i) / i;
+  return (int)c;
 }
-constexpr int kMaxFeat = nfeat(kCubicDim) > nfeat(kMaxDim) ? nfeat(kCubicDim) : nfeat(kMaxDim);
+// the feature order: by total degree t = 0..deg; within a degree the first
+// exponent from t down to 0, then the second from what is left down to 0,
+// and so on, the last taking the rest
+void multi_indices(int d, int deg, std::vector<unsigned char> &out) {
+  out.clear();
+  std::vector<int> m(d);
+  for (int t = 0; t <= deg; ++t) {
+    // recursive enumeration written as an explicit stack over positions
+    std::function<void(int, int)> rec = [&](int pos, int left) {
+      if (pos == d - 1) {
+        m[pos] = left;
+        for (int i = 0; i < d; ++i) out.push_back((unsigned char)m[i]);
+        return;
+      }
+      for (int k = left; k >= 0; --k) {
+        m[pos] = k;
+        rec(pos + 1, left - k);
+      }
+    };
+    rec(0, t);
+  }
+}
+// degree of the baseline for n training labels: the highest total degree
+// with at least 16 labels per coefficient and at most kMaxFeat terms
+int baseline_degree(int d, int n) {
+  int deg = 1;
+  while (deg < kMaxDeg && nfeat_of(d, deg + 1) <= kMaxFeat && 16LL * nfeat_of(d, deg + 1) <= n)
+    ++deg;
+  return deg;
+}
 // points in the outer 3 % shell of the box are treated as outside the
 // training hull: uniformly drawn samples thin out there and the two heads can
 // agree while both extrapolate
@@ -278,99 +314,129 @@ __global__ void pad_cols_kernel(const __nv_bfloat16 *src, int rows, int cols, __
   }
 }
 
-// polynomial features of normalised x: 1, x_i, x_i x_j (i <= j) and, for
-// d <= kCubicDim, x_i x_j x_l (i <= j <= l)
-__device__ int features(const double *x, int d, double *f) {
-  int k = 0;
-  f[k++] = 1.0;
-  for (int i = 0; i < d; ++i) f[k++] = x[i];
-  for (int i = 0; i < d; ++i)
-    for (int j = i; j < d; ++j) f[k++] = x[i] * x[j];
-  if (d <= kCubicDim)
-    for (int i = 0; i < d; ++i)
-      for (int j = i; j < d; ++j)
-        for (int l = j; l < d; ++l) f[k++] = x[i] * x[j] * x[l];
-  return k;
-}
-
-// per-block partial normal equations A^T A, A^T y (float64)
-__global__ void normal_eq_kernel(const double *theta, const double *y, int n, int d,
-                                 const double *centre, const double *half, double *partial) {
-  const int nf = nfeat(d);
-  __shared__ double acc[kMaxFeat * (kMaxFeat + 1)];
-  for (int t = threadIdx.x; t < nf * (nf + 1); t += blockDim.x) acc[t] = 0.0;
-  __syncthreads();
-  // one thread per sample; per-thread contributions added in a fixed order by
-  // thread 0 would serialise, so each thread owns a slice of the matrix
-  // entries instead and loops over this block's samples
-  const int s0 = blockIdx.x * 256, s1 = min(n, s0 + 256);
-  for (int e = threadIdx.x; e < nf * (nf + 1); e += blockDim.x) {
-    const int r = e / (nf + 1), c = e % (nf + 1);
-    double sacc = 0.0;
-    for (int s = s0; s < s1; ++s) {
-      double x[kMaxDim], f[kMaxFeat];
-      for (int i = 0; i < d; ++i) x[i] = (theta[s + (int64_t)i * n] - centre[i]) / half[i];
-      features(x, d, f);
-      sacc += f[r] * (c < nf ? f[c] : y[s]);
-    }
-    acc[e] = sacc;
+// Legendre values P_0..P_deg of each of the d coordinates (Bonnet's
+// recurrence (k + 1) P_{k+1} = (2k + 1) x P_k - k P_{k-1})
+__device__ __forceinline__ void legendre_table(const double *x, int d, int deg,
+                                               double (*leg)[kMaxDeg + 1]) {
+  for (int i = 0; i < d; ++i) {
+    leg[i][0] = 1.0;
+    if (deg >= 1) leg[i][1] = x[i];
+    for (int k = 1; k < deg; ++k)
+      leg[i][k + 1] = ((2 * k + 1) * x[i] * leg[i][k] - k * leg[i][k - 1]) / (k + 1);
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nf * (nf + 1); e += blockDim.x)
-    partial[(int64_t)blockIdx.x * nf * (nf + 1) + e] = acc[e];
 }
-
-// sum the partials, solve (A^T A + ridge) c = A^T y by Cholesky (one thread)
-__global__ void solve_quad_kernel(const double *partial, int nblocks, int d, double *coef) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int nf = nfeat(d);
-  double A[kMaxFeat][kMaxFeat + 1];
-  for (int r = 0; r < nf; ++r)
-    for (int c = 0; c <= nf; ++c) {
-      double s = 0.0;
-      for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * nf * (nf + 1) + r * (nf + 1) + c];
-      A[r][c] = s;
-    }
-  double tr = 0.0;
-  for (int r = 0; r < nf; ++r) tr += A[r][r];
-  for (int r = 0; r < nf; ++r) A[r][r] += 1e-12 * tr / nf;
+// q(x) = sum_j coef_j prod_i P_{m_ji}(x_i) with the multi-indices m (nf x d)
+__device__ __forceinline__ double baseline_value(const double *x, int d, int deg, int nf,
+                                                 const unsigned char *midx, const double *coef) {
+  double leg[kMaxDim][kMaxDeg + 1];
+  legendre_table(x, d, deg, leg);
+  double q = 0.0;
   for (int j = 0; j < nf; ++j) {
-    double s = A[j][j];
-    for (int k = 0; k < j; ++k) s -= A[j][k] * A[j][k];
-    const double dj = sqrt(s > 0.0 ? s : 1e-300);
-    A[j][j] = dj;
-    for (int i = j + 1; i < nf; ++i) {
-      double t = A[i][j];
-      for (int k = 0; k < j; ++k) t -= A[i][k] * A[j][k];
-      A[i][j] = t / dj;
+    double f = 1.0;
+    for (int i = 0; i < d; ++i) f *= leg[i][midx[j * d + i]];
+    q = fma(coef[j], f, q);
+  }
+  return q;
+}
+
+// The same value for inference, where it runs once per predicted point: the
+// constant term in float64 and the other terms in float32 (the float64 pipe
+// of this part is narrow).  Each term is a product of Legendre values of
+// magnitude <= 1, so the float32 sum is off by at most about 2^-23 sum |coef_j|,
+// j >= 1, far below the emulator's tolerance.
+__device__ __forceinline__ double baseline_value_fast(const double *x, int d, int deg, int nf,
+                                                      const unsigned char *midx,
+                                                      const double *coef) {
+  float leg[kMaxDim][kMaxDeg + 1];
+  for (int i = 0; i < d; ++i) {
+    const float xi = (float)x[i];
+    leg[i][0] = 1.0f;
+    if (deg >= 1) leg[i][1] = xi;
+    for (int k = 1; k < deg; ++k)
+      leg[i][k + 1] = ((2 * k + 1) * xi * leg[i][k] - k * leg[i][k - 1]) / (float)(k + 1);
+  }
+  float q = 0.0f;
+  for (int j = 1; j < nf; ++j) {
+    float f = 1.0f;
+    for (int i = 0; i < d; ++i) f *= leg[i][midx[j * d + i]];
+    q = fmaf((float)coef[j], f, q);
+  }
+  return coef[0] + (double)q;
+}
+
+// Phi (n x nf, column-major): the features of every training point
+__global__ void phi_kernel(const double *theta, int n, int d, int deg, int nf,
+                           const unsigned char *midx, const double *centre, const double *half,
+                           double *Phi) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    double x[kMaxDim], leg[kMaxDim][kMaxDeg + 1];
+    for (int i = 0; i < d; ++i) x[i] = (theta[s + (int64_t)i * n] - centre[i]) / half[i];
+    legendre_table(x, d, deg, leg);
+    for (int j = 0; j < nf; ++j) {
+      double f = 1.0;
+      for (int i = 0; i < d; ++i) f *= leg[i][midx[j * d + i]];
+      Phi[s + (int64_t)j * n] = f;
     }
   }
-  double z[kMaxFeat];
-  for (int i = 0; i < nf; ++i) {
-    double t = A[i][nf];
-    for (int k = 0; k < i; ++k) t -= A[i][k] * z[k];
-    z[i] = t / A[i][i];
+}
+
+// (G + ridge) coef = r by Cholesky, G (nf x nf, column-major, overwritten by
+// its factor) and r in global memory; one block, fixed operation order.  The
+// ridge, 1e-12 of the mean diagonal, keeps a rank-deficient G solvable.
+__global__ void chol_solve_kernel(double *G, const double *r, int nf, double *coef) {
+  __shared__ double sd;
+  __shared__ double z[kMaxFeat];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < nf; ++i) tr += G[i + (int64_t)i * nf];
+    sd = 1e-12 * tr / nf;
   }
-  for (int i = nf - 1; i >= 0; --i) {
-    double t = z[i];
-    for (int k = i + 1; k < nf; ++k) t -= A[k][i] * coef[k];
-    coef[i] = t / A[i][i];
+  __syncthreads();
+  for (int i = tid; i < nf; i += blockDim.x) G[i + (int64_t)i * nf] += sd;
+  __syncthreads();
+  for (int j = 0; j < nf; ++j) {
+    if (tid == 0) {
+      const double v = G[j + (int64_t)j * nf];
+      sd = sqrt(v > 0.0 ? v : 1e-300);
+      G[j + (int64_t)j * nf] = sd;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nf; i += blockDim.x) G[i + (int64_t)j * nf] /= sd;
+    __syncthreads();
+    // trailing update of the lower triangle, column by column
+    const int m = nf - j - 1;
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      const int ii = j + 1 + t % m, kk = j + 1 + t / m;
+      if (ii >= kk) G[ii + (int64_t)kk * nf] -= G[ii + (int64_t)j * nf] * G[kk + (int64_t)j * nf];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < nf; ++i) {  // L z = r
+      double t = r[i];
+      for (int k = 0; k < i; ++k) t -= G[i + (int64_t)k * nf] * z[k];
+      z[i] = t / G[i + (int64_t)i * nf];
+    }
+    for (int i = nf - 1; i >= 0; --i) {  // L^T coef = z
+      double t = z[i];
+      for (int k = i + 1; k < nf; ++k) t -= G[k + (int64_t)i * nf] * coef[k];
+      coef[i] = t / G[i + (int64_t)i * nf];
+    }
   }
 }
 
 // residual r = y - q(x) and its sum of squares partials
-__global__ void residual_kernel(const double *theta, const double *y, int n, int d,
-                                const double *centre, const double *half, const double *coef,
-                                double *res, double *partial) {
+__global__ void residual_kernel(const double *theta, const double *y, int n, int d, int deg,
+                                int nf, const unsigned char *midx, const double *centre,
+                                const double *half, const double *coef, double *res,
+                                double *partial) {
   __shared__ double red[256];
   double ss = 0.0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    double x[kMaxDim], f[kMaxFeat];
+    double x[kMaxDim];
     for (int i = 0; i < d; ++i) x[i] = (theta[s + (int64_t)i * n] - centre[i]) / half[i];
-    const int nf = features(x, d, f);
-    double q = 0.0;
-    for (int k = 0; k < nf; ++k) q += coef[k] * f[k];
-    const double r = y[s] - q;
+    const double r = y[s] - baseline_value(x, d, deg, nf, midx, coef);
     res[s] = r;
     ss += r * r;
   }
@@ -394,21 +460,20 @@ __global__ void scale_targets_kernel(const double *res, int n, const double *sum
 // prediction: q(x) + sigma (f0 + f1) / 2; flag outside the hull (box minus
 // its outer shell) or when the heads differ by more than thr (in lnL units)
 __global__ void predict_finish_kernel(const double *theta, int ntot, int off, int cnt, int d,
+                                      int deg, int nf, const unsigned char *midx,
                                       const double *centre, const double *half,
                                       const double *coef, const double *sigma, const float *o0,
                                       const float *o1, double thr, double *out, int *flags,
                                       double *dis) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += gridDim.x * blockDim.x) {
     const int s = off + j;
-    double x[kMaxDim], f[kMaxFeat];
+    double x[kMaxDim];
     bool outside = false;
     for (int i = 0; i < d; ++i) {
       x[i] = (theta[s + (int64_t)i * ntot] - centre[i]) / half[i];
       outside |= (fabs(x[i]) > kHullMargin);
     }
-    const int nf = features(x, d, f);
-    double q = 0.0;
-    for (int k = 0; k < nf; ++k) q += coef[k] * f[k];
+    const double q = baseline_value_fast(x, d, deg, nf, midx, coef);
     const double a = o0[(int64_t)j * kOut0], b = o1[(int64_t)j * kOut0];
     out[s] = q + *sigma * 0.5 * (a + b);
     const double dab = *sigma * fabs(a - b);
@@ -572,6 +637,9 @@ struct qml_emu {
   int64_t nparam = 0;
   // device
   double *centre = nullptr, *half = nullptr, *coef = nullptr, *sigma = nullptr;
+  // baseline: total degree, feature count and multi-indices (nf x d, device)
+  int deg = 0, nf = 1;
+  unsigned char *midx = nullptr;
   float *p[2] = {nullptr, nullptr}, *m[2] = {nullptr, nullptr}, *v[2] = {nullptr, nullptr};
   __nv_bfloat16 *ph[2] = {nullptr, nullptr};
   float *grad = nullptr;
@@ -870,8 +938,9 @@ qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *
       forward(e, 1, A1, st);
     }
     const int nl = (int)e->layers.size();
-    predict_finish_kernel<<<grid_of(cnt), 256, 0, st>>>(th, n, off, cnt, e->d, e->centre, e->half,
-                                                        e->coef, e->sigma, A0.Z[nl - 1],
+    predict_finish_kernel<<<grid_of(cnt), 256, 0, st>>>(th, n, off, cnt, e->d, e->deg, e->nf,
+                                                        e->midx, e->centre, e->half, e->coef,
+                                                        e->sigma, A0.Z[nl - 1],
                                                         A1.Z[nl - 1], thr, od, fd, dis);
     count_launch();
   }
@@ -957,6 +1026,7 @@ qml_status emu_create(int32_t ndim, const double *lo, const double *hi, int32_t 
   e->centre = emu_alloc<double>(e, ndim);
   e->half = emu_alloc<double>(e, ndim);
   e->coef = emu_alloc<double>(e, kMaxFeat);
+  e->midx = emu_alloc<unsigned char>(e, kMaxFeat * kMaxDim);
   e->sigma = emu_alloc<double>(e, 1);
   e->grad = emu_alloc<float>(e, e->nparam);
   for (int h = 0; h < 2; ++h) {
@@ -965,13 +1035,15 @@ qml_status emu_create(int32_t ndim, const double *lo, const double *hi, int32_t 
     e->v[h] = emu_alloc<float>(e, e->nparam);
     e->ph[h] = emu_alloc<__nv_bfloat16>(e, e->nparam);
   }
-  if (!e->centre || !e->half || !e->coef || !e->sigma || !e->grad || !e->p[1] || !e->ph[1]) {
+  if (!e->centre || !e->half || !e->coef || !e->midx || !e->sigma || !e->grad || !e->p[1] ||
+      !e->ph[1]) {
     emu_free(e);
     return efail(QML_ENOMEM, "emu_create: device allocation failed");
   }
   cudaMemcpy(e->centre, c.data(), ndim * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(e->half, hw.data(), ndim * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemset(e->coef, 0, kMaxFeat * sizeof(double));
+  cudaMemset(e->midx, 0, kMaxFeat * kMaxDim);  // untrained: one constant feature, q = 0
   const double one = 1.0;
   cudaMemcpy(e->sigma, &one, sizeof(double), cudaMemcpyHostToDevice);
   for (int h = 0; h < 2; ++h) {
@@ -1039,32 +1111,49 @@ qml_status emu_train(qml_emu *e, int32_t n, const double *theta, const double *l
   }
   const double *th = dev_in(th_h.data(), (size_t)n_all * e->d, keep);
   const double *y = dev_in(y_h.data(), n_all, keep);
-  double *res = nullptr, *part = nullptr, *sumsq = nullptr;
+  double *res = nullptr, *part = nullptr, *sumsq = nullptr, *phi = nullptr, *gram = nullptr;
   float *targ = nullptr;
-  const int nblk = (n + 255) / 256;
-  const int nf = nfeat(e->d);
+  // the baseline's degree and feature order for this many training labels
+  e->deg = baseline_degree(e->d, n);
+  e->nf = nfeat_of(e->d, e->deg);
+  const int nf = e->nf;
+  {
+    std::vector<unsigned char> mi;
+    multi_indices(e->d, e->deg, mi);
+    cudaMemcpy(e->midx, mi.data(), mi.size(), cudaMemcpyHostToDevice);
+  }
   cudaMalloc(&res, n * sizeof(double));
-  cudaMalloc(&part, (size_t)std::max(nblk, 256) * nf * (nf + 1) * sizeof(double));
+  cudaMalloc(&part, 256 * sizeof(double));
   cudaMalloc(&sumsq, sizeof(double));
   cudaMalloc(&targ, n * sizeof(float));
+  cudaMalloc(&phi, (size_t)n * nf * sizeof(double));
+  cudaMalloc(&gram, (size_t)nf * (nf + 1) * sizeof(double));
   keep.push_back(res);
   keep.push_back(part);
   keep.push_back(sumsq);
   keep.push_back(targ);
+  keep.push_back(phi);
+  keep.push_back(gram);
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
     for (void *p : keep) cudaFree(p);
   };
-  if (!th || !y || !res || !part || !sumsq || !targ) {
+  if (!th || !y || !res || !part || !sumsq || !targ || !phi || !gram) {
     cleanup();
     return efail(QML_ENOMEM, "emu_train: allocation failed");
   }
-  // polynomial baseline and normalised residual targets (float64)
-  normal_eq_kernel<<<nblk, 256, 0, st>>>(th, y, n, e->d, e->centre, e->half, part);
+  // polynomial baseline (float64 least squares: Phi^T Phi c = Phi^T y by
+  // Cholesky) and normalised residual targets
+  phi_kernel<<<grid_of(n), 256, 0, st>>>(th, n, e->d, e->deg, nf, e->midx, e->centre, e->half,
+                                         phi);
   count_launch();
-  solve_quad_kernel<<<1, 32, 0, st>>>(part, nblk, e->d, e->coef);
+  launch_dgemm_fixed(1, 0, nf, nf, n, 1.0, phi, n, phi, n, 0.0, gram, nf, 0, nullptr, st);
+  launch_dgemm_fixed(1, 0, nf, 1, n, 1.0, phi, n, y, n, 0.0, gram + (size_t)nf * nf, nf, 0,
+                     nullptr, st);
+  chol_solve_kernel<<<1, 256, 0, st>>>(gram, gram + (size_t)nf * nf, nf, e->coef);
   count_launch();
-  residual_kernel<<<64, 256, 0, st>>>(th, y, n, e->d, e->centre, e->half, e->coef, res, part);
+  residual_kernel<<<64, 256, 0, st>>>(th, y, n, e->d, e->deg, nf, e->midx, e->centre, e->half,
+                                      e->coef, res, part);
   count_launch();
   sum_partials_kernel<<<1, 32, 0, st>>>(part, 64, 1.0, sumsq);
   count_launch();
@@ -1223,7 +1312,7 @@ qml_status emu_params(qml_emu *e, int32_t head, float *out) {
 
 qml_status emu_baseline(const qml_emu *e, double *coef, int32_t *nfeat_out, double *sigma) {
   if (!e || !coef || !nfeat_out || !sigma) return efail(QML_EINVAL, "emu_baseline: bad arguments");
-  const int nf = nfeat(e->d);
+  const int nf = e->nf;
   cudaDeviceSynchronize();
   if (cudaMemcpy(coef, e->coef, nf * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(sigma, e->sigma, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
