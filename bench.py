@@ -34,9 +34,9 @@ DGEMM_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum o
                              "--set full capture of this launch")
 # the same for the split kernel (ozaki_gemm_kernel<8, 2>, clusters of two) on
 # W = X^T X at this workload; None when the kernel changes until recaptured
-OZ_SYRK_TRAFFIC = 8.636111e9 + 0.178114e9
-OZ_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one --set full "
-                          "capture of the kernel alone (slicing not included)")
+OZ_SYRK_TRAFFIC = 5.69e9 + 0.17715e9
+OZ_SYRK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
+                          "the kernel alone (slicing not included), banded work order")
 UNIT = "solves/s"
 
 

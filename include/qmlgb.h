@@ -355,6 +355,9 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *                   layer through the WMMA product
  *   emu_tc0         1 (default) / 0: with emu_tc, the first layer (16
  *                   inputs, widened with zeros to 64) on tcgen05 too / WMMA
+ *   ozaki_band      6 (default): row pairs per band of the split kernel's
+ *                   work order (column by column inside a band; 1 = row pair
+ *                   after row pair); the results are the same for any value
  *   ozaki_prefetch_c 1 (default) / 0: with beta != 0 the split kernel
  *                   fetches each output tile's C into L2 when the tile
  *                   starts / reads it from memory when the tile is written

@@ -116,7 +116,8 @@ struct OzParams {
   int stage_tiles;         // digit tiles per operand a ring stage holds
   int nstages;             // ring depth
   int shift_top;           // left shift of level-2 chunk sums in the int64 accumulator
-  int tiles_n, lower;
+  int tiles_m, tiles_n, lower;
+  int band;                // row pairs per band of the pair order (>= 1)
   int ntiles;              // work items (tiles, or tile pairs); the grid takes them round-robin
   double alpha, betac;
   int alpha_pow2, alpha_exp, alpha_neg;  // alpha = (-1)^neg 2^exp when alpha_pow2
@@ -159,23 +160,52 @@ __device__ __forceinline__ void tile_of(const OzParams &p, int bid, int &tm, int
   tm = r;
   tn = bid - r * (r + 1) / 2;
 }
-// Pairs of tiles for the two CTAs of a cluster: pair idx is tile rows 2 TM
-// and 2 TM + 1 of tile column tn (one B tile shared by both).  Lower C: the
-// pairs with tn <= 2 TM + 1, row pair by row pair (2 TM + 2 of them, fewer
-// in a last row pair of one tile row); a tile above the diagonal or past the
-// last tile row is computed on zeros or discarded, and stores nothing.
+// Pairs of tiles for the two CTAs of a cluster: pair (TM, tn) is tile rows
+// 2 TM and 2 TM + 1 of tile column tn (one B tile shared by both).  Lower C:
+// only the pairs with tn <= 2 TM + 1 (and tn < tiles_m); a tile above the
+// diagonal or past the last tile row is computed on zeros or discarded, and
+// stores nothing.  Order: bands of p.band row pairs (tuning key ozaki_band,
+// default 6; 1 gives row-pair by row-pair order), inside a band column by
+// column and the band's row pairs within each column.  The persistent grid
+// takes the items in waves of one pair per cluster, which all stream K in
+// step, and a wave over a compact band of rows and columns reads fewer
+// distinct digit panels from DRAM than one along whole rows (about 25 panels
+// a wave instead of about 45 at k = 6900).
+// items of column tn in the band of row pairs [t0, t1) (lower C)
+__device__ __forceinline__ int band_col_count(int tn, int t0, int t1) {
+  const int need = tn >= 1 ? tn / 2 : 0;  // the smallest TM with 2 TM + 1 >= tn
+  const int lo = need > t0 ? need : t0;
+  return t1 > lo ? t1 - lo : 0;
+}
 __device__ __forceinline__ void pair_of(const OzParams &p, int idx, int &TM, int &tn) {
-  if (!p.lower) {
-    TM = idx / p.tiles_n;
-    tn = idx % p.tiles_n;
-    return;
+  const int T2 = (p.tiles_m + 1) / 2;
+  for (int t0 = 0; t0 < T2; t0 += p.band) {
+    const int t1 = t0 + p.band < T2 ? t0 + p.band : T2;
+    // columns of this band: all of C, or for a lower C those up to the last
+    // row pair's diagonal (and inside the matrix)
+    const int ncol = p.lower ? (2 * t1 < p.tiles_m ? 2 * t1 : p.tiles_m) : p.tiles_n;
+    if (!p.lower) {
+      const int cnt = (t1 - t0) * ncol;
+      if (idx < cnt) {
+        tn = idx / (t1 - t0);
+        TM = t0 + idx % (t1 - t0);
+        return;
+      }
+      idx -= cnt;
+      continue;
+    }
+    for (int c = 0; c < ncol; ++c) {
+      const int cc = band_col_count(c, t0, t1);
+      if (idx < cc) {
+        tn = c;
+        TM = t1 - cc + idx;
+        return;
+      }
+      idx -= cc;
+    }
   }
-  // TM (TM + 1) <= idx < (TM + 1) (TM + 2)
-  int r = (int)((sqrt(4.0 * idx + 1.0) - 1.0) * 0.5);
-  while ((r + 1) * (r + 2) <= idx) ++r;
-  while (r * (r + 1) > idx) --r;
-  TM = r;
-  tn = idx - r * (r + 1);
+  TM = T2;  // past the last item (not reached for idx < p.ntiles)
+  tn = 0;
 }
 // This CTA's rank in its pair, its first work item and the stride between
 // its items (read from special registers where used: held in registers
@@ -1061,6 +1091,11 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
   p.no_loads = tune_get("test_wait_timeout", 0) != 0 ? 1 : 0;
   p.wait_ns = p.no_loads ? 1000000ull : kWaitNs;  // 1 ms in the failure-path test
   const int tiles_m = (int)(Mpad / OBM);
+  p.tiles_m = tiles_m;
+  {
+    const int64_t b = tune_get("ozaki_band", 6);
+    p.band = b < 1 ? 1 : (b > 4096 ? 4096 : (int)b);
+  }
   const int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
   // clusters of two on tile-row pairs (B shared through multicast) unless
   // switched off or the output has a single tile row
