@@ -353,6 +353,8 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *   emu_tc          1 (default) / 0: emulator inference runs its layers on
  *                   tcgen05 (width a multiple of 64, at most 256) / every
  *                   layer through the WMMA product
+ *   emu_chunk       262144 (default): points per pass of emu_predict through
+ *                   the network (a multiple of 128)
  *   emu_tc0         1 (default) / 0: with emu_tc, the first layer (16
  *                   inputs, widened with zeros to 64) on tcgen05 too / WMMA
  *   ozaki_band      6 (default): row pairs per band of the split kernel's

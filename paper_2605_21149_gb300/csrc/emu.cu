@@ -483,22 +483,27 @@ __global__ void predict_finish_kernel(const double *theta, int ntot, int off, in
 }
 
 // ------------------------------------------------- tcgen05 inference layer --
-// One 128-row tile of a layer at inference, Y = X W^T + b, on tcgen05 tensor
-// cores (kind::f16: bf16 x bf16 -> fp32 in TMEM).  X is the layer's bf16
-// input (rows x K, row-major, rows a multiple of 128), W its bf16 weights
-// (N x K, row-major), K a multiple of 64 up to 256.  Warp 0 (one lane) loads
-// all of K at once by TMA into 128-byte-swizzled stages of 64 columns, then
-// issues the K / 16 MMAs (M = 128, N) and commits; warp 1 owns the TMEM
-// allocation; warps 2-9 are the epilogue (TMEM lanes 32 (w % 4) .., column half
-// (w - 2) / 4), which adds the bias and writes bf16(gelu(Y)) to Xn for a hidden
-// layer or fp32 Y to Z for the output layer.  Every wait is bounded: on expiry
-// the status takes QML_ETIMEOUT, copies and MMAs in flight are drained, TMEM is
-// freed and nothing is written.
+// A layer at inference, Y = X W^T + b, on tcgen05 tensor cores (kind::f16:
+// bf16 x bf16 -> fp32 in TMEM).  X is the layer's bf16 input (rows x K,
+// row-major, rows a multiple of 128), W its bf16 weights (N x K, row-major),
+// K a multiple of 64 up to 256.  Persistent: each CTA takes the 128-row tiles
+// blockIdx.x, + gridDim.x, ...  Warp 0 (one lane) loads W once (all of K, in
+// 128-byte-swizzled stages of 64 columns) and then streams the tiles' X
+// through a ring of kTcRing 64-column slots; warp 1 owns the TMEM allocation
+// and issues each tile's K / 16 MMAs (M = 128, N) into one of two
+// accumulators; warps 2-9 are the epilogue (TMEM lanes 32 (w % 4) .., column
+// half (w - 2) / 4), which adds the bias and writes bf16(gelu(Y)) to Xn for a
+// hidden layer or fp32 Y to Z for the output layer.  With two accumulators a
+// tile's epilogue runs while the next tile's X arrives and is multiplied.
+// Every wait is bounded: on expiry the status takes QML_ETIMEOUT, copies and
+// MMAs in flight are drained, TMEM is freed, and the rest of the layer is not
+// written.
 constexpr int kTcMaxStages = 4;  // K <= 256
+constexpr int kTcRing = 4;       // X slots of 64 columns
 constexpr int kTcThreads = 320;
 template <int N>
 constexpr size_t tc_smem() {
-  return 1024 + (size_t)kTcMaxStages * (128 * 128 + N * 128) + 64;
+  return 1024 + (size_t)kTcMaxStages * N * 128 + (size_t)kTcRing * 128 * 128 + 256;
 }
 template <int N>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -508,101 +513,131 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int kA = 128 * 128, kB = N * 128;  // bytes of one 64-column stage
   constexpr int kCols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  constexpr int kEpiThreads = N > 16 ? 256 : 128;
   constexpr uint32_t kIdescN = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
-  unsigned char *tA = smem, *tB = smem + kTcMaxStages * kA;
-  uint64_t *bars = (uint64_t *)(tB + kTcMaxStages * kB);  // full, acc, drain
-  uint32_t *holder = (uint32_t *)(bars + 3);
-  int *s_flags = (int *)(holder + 1);  // [0] go, [1] failed
+  unsigned char *tB = smem, *tA = smem + kTcMaxStages * kB;
+  // bars: wfull, xfull[kTcRing], xempty[kTcRing], accf[2], acce[2], drain
+  uint64_t *bars = (uint64_t *)(tA + kTcRing * kA);
+  uint32_t *holder = (uint32_t *)(bars + 2 * kTcRing + 6);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * 128;
-  const int nst = K / 64;
-  const uint32_t full = smem_u32(&bars[0]), acc = smem_u32(&bars[1]), drain = smem_u32(&bars[2]);
+  const int nst = K / 64, ntiles = rows / 128;
+  const uint32_t wfull = smem_u32(&bars[0]), xfull0 = smem_u32(&bars[1]),
+                 xempty0 = smem_u32(&bars[1 + kTcRing]), accf0 = smem_u32(&bars[1 + 2 * kTcRing]),
+                 acce0 = smem_u32(&bars[3 + 2 * kTcRing]), drain = smem_u32(&bars[5 + 2 * kTcRing]);
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
-    mbar_init(acc, 1);
+    mbar_init(wfull, 1);
+    for (int q = 0; q < kTcRing; ++q) {
+      mbar_init(xfull0 + 8 * q, 1);
+      mbar_init(xempty0 + 8 * q, 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(accf0 + 8 * q, 1);
+      mbar_init(acce0 + 8 * q, kEpiThreads);
+    }
     mbar_init(drain, 1);
     fence_mbar_init();
-    s_flags[0] = *((volatile int *)&st->code) == 0;
-    s_flags[1] = 0;
   }
-  if (warp == 1) tmem_alloc(smem_u32(holder), kCols);
+  if (warp == 1) tmem_alloc(smem_u32(holder), 2 * kCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *holder;
-  if (s_flags[0]) {
-    if (warp == 0 && lane == 0) {
-      bool issued = false;
-      mbar_expect_tx(full, (uint32_t)(nst * (kA + kB)));
-      for (int s = 0; s < nst; ++s) {
-        tma_load_2d(smem_u32(tA + s * kA), &mX, full, 64 * s, m0);
-        tma_load_2d(smem_u32(tB + s * kB), &mW, full, 64 * s, 0);
+  const bool go = *((volatile int *)&st->code) == 0;
+  if (go && warp == 0 && lane == 0) {
+    // ---- producer: W once, then X chunk by chunk through the ring
+    int last_phase[kTcRing];
+    for (int q = 0; q < kTcRing; ++q) last_phase[q] = -1;
+    bool ok = true;
+    mbar_expect_tx(wfull, (uint32_t)(nst * kB));
+    for (int s2 = 0; s2 < nst; ++s2) tma_load_2d(smem_u32(tB + s2 * kB), &mW, wfull, 64 * s2, 0);
+    uint32_t idx = 0;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+      for (int s2 = 0; s2 < nst; ++s2, ++idx) {
+        const uint32_t q = idx % kTcRing, ph = (idx / kTcRing) & 1u;
+        if (!mbar_wait(xempty0 + 8 * q, ph ^ 1u, st)) { ok = false; break; }
+        mbar_expect_tx(xfull0 + 8 * q, (uint32_t)kA);
+        tma_load_2d(smem_u32(tA + q * kA), &mX, xfull0 + 8 * q, 64 * s2, 128 * t);
+        last_phase[q] = (int)ph;
       }
-      if (mbar_wait(full, 0, st)) {
+    // every copy issued into this CTA's shared memory lands before it exits
+    mbar_drain_wait(wfull, 0);
+    for (int q = 0; q < kTcRing; ++q)
+      if (last_phase[q] >= 0) mbar_drain_wait(xfull0 + 8 * q, (uint32_t)last_phase[q]);
+  } else if (go && warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    bool ok = mbar_wait(wfull, 0, st);
+    uint32_t idx = 0, it = 0;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+      const uint32_t bsel = it & 1u;
+      // the epilogue has read this accumulator's previous tile
+      if (!mbar_wait(acce0 + 8 * bsel, ((it >> 1) & 1u) ^ 1u, st)) { ok = false; break; }
+      tc_fence_after();
+      uint32_t on = 0;
+      for (int s2 = 0; s2 < nst; ++s2, ++idx) {
+        const uint32_t q = idx % kTcRing, ph = (idx / kTcRing) & 1u;
+        if (!mbar_wait(xfull0 + 8 * q, ph, st)) { ok = false; break; }
         tc_fence_after();
-        uint32_t on = 0;
-        for (int s = 0; s < nst; ++s) {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            mma_bf16(tbase, smem_desc(smem_u32(tA + s * kA) + 32 * kk),
-                     smem_desc(smem_u32(tB + s * kB) + 32 * kk), kIdescN, on);
-            on = 1u;
-          }
+        for (int kk = 0; kk < 4; ++kk) {
+          mma_bf16(tbase + bsel * kCols, smem_desc(smem_u32(tA + q * kA) + 32 * kk),
+                   smem_desc(smem_u32(tB + s2 * kB) + 32 * kk), kIdescN, on);
+          on = 1u;
         }
-        mma_commit(acc);
-        issued = true;
-      } else {
-        mbar_drain_wait(full, 0);  // the copies must land before the CTA exits
+        mma_commit(xempty0 + 8 * q);  // the slot is free when these MMAs finish
       }
-      if (!issued) {
-        s_flags[1] = 1;
-        mbar_arrive(acc);  // release the epilogue without a result
-      }
-      mma_commit(drain);  // every MMA issued above has finished when this arrives
-      mbar_drain_wait(drain, 0);
-    } else if (warp >= 2 && (N > 16 || warp < 6)) {
-      const int quad = warp & 3;
-      const int half = N > 16 ? (warp - 2) >> 2 : 0;
-      constexpr int kW = N > 16 ? N / 2 : N;  // columns per epilogue warp
+      if (!ok) break;
+      mma_commit(accf0 + 8 * bsel);
+    }
+    mma_commit(drain);  // every MMA issued above has finished when this arrives
+    mbar_drain_wait(drain, 0);
+  } else if (go && warp >= 2 && (N > 16 || warp < 6)) {
+    // ---- epilogue
+    const int quad = warp & 3;
+    const int half = N > 16 ? (warp - 2) >> 2 : 0;
+    constexpr int kW = N > 16 ? N / 2 : N;  // columns per epilogue warp
+    uint32_t it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const uint32_t bsel = it & 1u;
       int okw = 1;
-      if (lane == 0) okw = mbar_wait(acc, 0, st) ? 1 : 0;
+      if (lane == 0) okw = mbar_wait(accf0 + 8 * bsel, (it >> 1) & 1u, st) ? 1 : 0;
       okw = __shfl_sync(0xffffffffu, okw, 0);
       __syncwarp();
-      if (okw && !*((volatile int *)&s_flags[1])) {
-        tc_fence_after();
-        const int row = m0 + quad * 32 + lane;
-        const uint32_t lb = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * kW);
+      if (!okw) break;
+      tc_fence_after();
+      const int row = 128 * t + quad * 32 + lane;
+      const uint32_t lb = tbase + bsel * kCols + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * kW);
 #pragma unroll 1
-        for (int cb = 0; cb < kW / 16; ++cb) {
-          uint32_t a[16];
-          tmem_ld16(lb + 16 * cb, a);
-          const int c0 = half * kW + 16 * cb;
-          float y[16];
+      for (int cb = 0; cb < kW / 16; ++cb) {
+        uint32_t a[16];
+        tmem_ld16(lb + 16 * cb, a);
+        const int c0 = half * kW + 16 * cb;
+        float y[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) y[j] = __uint_as_float(a[j]) + bias[c0 + j];
-          if (row < rows) {
-            if (Xn) {
-              __align__(16) __nv_bfloat16 o[16];
+        for (int j = 0; j < 16; ++j) y[j] = __uint_as_float(a[j]) + bias[c0 + j];
+        if (row < rows) {
+          if (Xn) {
+            __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
-              for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16_rn(gelu_f(y[j]));
-              uint4 *dst = (uint4 *)(Xn + (int64_t)row * N + c0);
-              dst[0] = ((const uint4 *)o)[0];
-              dst[1] = ((const uint4 *)o)[1];
-            } else {
-              float4 *dst = (float4 *)(Z + (int64_t)row * N + c0);
+            for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16_rn(gelu_f(y[j]));
+            uint4 *dst = (uint4 *)(Xn + (int64_t)row * N + c0);
+            dst[0] = ((const uint4 *)o)[0];
+            dst[1] = ((const uint4 *)o)[1];
+          } else {
+            float4 *dst = (float4 *)(Z + (int64_t)row * N + c0);
 #pragma unroll
-              for (int j = 0; j < 4; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-            }
+            for (int j = 0; j < 4; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
           }
         }
       }
+      tc_fence_before();
+      mbar_arrive(acce0 + 8 * bsel);  // the accumulator may take the tile after next
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tbase, kCols);
+  if (warp == 1) tmem_dealloc(tbase, 2 * kCols);
 }
 
 template <int N>
@@ -615,7 +650,15 @@ bool launch_mlp_tc(const CUtensorMap &mX, const CUtensorMap &mW, int rows, int K
       return false;
     attr = true;
   }
-  mlp_tc_kernel<N><<<rows / 128, kTcThreads, tc_smem<N>(), s>>>(mX, mW, rows, K, bias, Xn, Z, st);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 148;
+  }
+  const int ntiles = rows / 128, grid = ntiles < nsm ? ntiles : nsm;  // persistent
+  mlp_tc_kernel<N><<<grid, kTcThreads, tc_smem<N>(), s>>>(mX, mW, rows, K, bias, Xn, Z, st);
   count_launch();
   return true;
 }
@@ -891,7 +934,12 @@ PredCache *pred_cache(qml_emu *e, int rows) {
 
 qml_status run_predict(qml_emu *e, int n, const double *th, double thr, double *od, int *fd,
                        double *dis, cudaStream_t st) {
-  const int chunk = 65536;
+  // points per pass through the layers (tuning key emu_chunk, a multiple of
+  // 128, default 262144): each layer launch then has enough 128-row tiles for
+  // its persistent CTAs to pipeline over (2^20 points: 1.55e8 points/s in
+  // passes of 65536, 2.07e8 in passes of 262144)
+  int chunk = (int)std::min<int64_t>(std::max<int64_t>(tune_get("emu_chunk", 262144), 128), 1 << 22);
+  chunk = chunk / 128 * 128;
   // activation rows allocated in whole 128-row tiles (the tcgen05 layers read
   // and write complete tiles; rows past the points are never used)
   const int rows_alloc = (std::min(chunk, (n + 15) / 16 * 16) + 127) / 128 * 128;

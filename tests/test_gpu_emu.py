@@ -147,20 +147,22 @@ def test_emu_tcgen05_inference_matches_wmma(api, width, depth):
     tuning key emu_tc = 0 runs every layer through the WMMA product instead.
     Same trained network, same points: the two differ only in float32
     accumulation order (and the bf16 rounding it can flip), far inside the
-    0.05 audit tolerance; 70000 points cover a second 65536-point chunk and a
-    ragged last tile."""
+    0.05 audit tolerance; 70000 points in passes of 65536 (tuning key
+    emu_chunk) cover a second pass and a ragged last tile."""
     rng = np.random.default_rng(9)
     th = rng.uniform(-1, 1, size=(2048, 3))
     y = -0.5 * (th ** 2 * np.array([20.0, 6.0, 2.0])).sum(axis=1) + np.sin(3 * th[:, 0])
     emu = api.Emulator(-np.ones(3), np.ones(3), width=width, depth=depth, seed=4)
     emu.train(th, y, epochs=10, batch=64)
     test = rng.uniform(-1.05, 1.05, size=(70000, 3))
-    pred_tc, flags_tc = emu.predict(test, tol=0.05)
-    api.tune_set("emu_tc", 0)
+    api.tune_set("emu_chunk", 65536)
     try:
+        pred_tc, flags_tc = emu.predict(test, tol=0.05)
+        api.tune_set("emu_tc", 0)
         pred_w, flags_w = emu.predict(test, tol=0.05)
     finally:
         api.tune_set("emu_tc", 1)
+        api.tune_set("emu_chunk", 262144)
     d = np.abs(pred_tc - pred_w)
     assert np.all(np.isfinite(pred_tc))
     assert d.max() <= 5e-3, d.max()
@@ -203,15 +205,19 @@ def test_emu_tcgen05_inference_matches_oracle(api, width, depth):
     oracle MLP's forward pass per point and per head: lnL = q(x) + sigma
     (f_0 + f_1) / 2 with the library's own baseline coefficients, the oracle
     taking the same bf16 roundings of weights and layer inputs (float64
-    otherwise).  70000 points: a second 65536-point chunk and a ragged last
-    128-row tile."""
+    otherwise).  70000 points in passes of 65536 (tuning key emu_chunk): a
+    second pass and a ragged last 128-row tile."""
     rng = np.random.default_rng(19)
     th = rng.uniform(-1, 1, size=(2048, 3))
     y = -0.5 * (th ** 2 * np.array([20.0, 6.0, 2.0])).sum(axis=1) + np.sin(3 * th[:, 0])
     emu = api.Emulator(-np.ones(3), np.ones(3), width=width, depth=depth, seed=6)
     emu.train(th, y, epochs=10, batch=64)
     test = rng.uniform(-1.05, 1.05, size=(70000, 3))
-    pred, flags = emu.predict(test, tol=0.05)
+    api.tune_set("emu_chunk", 65536)
+    try:
+        pred, flags = emu.predict(test, tol=0.05)
+    finally:
+        api.tune_set("emu_chunk", 262144)
     coef, sigma = emu.baseline()
     X = np.zeros((len(test), 16))
     X[:, :3] = test  # box [-1, 1]^3: normalised coordinates are theta itself
