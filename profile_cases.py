@@ -8,6 +8,9 @@
     python profile_cases.py fisher   # one full qml_fisher
     python profile_cases.py step --precision 1
         # one bench step: qml_fisher + qml_estimate (100 maps) + pix_loglike
+    python profile_cases.py emu_predict
+        # emulator inference: a 4 x 256 emulator trained for two epochs on
+        # 8192 points of a 4-D test function predicts 2^18 points
 
 Each case runs its call `--reps` times (default 2) after one untimed call and
 prints the CUDA-event time per call.
@@ -27,7 +30,8 @@ def main():
     from paper_2605_21149_gb300 import api, build, synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=("syrk", "syrk_split", "trail_split", "ybuild", "fisher", "step"))
+    ap.add_argument("case", choices=("syrk", "syrk_split", "trail_split", "ybuild", "fisher", "step",
+                                     "emu_predict"))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--tune", action="append", default=[],
@@ -48,6 +52,16 @@ def main():
         P = torch.randn(512, 6400, dtype=torch.float64, device="cuda").t()
         T = torch.zeros(6400, 6400, dtype=torch.float64, device="cuda").t()
         fn = lambda: api.gemm(P, P, T, transB=True, lower=True, alpha=-1.0, beta=1.0, precision=1)
+    elif args.case == "emu_predict":
+        import numpy as np
+        rng = np.random.default_rng(1)
+        th = rng.uniform(-1, 1, size=(8192, 4))
+        y = (-0.5 * (th ** 2 * np.array([30.0, 10.0, 5.0, 2.0])).sum(axis=1)
+             + np.sin(2 * th[:, 0]) * th[:, 1])
+        emu = api.Emulator(-np.ones(4), np.ones(4), seed=7)
+        emu.train(th, y, epochs=2, batch=64)
+        thi = torch.as_tensor(rng.uniform(-1.05, 1.05, size=(1 << 18, 4)), device="cuda")
+        fn = lambda: emu.predict(thi)
     elif args.case == "ybuild":
         fn = lambda: api.ybuild(prob)
     elif args.case == "fisher":
