@@ -370,6 +370,15 @@ qml_status qml_gemm(int32_t transA, int32_t transB, int64_t m, int64_t nn, int64
  *                   moving between neighbouring CTAs, one grid barrier a
  *                   sweep; slower on this part); both within the parity
  *                   tolerances
+ *   eig_mixed       1 (default) / 0: the two-sided form first runs float32
+ *                   Jacobi sweeps on one thread-block cluster, rebuilds
+ *                   their rotations in float64 as an orthogonal V0 and starts
+ *                   the float64 sweeps from V0^T F V0 (same stopping rule,
+ *                   two float64 sweeps instead of about seven at TQU Nside
+ *                   16) / float64 sweeps only.  Used for padded orders
+ *                   64 .. 640; other orders take the float64 sweeps only
+ *   eig_cluster     16 (default) / 8: CTAs in the float32 phase's cluster
+ *                   (16 falls back to 8 where the part cannot launch it)
  *   split_lookahead 1 (default) / 0: the split-precision Cholesky runs the
  *                   next panel's float64 diagonal chain on a second,
  *                   high-priority stream beside the trailing update and the

@@ -3,7 +3,10 @@
 // F^-1/2 = U Xi^-1/2 U^T with eigenvalues below 1e-12 x max set to zero) and
 // the inverse used by the deconvolved normalisation (Eq. deconvolved).
 //
-// Two forms.  The default is the two-sided form that follows.  The other
+// Two forms.  The default is the two-sided form that follows, which by
+// default (tuning key eig_mixed) first runs float32 sweeps on one
+// thread-block cluster and starts its float64 sweeps from the rotated matrix
+// (the float32 pre-rotation phase, further below).  The other
 // (tuning key eig_onesided = 1) is a one-sided Jacobi on the Cholesky factor
 // of F (ojacobi_kernel below) with one grid barrier a sweep; on this part it
 // is the slower one (TQU Nside 16: qml_fisher 52.3 against 45.8 ms), since
@@ -22,6 +25,7 @@
 // which keeps A exactly symmetric.  Barrier waits are bounded: after
 // kSpinLimit polls a block records QML_ETIMEOUT and every block returns.
 #include "internal.cuh"
+#include "ptx.cuh"
 
 #include <math.h>
 
@@ -596,17 +600,374 @@ __global__ void eig_scale_kernel(const double *V, int n, const double *fac, doub
   }
 }
 
+// ------------------------------------------- float32 pre-rotation phase --
+// The same cyclic Jacobi, first in float32 on one thread-block cluster
+// (float32 arithmetic is 64 times the float64 rate on this part, and a
+// cluster barrier is far cheaper than a grid barrier).  Only its rotations
+// are kept: each is stored as its half-angle tau, from which an orthogonal
+// basis V0 is rebuilt in float64 exactly as the float64 rounds build theirs
+// (c = (1 - tau^2) / (1 + tau^2), s = 2 tau / (1 + tau^2)), so V0 is
+// orthogonal to float64 rounding whatever float32 did.  The float64 sweeps
+// then start from V0^T F V0, which is diagonal to float32 accuracy and needs
+// two sweeps where F itself needs about seven; the eigenpairs are still
+// those of the float64 sweeps and their stopping rule.
+//
+// Layout: CTA c of the cluster owns pairs [c h / CN, (c + 1) h / CN); a pair
+// a holds the columns in slots a (side P) and n - 1 - a (side Q), float32,
+// rows indexed by player, double-buffered by round parity.  A round: every
+// CTA forms all h rotations from their three entries (a_pp, a_qq, a_qp, in
+// a table of its own), then applies J^T B J to each 2 x 2 block of its own
+// column pairs and writes the result where the column sits in the next round
+// (slot x -> x - 1 for x >= 2, slot 1 -> n - 1, slot 0 fixed: pair a's P
+// column goes to P(a - 1), except P(1) -> Q(0) and P(0) -> P(0); its Q column
+// to Q(a + 1), except Q(h - 1) -> P(h - 1)).  The thread that writes one of
+// the next round's three entries of a pair also stores it into every CTA's
+// table, so that no CTA waits on a remote load after the cluster barrier
+// that ends the round.  Between that barrier's arrive and its wait a CTA
+// stores its half-angles to global memory and builds the player table of a
+// later round, so neither delays the barrier.  Every CTA takes the same sweep
+// decision from the same sums, so all of them pass the same barriers.
+constexpr int kJ32Threads = 512;
+constexpr int kJ32MaxSweeps = 8;
+// largest padded order of the float32 phase (its columns fit in shared
+// memory at 16 CTAs per cluster)
+constexpr int kJ32MaxN = 640;
+
+__host__ __device__ constexpr size_t j32_smem_bytes(int n, int cn) {
+  return 16 * (size_t)((n / 2 + cn - 1) / cn) * n  // columns
+         + 32                                        // partial sums, decision
+         + 8 * (size_t)(n / 2)                       // rotations (c, s)
+         + 24 * (size_t)(n / 2)                      // rotation inputs, two rounds
+         + 8 * (size_t)n                             // players of four rounds
+         + (size_t)(n / 2) + 16;                     // owner of each pair
+}
+
+// half-angle of the Jacobi rotation zeroing a_pq (the steps of the float64
+// `rotation` above, in float32 with the fast reciprocal and square root: the
+// float64 sweeps do not depend on this angle's accuracy)
+__device__ __forceinline__ float rotation_tau32(float app, float aqq, float apq) {
+  const float d = aqq - app, tw = 2.0f * apq;
+  const float m = fmaxf(fabsf(d), fabsf(tw));
+  if (!(m > 0.0f) || !isfinite(m)) return 0.0f;
+  const float inv = __fdividef(1.0f, m);
+  const float ds = d * inv, ts = tw * inv;
+  const float r2 = ds * ds + ts * ts;  // in [1, 2]
+  const float t = __fdividef(ds >= 0.0f ? ts : -ts, fabsf(ds) + r2 * rsqrtf(r2));
+  const float u = 1.0f + t * t;  // in [1, 2]
+  const float tau = __fdividef(t, 1.0f + u * rsqrtf(u));
+  return isfinite(tau) ? tau : 0.0f;
+}
+
+template <int CN>
+__global__ void __launch_bounds__(kJ32Threads) jacobi32_kernel(const double *A, int n, int max_sweeps,
+                                                                float *taus, int *rounds_out) {
+  extern __shared__ __align__(16) unsigned char j32_smem[];
+  const int h = n / 2;
+  const int rank = (int)cluster_ctarank();
+  const int lo = rank * h / CN, np = (rank + 1) * h / CN - lo;
+  const int maxp = (h + CN - 1) / CN;
+  float *cols = (float *)j32_smem;
+  double *part = (double *)(j32_smem + 16 * (size_t)maxp * n);
+  int *s_go = (int *)(part + 2);
+  float2 *rot = (float2 *)(part + 4);
+  float *inp = (float *)(rot + h);  // [2][h][3]: a_pp, a_qq, a_qp of each pair
+  short *tab = (short *)(inp + 6 * h);  // [4][n]: round g's players in table g mod 4
+  unsigned char *own = (unsigned char *)(tab + 4 * n);
+  __shared__ double sred[2][kJ32Threads / 32];
+  auto col = [&](int par, int la, int side) { return cols + ((size_t)(par * maxp + la) * 2 + side) * n; };
+  for (int a = threadIdx.x; a < h; a += blockDim.x) own[a] = (unsigned char)(((a + 1) * CN + h - 1) / h - 1);
+  // scale by 2^-e, e the binary exponent of the largest diagonal entry
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(A[i + (size_t)i * n]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sred[0][threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sred[0][w]);
+  int ex = 0;
+  if (mx > 0.0 && isfinite(mx)) frexp(mx, &ex);
+  const double sc = ldexp(1.0, -ex);
+  for (int e = threadIdx.x; e < np * 2 * n; e += blockDim.x) {
+    const int i = e % n, cs = e / n, la = cs >> 1, side = cs & 1;
+    const int j = side ? n - 1 - (lo + la) : lo + la;
+    col(0, la, side)[i] = (float)(A[i + (size_t)j * n] * sc);
+  }
+  for (int x = threadIdx.x; x < n; x += blockDim.x)
+    for (int k = 0; k < 3; ++k) tab[k * n + x] = (short)player(x, k, n);
+  // the first round's rotation inputs (pair a: players a and n - 1 - a)
+  for (int a = threadIdx.x; a < h; a += blockDim.x) {
+    const int q = n - 1 - a;
+    inp[3 * a] = (float)(A[a + (size_t)a * n] * sc);
+    inp[3 * a + 1] = (float)(A[q + (size_t)q * n] * sc);
+    inp[3 * a + 2] = (float)(A[q + (size_t)a * n] * sc);
+  }
+  cluster_sync_all();  // every CTA of the cluster has started and loaded its columns
+  const uint32_t part_u32 = smem_u32(part), inp_u32 = smem_u32(inp);
+  // this thread's first 2 x 2 block (local pair la, row pair b) and its stride
+  const int la0 = (int)threadIdx.x / h, b0 = (int)threadIdx.x - la0 * h;
+  const int dla = (int)blockDim.x / h, db = (int)blockDim.x - dla * h;
+  int par = 0, g = 0;
+  double prev = 0.0;
+  for (int sweep = 0;; ++sweep) {
+    // off-diagonal and diagonal sums of squares of this CTA's columns (at a
+    // sweep's start slot x holds player x)
+    double off = 0.0, dia = 0.0;
+    for (int e = threadIdx.x; e < np * 2 * n; e += blockDim.x) {
+      const int i = e % n, cs = e / n, la = cs >> 1, side = cs & 1;
+      const int j = side ? n - 1 - (lo + la) : lo + la;
+      const double v = (double)col(par, la, side)[i];
+      if (i == j) dia += v * v; else off += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_down_sync(0xffffffffu, off, o);
+      dia += __shfl_down_sync(0xffffffffu, dia, o);
+    }
+    __syncthreads();  // sred is free again
+    if ((threadIdx.x & 31) == 0) {
+      sred[0][threadIdx.x >> 5] = off;
+      sred[1][threadIdx.x >> 5] = dia;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double so = 0.0, sd = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        so += sred[0][w];
+        sd += sred[1][w];
+      }
+      part[0] = so;
+      part[1] = sd;
+    }
+    cluster_sync_all();
+    if (threadIdx.x == 0) {
+      // the same sums in the same order in every CTA: the same decision
+      double to = 0.0, td = 0.0;
+      for (int c = 0; c < CN; ++c) {
+        to += dsm_ld_f64(dsm_map(part_u32, (uint32_t)c));
+        td += dsm_ld_f64(dsm_map(part_u32 + 8, (uint32_t)c));
+      }
+      int go = 1;
+      if (sweep >= max_sweeps) go = 0;
+      else if (to <= 0x1p-46 * (td + to)) go = 0;  // float32 rounding level
+      else if (sweep > 0 && to > 0.25 * prev) go = 0;  // stalled
+      prev = to;
+      *s_go = go;
+    }
+    __syncthreads();
+    if (!*s_go) break;
+    for (int r = 0; r < n - 1; ++r, ++g) {
+      const short *pl = tab + (g & 3) * n, *pl2 = tab + ((g + 1) & 3) * n;
+      // one pair per thread (h <= kJ32MaxN / 2 < kJ32Threads)
+      float my_tau = 0.0f;
+      if ((int)threadIdx.x < h) {
+        const float *in = inp + 3 * ((size_t)par * h + threadIdx.x);
+        my_tau = rotation_tau32(in[0], in[1], in[2]);
+        const float t2 = my_tau * my_tau, w = __fdividef(1.0f, 1.0f + t2);
+        rot[threadIdx.x] = make_float2((1.0f - t2) * w, 2.0f * my_tau * w);
+      }
+      __syncthreads();
+      const uint32_t nin = inp_u32 + 12u * (uint32_t)((par ^ 1) * h);  // next round's table
+      auto bcast = [&](int pair, int slot, float v) {
+#pragma unroll
+        for (int c = 0; c < CN; ++c) dsm_st_f32(dsm_map(nin + 4u * (uint32_t)(3 * pair + slot), (uint32_t)c), v);
+      };
+      for (int la = la0, b = b0; la < np;) {
+        const int a = lo + la;
+        const float2 ra = rot[a], rb = rot[b];
+        const int pb = pl[b], qb = pl[n - 1 - b];
+        const float *P = col(par, la, 0), *Q = P + n;
+        const float x00 = P[pb], x01 = Q[pb], x10 = P[qb], x11 = Q[qb];
+        // X J_a (the pair's columns), then J_b^T (rows pb, qb)
+        const float y00 = ra.x * x00 - ra.y * x01, y01 = ra.y * x00 + ra.x * x01;
+        const float y10 = ra.x * x10 - ra.y * x11, y11 = ra.y * x10 + ra.x * x11;
+        const float z00 = rb.x * y00 - rb.y * y10, z10 = rb.y * y00 + rb.x * y10;
+        const float z01 = rb.x * y01 - rb.y * y11, z11 = rb.y * y01 + rb.x * y11;
+        const int dpa = a <= 1 ? 0 : a - 1, dps = a == 1 ? 1 : 0;
+        const int dqa = a == h - 1 ? h - 1 : a + 1, dqs = a == h - 1 ? 0 : 1;
+        const int cp = own[dpa], cq = own[dqa];
+        float *DP = col(par ^ 1, dpa - cp * h / CN, dps), *DQ = col(par ^ 1, dqa - cq * h / CN, dqs);
+        if (cp == rank) {
+          DP[pb] = z00;
+          DP[qb] = z10;
+        } else {
+          const uint32_t d = dsm_map(smem_u32(DP), (uint32_t)cp);
+          dsm_st_f32(d + 4u * pb, z00);
+          dsm_st_f32(d + 4u * qb, z10);
+        }
+        if (cq == rank) {
+          DQ[pb] = z01;
+          DQ[qb] = z11;
+        } else {
+          const uint32_t d = dsm_map(smem_u32(DQ), (uint32_t)cq);
+          dsm_st_f32(d + 4u * pb, z01);
+          dsm_st_f32(d + 4u * qb, z11);
+        }
+        // the next round's rotation inputs among these entries: the diagonal
+        // of both columns (in the pair's own block, b == a: rows pb and qb
+        // are the columns' players) and, for a column that becomes a P
+        // column, its row at the next round's partner
+        if (b == a) {
+          bcast(dpa, dps, z00);      // P column: a_pp of P(dpa), or a_qq of Q(0)
+          bcast(dqa, dqs, z11);      // Q column: a_qq of Q(dqa), or a_pp of P(h - 1)
+        }
+        if (dps == 0) {
+          const int rq = pl2[n - 1 - dpa];
+          if (pb == rq) bcast(dpa, 2, z00);
+          else if (qb == rq) bcast(dpa, 2, z10);
+        }
+        if (dqs == 0) {
+          const int rq = pl2[h];
+          if (pb == rq) bcast(dqa, 2, z01);
+          else if (qb == rq) bcast(dqa, 2, z11);
+        }
+        la += dla;
+        b += db;
+        if (b >= h) {
+          b -= h;
+          ++la;
+        }
+      }
+      cluster_arrive_release();
+      if (rank == 0 && (int)threadIdx.x < h) taus[(size_t)g * h + threadIdx.x] = my_tau;
+      // the table of round g + 3 (last read in round g - 1; first read after
+      // the next round's barrier, which every thread reaches after this)
+      for (int x = threadIdx.x; x < n; x += blockDim.x) tab[((g + 3) & 3) * n + x] = (short)player(x, g + 3, n);
+      __syncwarp();
+      cluster_wait_acquire();
+      par ^= 1;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) *rounds_out = g;
+  cluster_sync_all();  // no CTA leaves while another may read its shared memory
+}
+
+// (c, s) in float64 of every stored rotation, from its half-angle
+__global__ void rot_cs_kernel(const float *taus, const int *rounds, int h, double2 *cs) {
+  const int64_t total = (int64_t)(*rounds) * h;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double t = (double)taus[e];
+    if (!isfinite(t)) t = 0.0;
+    const double t2 = t * t;
+    const double w = 1.0 / (1.0 + t2);
+    cs[e] = make_double2((1.0 - t2) * w, (2.0 * t) * w);
+  }
+}
+
+// V0 = J_1 J_2 ... J_R, one CTA per row (rows are independent: v <- v J_g);
+// thread a applies pair a's rotation each round, the (c, s) of the next
+// rounds loaded ahead
+__global__ void vbuild_kernel(const double2 *cs, const int *rounds, int n, double *V) {
+  extern __shared__ double vrow[];
+  const int row = blockIdx.x, h = n / 2, a = threadIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) vrow[i] = (i == row) ? 1.0 : 0.0;
+  __syncthreads();
+  const int R = *rounds;
+  const bool act = a < h;
+  auto fetch = [&](int g) {
+    return (act && g < R) ? cs[(size_t)g * h + a] : make_double2(1.0, 0.0);
+  };
+  double2 c0 = fetch(0), c1 = fetch(1), c2 = fetch(2), c3 = fetch(3);
+  int p = act ? player(a, 0, n) : 0, q = act ? player(n - 1 - a, 0, n) : 0;
+  for (int g = 0; g < R; ++g) {
+    const double2 cur = c0;
+    c0 = c1;
+    c1 = c2;
+    c2 = c3;
+    c3 = fetch(g + 4);
+    if (act) {
+      const double vp = vrow[p], vq = vrow[q];
+      vrow[p] = cur.x * vp - cur.y * vq;
+      vrow[q] = cur.y * vp + cur.x * vq;
+      // players of pair a in the next round (slot a > 0 and slot n - 1 - a
+      // advance by one along 1 .. n - 1; slot 0 holds player 0)
+      p = p == 0 ? 0 : (p == n - 1 ? 1 : p + 1);
+      q = q == n - 1 ? 1 : q + 1;
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) V[row + (size_t)j * n] = vrow[j];
+}
+
+// A <- (A + A^T) / 2 in place
+__global__ void symmetrize_kernel(double *A, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) {
+      const double v = 0.5 * (A[e] + A[j + (int64_t)i * n]);
+      A[e] = v;
+      A[j + (int64_t)i * n] = v;
+    }
+  }
+}
+
 }  // namespace
 
-size_t fisher_eig_work_doubles(int na) {
-  const size_t n = (size_t)(na + (na & 1)), h = n / 2, nb = (n + kNB - 1) / kNB;
+namespace {
+// doubles of the work area before the float32 phase's buffers (even, so
+// that the (c, s) pairs after them are 16-byte aligned)
+size_t eig_base_doubles(size_t n) {
+  const size_t h = n / 2, nb = (n + kNB - 1) / kNB;
   // two-sided: A0, A1, V, S1, S2, the barrier area, rotations; one-sided adds
   // the 64-block inverses and log parts of the Cholesky, pair flags, grid
   // flags and the mailboxes
-  return 5 * n * n + 2 * 4096 + 4 * n + nb * kNB * kNB + nb + 8 + 32 * h + 16 * h + 8 * h * n;
+  const size_t b = 5 * n * n + 2 * 4096 + 4 * n + nb * kNB * kNB + nb + 8 + 32 * h + 16 * h + 8 * h * n;
+  return b + (b & 1);
+}
+// stored rotations of the float32 phase
+size_t j32_rotations(size_t n) { return (size_t)kJ32MaxSweeps * (n - 1) * (n / 2); }
+}  // namespace
+
+size_t fisher_eig_work_doubles(int na) {
+  const size_t n = (size_t)(na + (na & 1));
+  size_t total = eig_base_doubles(n);
+  // float32 phase: half-angles (float), (c, s) pairs, the round count
+  if (n <= (size_t)kJ32MaxN) {
+    const size_t cnt = j32_rotations(n);
+    total += (cnt + 1) / 2 + ((cnt + 1) / 2 & 1) + 2 * cnt + 2;
+  }
+  return total;
 }
 
 namespace {
+// the float32 phase on one cluster of CN CTAs; false (nothing launched, no
+// error left behind) when this part cannot run it
+template <int CN>
+bool launch_j32(const double *A0, int n, float *taus, int *rounds, cudaStream_t st) {
+  const size_t smem = j32_smem_bytes(n, CN);
+  if (smem > 227 * 1024) return false;
+  if (cudaFuncSetAttribute(jacobi32_kernel<CN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      (CN > 8 && cudaFuncSetAttribute(jacobi32_kernel<CN>,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CN);
+  cfg.blockDim = dim3(kJ32Threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CN;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, jacobi32_kernel<CN>, &cfg) != cudaSuccess || ncl < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaLaunchKernelEx(&cfg, jacobi32_kernel<CN>, A0, n, kJ32MaxSweeps, taus, rounds) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  count_launch();
+  return true;
+}
+
 // F = L L^T in place in A (n x n, ld n, lower) by 64-wide blocks: factor and
 // invert each diagonal block, solve the rows below with the inverse, update
 // the rest (the float64 kernels of the Cholesky path).  A non-positive pivot
@@ -677,6 +1038,30 @@ cudaError_t run_fisher_eig(const double *F, int na, double *work, double *Finv, 
     if (e != cudaSuccess) return e;
     count_launch();
   } else {
+    // float32 pre-rotation (tuning key eig_mixed, default on): the float64
+    // sweeps below then start from A0 = V0^T A0 V0 with V = V0
+    if (tune_get("eig_mixed", 1) != 0 && n <= kJ32MaxN && h >= 32) {
+      const size_t cnt = j32_rotations((size_t)n);
+      double *mix = work + eig_base_doubles((size_t)n);
+      float *taus = (float *)mix;
+      const size_t tw = (cnt + 1) / 2 + ((cnt + 1) / 2 & 1);
+      double2 *cs = (double2 *)(mix + tw);
+      int *rounds = (int *)(mix + tw + 2 * cnt);
+      const int want = (int)tune_get("eig_cluster", 16);
+      const bool ran = (want >= 16 && launch_j32<16>(A0, n, taus, rounds, st)) ||
+                       launch_j32<8>(A0, n, taus, rounds, st);
+      if (ran) {
+        rot_cs_kernel<<<4 * (unsigned)nsm, 256, 0, st>>>(taus, rounds, h, cs);
+        count_launch();
+        vbuild_kernel<<<(unsigned)n, (unsigned)((h + 31) / 32 * 32), (size_t)n * sizeof(double), st>>>(
+            cs, rounds, n, V);
+        count_launch();
+        launch_dgemm(0, 0, n, n, n, 1.0, A0, n, V, n, 0.0, A1, n, 0, nullptr, st);
+        launch_dgemm(1, 0, n, n, n, 1.0, V, n, A1, n, 0.0, A0, n, 0, nullptr, st);
+        symmetrize_kernel<<<64, 256, 0, st>>>(A0, n);
+        count_launch();
+      }
+    }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, kJacobiThreads, 0);
     int nblocks = nsm * (occ > 0 ? 1 : 0);

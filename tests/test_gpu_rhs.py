@@ -104,17 +104,24 @@ def test_decorrelated_vs_extended_small(api, cfg, scale):
     assert e_gpu <= max(P.TOL, 20 * P.EPS * kappa), (e_gpu, kappa)
 
 
-@pytest.mark.parametrize("onesided", [0, 1])
-def test_decorrelated_vs_extended_tqu16(api, tqu16, onesided):
+@pytest.mark.parametrize("mode", ["mixed16", "mixed8", "float64", "onesided"])
+def test_decorrelated_vs_extended_tqu16(api, tqu16, mode):
     """TQU Nside 16 (kappa(F) ~ 7e8): the GPU's float64 F^-1/2 q against the
     extended-precision value; the measured error stays within the bound
-    20 eps kappa(F) that the float64 parity tests use.  Both eigensolvers:
-    the two-sided Jacobi on F (default) and the one-sided Jacobi on its
-    Cholesky factor (tuning key eig_onesided = 1); with each, the deconvolved
-    estimate stays within the parity tolerance too."""
+    20 eps kappa(F) that the float64 parity tests use.  Every eigensolver
+    form: the two-sided Jacobi on F after the float32 pre-rotation on a
+    cluster of 16 or of 8 CTAs (default: eig_mixed = 1), the two-sided
+    Jacobi alone (eig_mixed = 0), and the one-sided Jacobi on the Cholesky
+    factor (eig_onesided = 1); with each, the deconvolved estimate stays
+    within the parity tolerance too."""
     wl, maps, ref = tqu16
     sub = {"F": ref["F"], "q": ref["q"][:, :100], "cl_decorr": ref["cl_decorr"][:, :100]}
-    api.tune_set("eig_onesided", onesided)
+    keys = {"mixed16": {"eig_mixed": 1, "eig_cluster": 16},
+            "mixed8": {"eig_mixed": 1, "eig_cluster": 8},
+            "float64": {"eig_mixed": 0},
+            "onesided": {"eig_onesided": 1}}[mode]
+    for k, v in keys.items():
+        api.tune_set(k, v)
     try:
         e_gpu, e_ora, kappa = _decorr_errors(api, wl, maps[:, :100], sub)
         F, plan = api.fisher(api.Problem.from_workload(wl))
@@ -122,7 +129,9 @@ def test_decorrelated_vs_extended_tqu16(api, tqu16, onesided):
         plan.free()
     finally:
         api.tune_set("eig_onesided", 0)
-    print(f"decorrelated vs long double: {wl.name}: onesided {onesided}, kappa {kappa:.3g}, "
+        api.tune_set("eig_mixed", 1)
+        api.tune_set("eig_cluster", 16)
+    print(f"decorrelated vs long double: {wl.name}: {mode}, kappa {kappa:.3g}, "
           f"GPU {e_gpu:.3g}, oracle float64 {e_ora:.3g}, bound {20 * P.EPS * kappa:.3g}")
     assert e_gpu <= 20 * P.EPS * kappa, (e_gpu, kappa)
     assert P.cl_deconv_error(est["cl_deconv"], ref["cl_deconv"][:, :100], ref["F"]) <= P.TOL
