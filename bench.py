@@ -310,7 +310,10 @@ def emulator_form(api, torch, td, full=False):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     thi = torch.as_tensor(ilo + (ihi - ilo) * g.uniform(size=(ninf, 4)), device="cuda")
-    emu.predict(thi[:4096])
+    # steady state of repeated calls: one untimed call of the same size sizes
+    # the emulator's inference buffers, which it keeps between calls
+    emu.predict(thi)
+    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     _, fl = emu.predict(thi)

@@ -8,9 +8,9 @@
     python profile_cases.py fisher   # one full qml_fisher
     python profile_cases.py step --precision 1
         # one bench step: qml_fisher + qml_estimate (100 maps) + pix_loglike
-    python profile_cases.py emu_predict
+    python profile_cases.py emu_predict [--points N]
         # emulator inference: a 4 x 256 emulator trained for two epochs on
-        # 8192 points of a 4-D test function predicts 2^18 points
+        # 8192 points of a 4-D test function predicts N points (2^18)
 
 Each case runs its call `--reps` times (default 2) after one untimed call and
 prints the CUDA-event time per call.
@@ -34,6 +34,7 @@ def main():
                                      "emu_predict"))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--points", type=int, default=1 << 18, help="emu_predict: points per call")
     ap.add_argument("--tune", action="append", default=[],
                     help="key=value entry of the library's tuning table (repeatable)")
     args = ap.parse_args()
@@ -60,7 +61,7 @@ def main():
              + np.sin(2 * th[:, 0]) * th[:, 1])
         emu = api.Emulator(-np.ones(4), np.ones(4), seed=7)
         emu.train(th, y, epochs=2, batch=64)
-        thi = torch.as_tensor(rng.uniform(-1.05, 1.05, size=(1 << 18, 4)), device="cuda")
+        thi = torch.as_tensor(rng.uniform(-1.05, 1.05, size=(args.points, 4)), device="cuda")
         fn = lambda: emu.predict(thi)
     elif args.case == "ybuild":
         fn = lambda: api.ybuild(prob)
@@ -87,7 +88,10 @@ def main():
         fn()
     e1.record()
     e1.synchronize()
-    print(f"{args.case}: {e0.elapsed_time(e1) / args.reps:.3f} ms per call")
+    ms = e0.elapsed_time(e1) / args.reps
+    print(f"{args.case}: {ms:.3f} ms per call")
+    if args.case == "emu_predict":
+        print(f"emu_predict: {args.points / (ms * 1e-3):.4g} points/s")
 
 
 if __name__ == "__main__":
