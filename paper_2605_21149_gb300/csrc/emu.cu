@@ -160,9 +160,26 @@ void wmma_gemm(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_
 }
 
 // ------------------------------------------------------------ elementwise --
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// 2 Phi(z) = 1 + erf(z / sqrt 2), erf from the rational approximation of
+// Abramowitz & Stegun 7.1.26 (Hastings): for x >= 0, erf(x) = 1 - (a1 t +
+// a2 t^2 + ... + a5 t^5) e^(-x^2) with t = 1 / (1 + p x) and an absolute
+// error of at most 1.5e-7; erf(-x) = -erf(x).  So 1 + erf(z / sqrt 2) is
+// 2 - Q for z >= 0 and Q for z < 0, Q = poly(t) exp(-z^2 / 2).  Training and
+// inference both use it, so the network the inference evaluates is the one
+// trained; its error is far below the bf16 rounding of every activation.
+__device__ __forceinline__ float two_phi_f(float z) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+               0.254829592f);
+  const float q = poly * __expf(-0.5f * z * z);
+  return z >= 0.0f ? 2.0f - q : q;
+}
+// GELU(z) = z Phi(z) and its derivative Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * two_phi_f(z); }
 __device__ __forceinline__ float dgelu_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
+  return 0.5f * two_phi_f(z) + z * __expf(-0.5f * z * z) * 0.3989422804014327f;
 }
 
 // Z <- Z + b (row-major B x N); Xn = bf16(gelu(Z)) or bf16(Z)
@@ -612,9 +629,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         uint32_t a[16];
         tmem_ld16(lb + 16 * cb, a);
         const int c0 = half * kW + 16 * cb;
+        // bias + c0 is 64-byte aligned: every layer's bias starts at a
+        // multiple of 16 floats of the parameter block (widths are multiples
+        // of 16), and the launch checks the block's alignment
+        const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
         float y[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) y[j] = __uint_as_float(a[j]) + bias[c0 + j];
+        for (int j = 0; j < 4; ++j) {
+          const float4 bv = b4[j];
+          y[4 * j] = __uint_as_float(a[4 * j]) + bv.x;
+          y[4 * j + 1] = __uint_as_float(a[4 * j + 1]) + bv.y;
+          y[4 * j + 2] = __uint_as_float(a[4 * j + 2]) + bv.z;
+          y[4 * j + 3] = __uint_as_float(a[4 * j + 3]) + bv.w;
+        }
         if (row < rows) {
           if (Xn) {
             __align__(16) __nv_bfloat16 o[16];
@@ -643,6 +670,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 template <int N>
 bool launch_mlp_tc(const CUtensorMap &mX, const CUtensorMap &mW, int rows, int K, const float *bias,
                    __nv_bfloat16 *Xn, float *Z, DevStatus *st, cudaStream_t s) {
+  if (((uintptr_t)bias & 15) != 0) return false;  // the epilogue reads the bias as float4
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(mlp_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
