@@ -137,6 +137,34 @@ def test_decorrelated_vs_extended_tqu16(api, tqu16, mode):
     assert P.cl_deconv_error(est["cl_deconv"], ref["cl_deconv"][:, :100], ref["F"]) <= P.TOL
 
 
+@pytest.mark.parametrize("mode", ["mixed16", "mixed8", "float64"])
+def test_eigensolver_odd_order(api, mode):
+    """QU Nside 8, l = 2..22: F of odd order 63, padded to 64 with a
+    decoupled index, the smallest order the float32 pre-rotation takes (32
+    pairs, two per CTA at 16 CTAs).  Deconvolved and decorrelated estimates
+    against the oracle with every eigensolver form."""
+    wl = synth.make_workload("QU nside8 lmax22", 8, 22, False, True, 20.0, ("EE", "BB", "EB"), 20, 15)
+    Y, alm, noise, maps = P.oracle_maps(wl, 3)
+    ref = qml.qml_for(wl, Y, maps=maps)
+    assert ref["F"].shape[0] == 63
+    keys = {"mixed16": {"eig_mixed": 1, "eig_cluster": 16},
+            "mixed8": {"eig_mixed": 1, "eig_cluster": 8},
+            "float64": {"eig_mixed": 0}}[mode]
+    for k, v in keys.items():
+        api.tune_set(k, v)
+    try:
+        F, plan = api.fisher(api.Problem.from_workload(wl))
+        est = plan.estimate(td(maps))
+        plan.free()
+    finally:
+        api.tune_set("eig_mixed", 1)
+        api.tune_set("eig_cluster", 16)
+    ge, ee = P.fisher_errors(F, ref["F"])
+    assert ge <= P.TOL and ee <= P.TOL, (ge, ee)
+    assert P.cl_deconv_error(est["cl_deconv"], ref["cl_deconv"], ref["F"]) <= P.TOL
+    assert P.cl_decorr_error(est["cl_decorr"], ref["cl_decorr"]) <= P.decorr_tol(ref["F"])
+
+
 def test_free_plans():
     for F, plan in _PLANS.values():
         plan.free()
