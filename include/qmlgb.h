@@ -158,9 +158,12 @@ qml_status qml_synthesize(const qml_problem *prob, const double *alm, const doub
  * lmax_sig) the out-of-window fiducial signal is part of C (pixel basis) or
  * of N_eff (harmonic basis) and F covers the window.  With prob->nbins > 0 (Sect. 2.4) F is the
  * binned Fisher matrix, na_b x na_b with na_b = nspec nbins, and the plan's
- * noise bias and normalisations are binned too.  Errors: QML_ENOTSPD if C is
- * not positive definite; QML_EINVAL for bad bin edges, a bad signal band, or
- * (harmonic basis) a fiducial block that is not positive definite. */
+ * noise bias and normalisations are binned too.  The plan's F^-1 and F^-1/2
+ * come from a Jacobi eigendecomposition of F on the device (tuning keys
+ * eig_onesided, eig_mixed, eig_cluster).  Errors: QML_ENOTSPD if C is not
+ * positive definite (info = the failing column) or F has an eigenvalue <= 0
+ * (info = -1); QML_EINVAL for bad bin edges, a bad signal band, or (harmonic
+ * basis) a fiducial block that is not positive definite. */
 qml_status qml_fisher(const qml_problem *prob, double *F, qml_plan **plan, void *stream);
 
 /* Quadratic estimates for nsims maps (n x nsims) against a plan from
