@@ -25,6 +25,7 @@
 // which keeps A exactly symmetric.  Barrier waits are bounded: after
 // kSpinLimit polls a block records QML_ETIMEOUT and every block returns.
 #include "internal.cuh"
+#include "jacobi_sched.cuh"
 #include "ptx.cuh"
 
 #include <math.h>
@@ -86,10 +87,8 @@ __device__ bool grid_barrier(DevStatus *st, unsigned *flags, unsigned &epoch, un
 }
 
 // round-robin (circle) schedule: slot a of round r holds player(a, r); slots
-// a and n-1-a (a < n/2) form a pair, player 0 never moves
-__device__ __forceinline__ int player(int x, int r, int n) {
-  return x == 0 ? 0 : ((x - 1 + r) % (n - 1)) + 1;
-}
+// a and n-1-a (a < n/2) form a pair, player 0 never moves (jacobi_sched.cuh)
+__device__ __forceinline__ int player(int x, int r, int n) { return jac_player(x, r, n); }
 __device__ __forceinline__ int slot_of(int y, int r, int n) {
   return y == 0 ? 0 : (((y - 1 - r) % (n - 1)) + (n - 1)) % (n - 1) + 1;
 }
@@ -664,7 +663,7 @@ __global__ void __launch_bounds__(kJ32Threads) jacobi32_kernel(const double *A, 
   extern __shared__ __align__(16) unsigned char j32_smem[];
   const int h = n / 2;
   const int rank = (int)cluster_ctarank();
-  const int lo = rank * h / CN, np = (rank + 1) * h / CN - lo;
+  const int lo = j32_lo(rank, h, CN), np = j32_lo(rank + 1, h, CN) - lo;
   const int maxp = (h + CN - 1) / CN;
   float *cols = (float *)j32_smem;
   double *part = (double *)(j32_smem + 16 * (size_t)maxp * n);
@@ -675,7 +674,7 @@ __global__ void __launch_bounds__(kJ32Threads) jacobi32_kernel(const double *A, 
   unsigned char *own = (unsigned char *)(tab + 4 * n);
   __shared__ double sred[2][kJ32Threads / 32];
   auto col = [&](int par, int la, int side) { return cols + ((size_t)(par * maxp + la) * 2 + side) * n; };
-  for (int a = threadIdx.x; a < h; a += blockDim.x) own[a] = (unsigned char)(((a + 1) * CN + h - 1) / h - 1);
+  for (int a = threadIdx.x; a < h; a += blockDim.x) own[a] = (unsigned char)j32_owner(a, h, CN);
   // scale by 2^-e, e the binary exponent of the largest diagonal entry
   double mx = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(A[i + (size_t)i * n]));
@@ -781,10 +780,12 @@ __global__ void __launch_bounds__(kJ32Threads) jacobi32_kernel(const double *A, 
         const float y10 = ra.x * x10 - ra.y * x11, y11 = ra.y * x10 + ra.x * x11;
         const float z00 = rb.x * y00 - rb.y * y10, z10 = rb.y * y00 + rb.x * y10;
         const float z01 = rb.x * y01 - rb.y * y11, z11 = rb.y * y01 + rb.x * y11;
-        const int dpa = a <= 1 ? 0 : a - 1, dps = a == 1 ? 1 : 0;
-        const int dqa = a == h - 1 ? h - 1 : a + 1, dqs = a == h - 1 ? 0 : 1;
+        int dpa, dps, dqa, dqs;
+        j32_dest_P(a, dpa, dps);
+        j32_dest_Q(a, h, dqa, dqs);
         const int cp = own[dpa], cq = own[dqa];
-        float *DP = col(par ^ 1, dpa - cp * h / CN, dps), *DQ = col(par ^ 1, dqa - cq * h / CN, dqs);
+        float *DP = col(par ^ 1, dpa - j32_lo(cp, h, CN), dps);
+        float *DQ = col(par ^ 1, dqa - j32_lo(cq, h, CN), dqs);
         if (cp == rank) {
           DP[pb] = z00;
           DP[qb] = z10;
@@ -801,24 +802,14 @@ __global__ void __launch_bounds__(kJ32Threads) jacobi32_kernel(const double *A, 
           dsm_st_f32(d + 4u * pb, z01);
           dsm_st_f32(d + 4u * qb, z11);
         }
-        // the next round's rotation inputs among these entries: the diagonal
-        // of both columns (in the pair's own block, b == a: rows pb and qb
-        // are the columns' players) and, for a column that becomes a P
-        // column, its row at the next round's partner
-        if (b == a) {
-          bcast(dpa, dps, z00);      // P column: a_pp of P(dpa), or a_qq of Q(0)
-          bcast(dqa, dqs, z11);      // Q column: a_qq of Q(dqa), or a_pp of P(h - 1)
-        }
-        if (dps == 0) {
-          const int rq = pl2[n - 1 - dpa];
-          if (pb == rq) bcast(dpa, 2, z00);
-          else if (qb == rq) bcast(dpa, 2, z10);
-        }
-        if (dqs == 0) {
-          const int rq = pl2[h];
-          if (pb == rq) bcast(dqa, 2, z01);
-          else if (qb == rq) bcast(dqa, 2, z11);
-        }
+        // the next round's rotation inputs among these entries, into every
+        // CTA's table
+        int tp[4], ts[4], te[4];
+        const int m = j32_next_inputs(a, b, h, pb, qb, dps == 0 ? (int)pl2[n - 1 - dpa] : -1,
+                                      dqs == 0 ? (int)pl2[h] : -1, tp, ts, te);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (i < m) bcast(tp[i], ts[i], te[i] == 0 ? z00 : (te[i] == 1 ? z10 : (te[i] == 2 ? z01 : z11)));
         la += dla;
         b += db;
         if (b >= h) {
