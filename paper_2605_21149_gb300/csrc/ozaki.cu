@@ -46,6 +46,7 @@
 // Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the CTA records
 // QML_ETIMEOUT, drains what it issued, frees TMEM and returns.
 #include "fixconv.cuh"
+#include "oz_order.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -147,65 +148,13 @@ __device__ __forceinline__ bool fixed_to_double(long long acc, int E, bool neg, 
   return true;
 }
 
+// the tile (single form) or tile-row pair (pair form) of a work item
+// (oz_order.cuh)
 __device__ __forceinline__ void tile_of(const OzParams &p, int bid, int &tm, int &tn) {
-  if (!p.lower) {
-    tm = bid / p.tiles_n;
-    tn = bid % p.tiles_n;
-    return;
-  }
-  // lower-triangle tiles (tm >= tn), row by row
-  int r = (int)((sqrt(8.0 * bid + 1.0) - 1.0) * 0.5);
-  while ((r + 1) * (r + 2) / 2 <= bid) ++r;
-  while (r * (r + 1) / 2 > bid) --r;
-  tm = r;
-  tn = bid - r * (r + 1) / 2;
-}
-// Pairs of tiles for the two CTAs of a cluster: pair (TM, tn) is tile rows
-// 2 TM and 2 TM + 1 of tile column tn (one B tile shared by both).  Lower C:
-// only the pairs with tn <= 2 TM + 1 (and tn < tiles_m); a tile above the
-// diagonal or past the last tile row is computed on zeros or discarded, and
-// stores nothing.  Order: bands of p.band row pairs (tuning key ozaki_band,
-// default 6; 1 gives row-pair by row-pair order), inside a band column by
-// column and the band's row pairs within each column.  The persistent grid
-// takes the items in waves of one pair per cluster, which all stream K in
-// step, and a wave over a compact band of rows and columns reads fewer
-// distinct digit panels from DRAM than one along whole rows (about 25 panels
-// a wave instead of about 45 at k = 6900).
-// items of column tn in the band of row pairs [t0, t1) (lower C)
-__device__ __forceinline__ int band_col_count(int tn, int t0, int t1) {
-  const int need = tn >= 1 ? tn / 2 : 0;  // the smallest TM with 2 TM + 1 >= tn
-  const int lo = need > t0 ? need : t0;
-  return t1 > lo ? t1 - lo : 0;
+  oz_tile_of(p.lower, p.tiles_n, bid, tm, tn);
 }
 __device__ __forceinline__ void pair_of(const OzParams &p, int idx, int &TM, int &tn) {
-  const int T2 = (p.tiles_m + 1) / 2;
-  for (int t0 = 0; t0 < T2; t0 += p.band) {
-    const int t1 = t0 + p.band < T2 ? t0 + p.band : T2;
-    // columns of this band: all of C, or for a lower C those up to the last
-    // row pair's diagonal (and inside the matrix)
-    const int ncol = p.lower ? (2 * t1 < p.tiles_m ? 2 * t1 : p.tiles_m) : p.tiles_n;
-    if (!p.lower) {
-      const int cnt = (t1 - t0) * ncol;
-      if (idx < cnt) {
-        tn = idx / (t1 - t0);
-        TM = t0 + idx % (t1 - t0);
-        return;
-      }
-      idx -= cnt;
-      continue;
-    }
-    for (int c = 0; c < ncol; ++c) {
-      const int cc = band_col_count(c, t0, t1);
-      if (idx < cc) {
-        tn = c;
-        TM = t1 - cc + idx;
-        return;
-      }
-      idx -= cc;
-    }
-  }
-  TM = T2;  // past the last item (not reached for idx < p.ntiles)
-  tn = 0;
+  oz_pair_of(p.tiles_m, p.tiles_n, p.lower, p.band, idx, TM, tn);
 }
 // This CTA's rank in its pair, its first work item and the stride between
 // its items (read from special registers where used: held in registers
@@ -1096,17 +1045,10 @@ cudaError_t ozaki_gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, double a
     const int64_t b = tune_get("ozaki_band", 6);
     p.band = b < 1 ? 1 : (b > 4096 ? 4096 : (int)b);
   }
-  const int ntiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * p.tiles_n;
   // clusters of two on tile-row pairs (B shared through multicast) unless
   // switched off or the output has a single tile row
   const bool pairs = tune_get("ozaki_pairs", 1) != 0 && tiles_m >= 2;
-  if (pairs) {
-    const int T2 = (tiles_m + 1) / 2;
-    p.ntiles = lower ? (tiles_m % 2 == 0 ? T2 * (T2 + 1) : (T2 - 1) * T2 + tiles_m)
-                     : T2 * p.tiles_n;
-  } else {
-    p.ntiles = ntiles;
-  }
+  p.ntiles = oz_item_count(tiles_m, p.tiles_n, lower ? 1 : 0, pairs ? 1 : 0);
   return launch_oz(p.ntiles, pairs, reserve_sms, mA, mB, m3, p, st);
 }
 
