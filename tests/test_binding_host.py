@@ -61,3 +61,29 @@ def test_vectors_and_flat_inputs():
 def test_host_outputs_are_column_major():
     out = api._empty(3, 4, False)
     assert out.shape == (3, 4) and out.flags["F_CONTIGUOUS"] and out.dtype == np.float64
+
+
+def test_problem_struct_from_workload():
+    """qml_problem filled from a workload in host mode: sizes, spectra ids,
+    pointers to the geometry, transfer, spectra and the column-major noise."""
+    from paper_2605_21149_gb300 import synth
+    wl = synth.make_workload("QU nside4 lmax7", 4, 7, False, True, 30.0, ("EE", "BB", "EB"), 4, 3)
+    edges = [3, 5, 7]  # bins l = 3..4 and 5..6 of the window
+    prob = api.Problem.from_workload(wl, device=False, precision=1, bin_edges=edges,
+                                     window=(3, 6), basis=api.BASIS_AUTO)
+    p = prob._p
+    assert (p.has_T, p.has_P) == (0, 1)
+    assert p.npix_T == 0 and p.npix_P == len(wl.theta_P)
+    assert prob.n == 2 * len(wl.theta_P) == wl.n
+    assert (p.lmin, p.lmax) == (3, 6) and (p.lmin_sig, p.lmax_sig) == (wl.lmin, wl.lmax)
+    assert p.nspec == 3 and [p.spec[i] for i in range(3)] == [1, 2, 5]
+    assert p.precision == 1 and p.basis == api.BASIS_AUTO
+    assert p.nbins == 2 and prob.na == 3 * 2
+    got_edges = np.ctypeslib.as_array((ctypes.c_int32 * 3).from_address(p.bin_edges))
+    np.testing.assert_array_equal(got_edges, edges)
+    th = np.ctypeslib.as_array((ctypes.c_double * p.npix_P).from_address(p.theta_P))
+    np.testing.assert_array_equal(th, wl.theta_P)
+    cl = np.ctypeslib.as_array((ctypes.c_double * wl.cl_fid.size).from_address(p.cl_fid))
+    np.testing.assert_array_equal(cl, wl.cl_fid.reshape(-1))
+    np.testing.assert_array_equal(_read_colmajor(p.N, wl.n, wl.n), wl.N())
+    assert not p.theta_T and not p.transfer_T
